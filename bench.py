@@ -1,0 +1,310 @@
+#!/usr/bin/env python
+"""Benchmark of GB300 sort-based matching (one JSON line on stdout).
+
+Workload (default): d = 1, N = 1e6 extents (500k subscriptions + 500k
+updates), float32 starts uniform in [0, 1e6), equal length alpha * L / N with
+alpha = 100 (the paper's Section 5 methodology), enumerate mode: the full
+sorted (sub, upd) pair list, K ~ 5e7 pairs.  One step = one ddm_match call
+(key build, radix sort, sweep scan, counts, offsets, emission, segment sort)
+with inputs and output resident in HBM; a 256 MiB buffer is written between
+timed steps so that the 8 MB of inputs never start in L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (serial Algorithm 4 in C) on the host
+cores instead, each step a bounded sample of the same workload.
+Under torchrun (N > 1) every rank runs an independent replica (its own seed):
+the matching of independent instances needs no exchange, so scaling is weak.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+L2_FLUSH_BYTES = 256 << 20
+REF_SAMPLE_SUBS = 250_000   # oracle sample: first 250k subscriptions x all updates
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--alpha", type=float, default=100.0)
+    ap.add_argument("--N", type=int, default=1_000_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def workload(args, rank: int):
+    return synth.large_1d(args.alpha, replica=rank, N=args.N)
+
+
+def workload_name(args):
+    return (f"d=1, N={args.N:.0e} ({args.N // 2} subs + {args.N - args.N // 2} upds), "
+            f"alpha={args.alpha:g}, enumerate (sorted pair list)")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait(timeout=5)
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4)
+                          if r[5 + k].strip().lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def cpu_baseline(reg, seconds: float):
+    import oracle
+    sample = synth.Regions(reg.sub_lo[:, :REF_SAMPLE_SUBS].copy(),
+                           reg.sub_hi[:, :REF_SAMPLE_SUBS].copy(), reg.upd_lo, reg.upd_hi)
+    times, K = [], 0
+    t_end = time.perf_counter() + seconds
+    while time.perf_counter() < t_end or not times:
+        t0 = time.perf_counter()
+        K = len(oracle.sbm(sample))
+        times.append(time.perf_counter() - t0)
+    return {"value": K / statistics.mean(times), "unit": "pairs/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {REF_SAMPLE_SUBS} subscriptions x all {reg.m} updates of the "
+                      f"same workload (K={K}), serial C Algorithm 4 + pair sort, "
+                      f"{len(times)} runs, host cpu_count={os.cpu_count()}"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    reg = workload(args, 0)
+    sample = synth.Regions(reg.sub_lo[:, :REF_SAMPLE_SUBS].copy(),
+                           reg.sub_hi[:, :REF_SAMPLE_SUBS].copy(), reg.upd_lo, reg.upd_hi)
+    for _ in range(args.warmup):
+        oracle.sbm(sample)
+    times, K = [], 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        K = len(oracle.sbm(sample))
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = K * args.steps / total
+    line = {"impl": "reference", "metric": "matched pairs/s", "value": value, "unit": "pairs/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_name(args) + f"; each step a bounded sample: first "
+                                                         f"{REF_SAMPLE_SUBS} subscriptions",
+                       "N": args.N, "d": 1, "alpha": args.alpha, "K_sample": K},
+            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+                             "sample": f"first {REF_SAMPLE_SUBS} subscriptions x all updates"},
+            "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1703_06680_gb300 as ddm
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    reg = workload(args, rank)
+    t_in = [torch.from_numpy(a).to(dev) for a in (reg.sub_lo, reg.sub_hi, reg.upd_lo, reg.upd_hi)]
+    stream = torch.cuda.current_stream(dev)
+    ctx = ddm.Context(local, stream=stream)
+    K = ctx.count(*t_in)
+    out = torch.empty((max(K, 1), 2), dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        return ctx.match_into(out[:K], *t_in)
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        assert step() == K
+    ctx.set_profiling(True)
+    stage_sum = {}
+    l0 = ctx.stats()["launches"]
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for s in range(args.steps):
+        flush.fill_(float(s))               # L2 flush, outside the timed events
+        ev[s][0].record(stream)
+        step()
+        ev[s][1].record(stream)
+        for k, v in ctx.stats()["stage_ms"].items():
+            stage_sum[k] = stage_sum.get(k, 0.0) + v
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - wall0
+    launches = ctx.stats()["launches"] - l0
+    clocks = sampler.stop()
+    ctx.set_profiling(False)
+    t_ms = sum(a.elapsed_time(b) for a, b in ev)
+    t_max = torch.tensor([t_ms], dtype=torch.float64, device=dev)
+    k_all = torch.tensor([float(K)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+        dist.all_reduce(k_all, op=dist.ReduceOp.SUM)
+    t_max_s = float(t_max.item()) / 1e3
+    value = float(k_all.item()) * args.steps / t_max_s
+    ms_step = 1e3 * t_max_s / args.steps
+
+    # End to end through the public API with HOST buffers (pinned), copies inside.
+    host_in = [torch.from_numpy(a).pin_memory().numpy() for a in
+               (reg.sub_lo, reg.sub_hi, reg.upd_lo, reg.upd_hi)]
+    host_out = torch.empty((max(K, 1), 2), dtype=torch.int32).pin_memory().numpy()
+    e2e_steps = max(3, min(args.steps, 30))
+    for _ in range(2):
+        ctx.match_host(*host_in, out=host_out[:K])
+    barrier()
+    e2e_t = 0.0
+    for _ in range(e2e_steps):
+        flush.fill_(2.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        got = ctx.match_host(*host_in, out=host_out[:K])
+        e2e_t += time.perf_counter() - t0
+    assert len(got) == K
+    e2e_t_all = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(e2e_t_all, op=dist.ReduceOp.MAX)
+    e2e_value = float(k_all.item()) * e2e_steps / float(e2e_t_all.item())
+
+    # Roofline of the dominant stage (per-stage CUDA events on the launching stream).
+    stage_avg = {k: v / args.steps for k, v in stage_sum.items()}
+    top = max(stage_avg, key=stage_avg.get)
+    N, n, m = args.N, reg.n, reg.m
+    E = 2 * N
+    alg_bytes = {   # algorithmic bytes per launch of each stage
+        "keybuild": 8 * N + 16 * E,
+        "radix_sort": 4 * 16 * E - 4 * E,
+        "sweep_scan": 4 * E + 20 * N + 4 * N,
+        "counts": 12 * n,
+        "offsets": 4 * n + 8 * (n + 1),
+        "emit": 8 * K,
+        "segsort": 8 * K,
+    }
+    hbm, peak_kind = peaks()
+    top_ms = stage_avg[top]
+    achieved = alg_bytes.get(top, 0) / (top_ms * 1e-3) / 1e9 if top_ms > 0 else 0.0
+    traffic = None
+    prof_txt = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof_txt):
+        with open(prof_txt) as fh:
+            traffic = json.load(fh).get(top)
+    path_bytes = 8 * N * 1 + 8 * K
+    line = {
+        "metric": "matched pairs/s", "value": value, "unit": "pairs/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": workload_name(args), "N": N, "d": 1, "alpha": args.alpha, "K": K,
+                   "seed": synth.seed_for(1, rank),
+                   "l2": f"{L2_FLUSH_BYTES >> 20} MiB buffer written between timed steps"},
+        "regions_per_s": N * world * args.steps / t_max_s,
+        "roofline": {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": hbm,
+                     "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
+                     "peak_kind": peak_kind},
+        "path_roofline": {"bytes_alg": path_bytes, "achieved_gbs": path_bytes / (ms_step * 1e-3) / 1e9,
+                          "frac": path_bytes / (ms_step * 1e-3) / 1e9 / hbm},
+        "stages_ms": stage_avg,
+        "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": 4 * 2 * (n + m),
+                "d2h_bytes_per_step": 8 * K},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "wall_s_timed": wall,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(reg, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

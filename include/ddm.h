@@ -1,0 +1,159 @@
+/*
+ * ddm.h -- C ABI of the GB300 (sm_103a) Sort-Based Matching library.
+ *
+ * The library solves the Data Distribution Management matching problem of
+ * Marzolla and D'Angelo, "Parallel Sort-Based Matching for Data Distribution
+ * Management on Shared-Memory Multiprocessors" (DS-RT 2017), Section 3: given
+ * subscription extents S_0..S_{n-1} and update extents U_0..U_{m-1}, which are
+ * d-dimensional axis-parallel rectangles with closed sides, report every pair
+ * (i, j) such that S_i and U_j intersect.  Two closed intervals intersect iff
+ * x.low <= y.high and y.low <= x.high (Algorithm 1); two rectangles intersect
+ * iff their projections intersect in every dimension (Section 3).
+ *
+ * Method (Algorithm 4, Sort-Based Matching, re-planned for one GPU): the
+ * endpoints of dimension 0 are turned into order-preserving integer keys and
+ * radix sorted, with every lower endpoint placed before every upper endpoint
+ * at equal coordinates (so that touching extents are reported, as closed
+ * intervals require); one scan over the sorted stream yields the sizes of the
+ * paper's active sets SubSet/UpdSet, and from them the exact number of matches
+ * of every subscription; an exclusive scan turns these counts into output
+ * offsets; the pairs are then written, with dimensions 1..d-1 filtered per
+ * candidate.  All work runs in the library's CUDA kernels; there is no CPU
+ * fallback.
+ *
+ * Conventions for every entry point:
+ *   - Ids are 0-based indices into the caller's arrays.
+ *   - Coordinates are IEEE float32.  -0 equals +0; +-inf are allowed; NaN,
+ *     or lo > hi in any dimension, makes the call fail with DDM_ERR_INVALID.
+ *   - Limits: 1 <= d <= DDM_MAX_DIMS; n >= 0, m >= 0, n + m <= DDM_MAX_REGIONS.
+ *   - Pointers marked "device" must be device memory of the context's GPU
+ *     (cudaMalloc, or torch tensors); pointers marked "host" are ordinary or
+ *     pinned host memory.  The caller owns all of them; the library only reads
+ *     inputs and writes outputs, and keeps no pointer after the call returns.
+ *   - Calls on one context are not thread-safe; use one context per thread and
+ *     stream.  Different contexts may run concurrently.
+ *   - On error the outputs are unspecified, except *K_out for
+ *     DDM_ERR_CAPACITY.  ddm_last_error() returns a message.
+ */
+#ifndef DDM_H
+#define DDM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DDM_OK                  0
+#define DDM_ERR_INVALID       (-1)  /* bad argument, NaN coordinate, or lo > hi   */
+#define DDM_ERR_CAPACITY      (-2)  /* more pairs than the output can hold        */
+#define DDM_ERR_NOMEM         (-3)  /* device memory or the context budget exhausted */
+#define DDM_ERR_DEVICE_TIMEOUT (-4) /* a bounded device-side wait expired         */
+#define DDM_ERR_CUDA          (-5)  /* a CUDA runtime call failed                 */
+#define DDM_ERR_INTERNAL      (-6)  /* a device-side consistency check failed     */
+
+#define DDM_MAX_DIMS      8
+#define DDM_MAX_REGIONS   ((int64_t)1 << 29)   /* n + m; keeps 2(n+m) < 2^30 */
+
+typedef struct ddm_ctx ddm_ctx;
+
+/*
+ * One matching instance (Section 3 problem statement).  sub_lo, sub_hi,
+ * upd_lo and upd_hi are HOST arrays of d pointers; sub_lo[k] points to n
+ * floats, the lower bounds of S_0..S_{n-1} along dimension k (likewise for the
+ * others).  Whether the d pointers themselves are device or host memory is
+ * fixed by the entry point (see each).
+ */
+typedef struct {
+    int d;
+    int64_t n, m;
+    const float *const *sub_lo;
+    const float *const *sub_hi;
+    const float *const *upd_lo;
+    const float *const *upd_hi;
+} ddm_regions;
+
+/*
+ * Creates a context on CUDA device `device`, bound to `cuda_stream` (a
+ * cudaStream_t; NULL means the legacy default stream).  All of the context's
+ * kernels run on that stream.  mem_budget_bytes caps the scratch memory the
+ * context may hold (0 = no cap); scratch is kept between calls and grows on
+ * demand.  Returns DDM_OK and *out, or an error code (then *out is NULL).
+ */
+int ddm_create(ddm_ctx **out, int device, void *cuda_stream, size_t mem_budget_bytes);
+
+/* Frees the context and its scratch memory.  ddm_destroy(NULL) is a no-op. */
+int ddm_destroy(ddm_ctx *ctx);
+
+/* Text of the last error on this context (never NULL; empty after success). */
+const char *ddm_last_error(const ddm_ctx *ctx);
+
+/*
+ * Exact number K of intersecting (S_i, U_j) pairs; the pairs are not stored
+ * (the paper's measured mode, Section 5, "Experimental setup").  Coordinate
+ * pointers are DEVICE memory.  Synchronous: returns after the work on the
+ * context's stream has finished.
+ */
+int ddm_count(ddm_ctx *ctx, const ddm_regions *regions, uint64_t *K_out);
+
+/*
+ * All intersecting pairs (Section 3), as K interleaved int32 pairs
+ * pairs[2k] = i (subscription id), pairs[2k+1] = j (update id), sorted
+ * lexicographically by (i, j); each pair appears once.  `pairs` is DEVICE
+ * memory for 2 * cap int32 values.  If K > cap nothing is written, *K_out = K
+ * and DDM_ERR_CAPACITY is returned, so the caller can retry with a larger
+ * buffer.  Synchronous, like ddm_count.
+ */
+int ddm_match(ddm_ctx *ctx, const ddm_regions *regions, int32_t *pairs, uint64_t cap,
+              uint64_t *K_out);
+
+/*
+ * ddm_match with HOST buffers: the coordinates are read from host memory and
+ * the pairs written to host memory (`pairs` holds 2 * cap int32).  The
+ * library copies through its own device buffers; pinned host memory makes the
+ * copies faster.  Same result and errors as ddm_match.
+ */
+int ddm_match_host(ddm_ctx *ctx, const ddm_regions *regions, int32_t *pairs, uint64_t cap,
+                   uint64_t *K_out);
+
+/*
+ * Counters and per-stage timing.  With profiling enabled (ddm_set_profiling),
+ * every call records CUDA events on the context's stream at the stage
+ * boundaries, and stage_ms[] holds the device time of each stage of the last
+ * call: 0 key build (a1), 1 radix sort (a2), 2 sweep scan (a3), 3 counts --
+ * rank arithmetic for d = 1, filter count for d > 1 (a4/a7), 4 offsets scan
+ * (a5), 5 pair emission (a6/a7), 6 per-segment sort (a6), 7 unused.
+ * `launches` counts every kernel the context has launched since creation.
+ */
+#define DDM_STAGES 8
+typedef struct {
+    uint64_t launches;
+    uint64_t calls;
+    float stage_ms[DDM_STAGES];
+} ddm_stats;
+
+int ddm_set_profiling(ddm_ctx *ctx, int enable);
+int ddm_get_stats(const ddm_ctx *ctx, ddm_stats *out);
+
+/*
+ * Diagnostic view of the sweep stages for dimension 0 (the sorted endpoint
+ * list T of Algorithm 4 and the active-set sizes it maintains), for tests.
+ * All outputs are DEVICE memory, E = 2(n+m) entries unless noted:
+ *   sorted_who[t]   endpoint t of the sorted list: (kind << 30) | id, kind 0 =
+ *                   S lower, 1 = U lower, 2 = S upper, 3 = U upper;
+ *   subset_size[t]  |SubSet| right after endpoint t is processed;
+ *   updset_size[t]  |UpdSet| right after endpoint t is processed;
+ *   sub_count[i]    number of updates intersecting S_i along dimension 0 (n);
+ *   upd_count[j]    number of subscriptions intersecting U_j along dim 0 (m).
+ * Any output pointer may be NULL to skip it.
+ */
+int ddm_debug_sweep(ddm_ctx *ctx, const ddm_regions *regions, uint32_t *sorted_who,
+                    uint32_t *subset_size, uint32_t *updset_size, uint32_t *sub_count,
+                    uint32_t *upd_count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DDM_H */

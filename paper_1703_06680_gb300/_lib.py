@@ -1,0 +1,250 @@
+"""ctypes binding of the C ABI in include/ddm.h (argument marshalling only).
+
+Every computation runs in the CUDA library; this module only turns torch
+tensors (device memory) and numpy arrays (host memory) into the pointers and
+sizes the C functions take.  If the library is missing the import of a
+Context fails loudly: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+
+DDM_OK = 0
+DDM_ERR_INVALID = -1
+DDM_ERR_CAPACITY = -2
+DDM_ERR_NOMEM = -3
+DDM_ERR_DEVICE_TIMEOUT = -4
+DDM_ERR_CUDA = -5
+DDM_ERR_INTERNAL = -6
+MAX_DIMS = 8
+
+
+class DDMError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+class CapacityError(DDMError):
+    def __init__(self, code: int, msg: str, K: int):
+        super().__init__(code, msg)
+        self.K = K
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint64), ("calls", ctypes.c_uint64),
+                ("stage_ms", ctypes.c_float * 8)]
+
+
+STAGE_NAMES = ["keybuild", "radix_sort", "sweep_scan", "counts", "offsets", "emit", "segsort",
+               "unused"]
+
+
+class _Regions(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("n", ctypes.c_int64), ("m", ctypes.c_int64),
+                ("sub_lo", ctypes.POINTER(ctypes.c_void_p)),
+                ("sub_hi", ctypes.POINTER(ctypes.c_void_p)),
+                ("upd_lo", ctypes.POINTER(ctypes.c_void_p)),
+                ("upd_hi", ctypes.POINTER(ctypes.c_void_p))]
+
+
+_lib = None
+_lock = threading.Lock()
+_P = ctypes.c_void_p
+_U64P = ctypes.POINTER(ctypes.c_uint64)
+_RP = ctypes.POINTER(_Regions)
+
+# name -> (restype, argtypes) for every entry point of include/ddm.h
+SIGNATURES = {
+    "ddm_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _P, ctypes.c_size_t]),
+    "ddm_destroy": (ctypes.c_int, [_P]),
+    "ddm_last_error": (ctypes.c_char_p, [_P]),
+    "ddm_count": (ctypes.c_int, [_P, _RP, _U64P]),
+    "ddm_match": (ctypes.c_int, [_P, _RP, _P, ctypes.c_uint64, _U64P]),
+    "ddm_match_host": (ctypes.c_int, [_P, _RP, _P, ctypes.c_uint64, _U64P]),
+    "ddm_debug_sweep": (ctypes.c_int, [_P, _RP, _P, _P, _P, _P, _P]),
+    "ddm_set_profiling": (ctypes.c_int, [_P, ctypes.c_int]),
+    "ddm_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(Stats)]),
+}
+
+
+def load_library(path: str | None = None):
+    """Loads libddm.so (built by build.build()); raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise ImportError(f"CUDA library {p} is missing: run paper_1703_06680_gb300.build."
+                              "build() (no CPU fallback exists)")
+        lib = ctypes.CDLL(p)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        if path is None:
+            _lib = lib
+        return lib
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class _Packed:
+    """Keeps the pointer arrays of one ddm_regions alive."""
+
+    def __init__(self, d, n, m, ptrs):
+        self.arrays = [(ctypes.c_void_p * d)(*p) for p in ptrs]
+        self.s = _Regions(d, n, m, *[ctypes.cast(a, ctypes.POINTER(ctypes.c_void_p))
+                                     for a in self.arrays])
+
+    @property
+    def ref(self):
+        return ctypes.byref(self.s)
+
+
+def _pack_device(sub_lo, sub_hi, upd_lo, upd_hi):
+    torch = _torch()
+    ts = [sub_lo, sub_hi, upd_lo, upd_hi]
+    for t in ts:
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32):
+            raise TypeError("coordinates must be float32 CUDA tensors of shape (d, count)")
+        if t.dim() != 2 or not t.is_contiguous():
+            raise TypeError("coordinates must be contiguous (d, count) tensors")
+    d, n = sub_lo.shape
+    m = upd_lo.shape[1]
+    if sub_hi.shape != (d, n) or upd_lo.shape[0] != d or upd_hi.shape != (d, m):
+        raise ValueError("inconsistent coordinate shapes")
+    ptrs = [[t.data_ptr() + 4 * k * t.shape[1] for k in range(d)] for t in ts]
+    return _Packed(d, n, m, ptrs)
+
+
+def _pack_host(sub_lo, sub_hi, upd_lo, upd_hi):
+    arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (sub_lo, sub_hi, upd_lo, upd_hi)]
+    d, n = arrs[0].shape
+    m = arrs[2].shape[1]
+    ptrs = [[a.ctypes.data + 4 * k * a.shape[1] for k in range(d)] for a in arrs]
+    p = _Packed(d, n, m, ptrs)
+    p.keep = arrs
+    return p
+
+
+class Context:
+    """A library context bound to one device and one CUDA stream."""
+
+    def __init__(self, device: int = 0, stream=None, mem_budget: int = 0):
+        self._lib = load_library()
+        torch = _torch()
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.device = device
+        self.stream = stream
+        handle = ctypes.c_void_p()
+        rc = self._lib.ddm_create(ctypes.byref(handle), device, ctypes.c_void_p(stream.cuda_stream),
+                                  mem_budget)
+        if rc != DDM_OK:
+            raise DDMError(rc, "ddm_create failed")
+        self._h = handle
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.ddm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, rc: int, K: int | None = None):
+        if rc == DDM_OK:
+            return
+        msg = self._lib.ddm_last_error(self._h).decode(errors="replace")
+        if rc == DDM_ERR_CAPACITY:
+            raise CapacityError(rc, msg, int(K or 0))
+        raise DDMError(rc, msg)
+
+    def set_profiling(self, on: bool):
+        self._check(self._lib.ddm_set_profiling(self._h, int(bool(on))))
+
+    def stats(self) -> dict:
+        s = Stats()
+        self._check(self._lib.ddm_get_stats(self._h, ctypes.byref(s)))
+        return {"launches": int(s.launches), "calls": int(s.calls),
+                "stage_ms": dict(zip(STAGE_NAMES, [float(x) for x in s.stage_ms]))}
+
+    # -- entry points ----------------------------------------------------------
+    def count(self, sub_lo, sub_hi, upd_lo, upd_hi) -> int:
+        """ddm_count: exact number of intersecting pairs (device tensors)."""
+        p = _pack_device(sub_lo, sub_hi, upd_lo, upd_hi)
+        K = ctypes.c_uint64(0)
+        self._check(self._lib.ddm_count(self._h, p.ref, ctypes.byref(K)))
+        return int(K.value)
+
+    def match_into(self, out, sub_lo, sub_hi, upd_lo, upd_hi) -> int:
+        """ddm_match into a preallocated (cap, 2) int32 CUDA tensor; returns K."""
+        torch = _torch()
+        if not (out.is_cuda and out.dtype == torch.int32 and out.is_contiguous()):
+            raise TypeError("out must be a contiguous int32 CUDA tensor")
+        p = _pack_device(sub_lo, sub_hi, upd_lo, upd_hi)
+        K = ctypes.c_uint64(0)
+        cap = out.numel() // 2
+        rc = self._lib.ddm_match(self._h, p.ref, ctypes.c_void_p(out.data_ptr() if cap else 0),
+                                 cap, ctypes.byref(K))
+        self._check(rc, K.value)
+        return int(K.value)
+
+    def match(self, sub_lo, sub_hi, upd_lo, upd_hi, cap: int | None = None):
+        """ddm_match; returns the sorted (K, 2) int32 pairs as a CUDA tensor."""
+        torch = _torch()
+        if cap is None:
+            cap = self.count(sub_lo, sub_hi, upd_lo, upd_hi)
+        out = torch.empty((max(cap, 1), 2), dtype=torch.int32, device=sub_lo.device)
+        K = self.match_into(out[:cap] if cap else out[:0], sub_lo, sub_hi, upd_lo, upd_hi)
+        return out[:K]
+
+    def match_host(self, sub_lo, sub_hi, upd_lo, upd_hi, cap: int | None = None,
+                   out: np.ndarray | None = None):
+        """ddm_match_host: numpy (d, count) float32 inputs, numpy (K, 2) int32 output."""
+        p = _pack_host(sub_lo, sub_hi, upd_lo, upd_hi)
+        if out is None:
+            if cap is None:
+                raise ValueError("give cap or a preallocated out array")
+            out = np.empty((cap, 2), np.int32)
+        cap = out.shape[0]
+        K = ctypes.c_uint64(0)
+        rc = self._lib.ddm_match_host(self._h, p.ref, ctypes.c_void_p(out.ctypes.data), cap,
+                                      ctypes.byref(K))
+        self._check(rc, K.value)
+        return out[:K.value]
+
+    def debug_sweep(self, sub_lo, sub_hi, upd_lo, upd_hi):
+        """ddm_debug_sweep: (sorted_who, subset_size, updset_size, sub_count, upd_count)."""
+        torch = _torch()
+        p = _pack_device(sub_lo, sub_hi, upd_lo, upd_hi)
+        n, m = p.s.n, p.s.m
+        E = 2 * (n + m)
+        dev = sub_lo.device
+        outs = [torch.zeros(max(k, 1), dtype=torch.int32, device=dev) for k in (E, E, E, n, m)]
+        rc = self._lib.ddm_debug_sweep(self._h, p.ref, *[ctypes.c_void_p(o.data_ptr()) for o in outs])
+        self._check(rc)
+        self.stream.synchronize()
+        return tuple(o[:k] for o, k in zip(outs, (E, E, E, n, m)))

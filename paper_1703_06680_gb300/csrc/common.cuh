@@ -1,0 +1,130 @@
+// Shared device-side helpers of the SBM library (sm_103a).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ddm.h"
+
+namespace ddm {
+
+// ---------------------------------------------------------------------------
+// Endpoint payload: (kind << 30) | id, kind 0 = S lower, 1 = U lower,
+// 2 = S upper, 3 = U upper.  The key build lays endpoints out in exactly this
+// kind order ([S lowers | U lowers | S uppers | U uppers]), so a stable sort
+// by coordinate key puts every lower endpoint before every upper endpoint at
+// equal coordinates: touching closed intervals are then reported, as
+// Algorithm 1 requires.
+// ---------------------------------------------------------------------------
+constexpr uint32_t KIND_SLO = 0, KIND_ULO = 1, KIND_SHI = 2, KIND_UHI = 3;
+constexpr uint32_t ID_MASK = (1u << 30) - 1;
+
+__host__ __device__ __forceinline__ uint32_t payload(uint32_t kind, uint32_t id) {
+    return (kind << 30) | id;
+}
+
+// Order-preserving map float32 -> uint32: a < b (IEEE) iff key(a) < key(b).
+// -0 is first mapped to +0, so the two compare equal as IEEE says.  Negative
+// floats have their bits inverted, non-negative ones get the sign bit set.
+__device__ __forceinline__ uint32_t float_key(float x) {
+    uint32_t u = __float_as_uint(x);
+    if (u == 0x80000000u) u = 0u;
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__device__ __forceinline__ bool is_nan_bits(float x) {
+    return (__float_as_uint(x) & 0x7fffffffu) > 0x7f800000u;
+}
+
+// ---------------------------------------------------------------------------
+// Device status block, one per context.  The first error wins.
+// ---------------------------------------------------------------------------
+struct DevStatus {
+    int error;                 // DDM_OK or a DDM_ERR_* code
+    int detail;                // where a timeout or check fired (diagnostics)
+    unsigned long long K;      // number of pairs (after the offsets scan)
+    unsigned long long aux[6]; // per-call diagnostics / plans
+};
+
+__device__ __forceinline__ void raise_error(DevStatus* st, int code, int detail) {
+    if (atomicCAS(&st->error, 0, code) == 0) st->detail = detail;
+}
+
+__device__ __forceinline__ int read_error(const DevStatus* st) {
+    return *(volatile const int*)&st->error;
+}
+
+// ---------------------------------------------------------------------------
+// Acquire / release accesses for single-pass scans with decoupled look-back.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Every device-side wait is bounded: after SPIN_LIMIT polls (with a growing
+// nanosleep back-off, well over a second in total) the waiter raises
+// DDM_ERR_DEVICE_TIMEOUT and proceeds with a neutral value, so a kernel can
+// never hang the GPU; the host then reports the error.
+constexpr uint32_t SPIN_LIMIT = 1u << 21;
+
+__device__ __forceinline__ void backoff(uint32_t iter) {
+    __nanosleep(iter < 64 ? 32 : (iter < 4096 ? 256 : 1024));
+}
+
+// 64-bit look-back words: [flag:2 | value:62], flag 1 = tile aggregate,
+// 2 = inclusive prefix.  A zero word means "not yet published".
+constexpr unsigned long long LB64_AGG = 1ull << 62, LB64_INC = 2ull << 62;
+constexpr unsigned long long LB64_VAL = (1ull << 62) - 1;
+
+// Warp-cooperative look-back: exclusive prefix of tile `tile` over the values
+// published by tiles 0..tile-1 in `status`.  Called by all 32 lanes of one warp.
+__device__ __forceinline__ unsigned long long warp_lookback_u64(unsigned long long* status,
+                                                                long long tile, DevStatus* st,
+                                                                int where) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long sum = 0;
+    long long p = tile - 1;
+    while (p >= 0) {
+        long long q = p - lane;
+        unsigned long long v = LB64_INC;  // before tile 0: inclusive prefix 0
+        if (q >= 0) {
+            uint32_t it = 0;
+            while ((v = ld_acquire_u64(status + q)) == 0ull) {
+                if (++it > SPIN_LIMIT) {
+                    raise_error(st, DDM_ERR_DEVICE_TIMEOUT, where);
+                    v = LB64_INC;
+                    break;
+                }
+                backoff(it);
+            }
+        }
+        unsigned inc = __ballot_sync(0xffffffffu, (v >> 62) == 2ull);
+        int stop = inc ? __ffs(inc) - 1 : 32;
+        unsigned long long mine = (lane <= stop) ? (v & LB64_VAL) : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+        sum += mine;
+        if (inc) break;
+        p -= 32;
+    }
+    return sum;
+}
+
+__host__ __device__ __forceinline__ uint64_t ceil_div(uint64_t a, uint64_t b) {
+    return (a + b - 1) / b;
+}
+
+}  // namespace ddm

@@ -1,0 +1,451 @@
+// C ABI of the SBM library: contexts, workspace, and the pipeline
+// a1 key build -> a2 radix sort -> a3 sweep scan -> a4 counts (d = 1) or a7
+// filter count (d > 1) -> a5 offsets -> a6 emission (+ a7 write filter) ->
+// per-segment sort.  Everything is enqueued on the context's stream; device
+// kernels gate on the device status word (an input error or a capacity
+// overflow stops the later stages), and the host reads {status, K} once.
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "emit.cuh"
+#include "sort.cuh"
+#include "sweep.cuh"
+
+using namespace ddm;
+
+struct ddm_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    size_t budget = 0;
+    std::string err;
+    char* ws = nullptr;
+    size_t ws_size = 0;
+    DevStatus* dstat = nullptr;  // device
+    DevStatus* hstat = nullptr;  // pinned host mirror
+    // host-buffer entry point staging (inputs, outputs)
+    char* io = nullptr;
+    size_t io_size = 0;
+    char* out = nullptr;
+    size_t out_size = 0;
+    // counters and per-stage timing
+    ddm_stats stats{};
+    bool prof = false;
+    cudaEvent_t ev[DDM_STAGES + 1] = {};
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int fail(ddm_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+int cuda_fail(ddm_ctx* c, cudaError_t e, const char* what) {
+    return fail(c, DDM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, #call);     \
+    } while (0)
+
+// Bump allocator over one workspace allocation; every region 256-byte aligned.
+struct Carve {
+    size_t off = 0;
+    char* base = nullptr;
+    template <typename T>
+    T* take(size_t count) {
+        off = (off + 255) & ~(size_t)255;
+        T* p = reinterpret_cast<T*>(base ? base + off : nullptr);
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+int ensure(ddm_ctx* c, char** buf, size_t* size, size_t need) {
+    if (need <= *size) return DDM_OK;
+    const size_t total_other = c->ws_size + c->io_size + c->out_size - *size;
+    if (c->budget && need + total_other > c->budget)
+        return fail(c, DDM_ERR_NOMEM, "scratch need " + std::to_string(need) +
+                                          " bytes exceeds the context budget");
+    if (*buf) {
+        cudaFree(*buf);
+        *buf = nullptr;
+        *size = 0;
+    }
+    size_t grow = need + need / 8;
+    cudaError_t e = cudaMalloc(buf, grow);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        e = cudaMalloc(buf, need);
+        grow = need;
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *buf = nullptr;
+        return fail(c, DDM_ERR_NOMEM, "cudaMalloc of " + std::to_string(need) + " bytes failed");
+    }
+    *size = grow;
+    return DDM_OK;
+}
+
+int check_regions(ddm_ctx* c, const ddm_regions* r) {
+    if (!r) return fail(c, DDM_ERR_INVALID, "regions is NULL");
+    if (r->d < 1 || r->d > DDM_MAX_DIMS) return fail(c, DDM_ERR_INVALID, "d out of range");
+    if (r->n < 0 || r->m < 0 || r->n + r->m > DDM_MAX_REGIONS)
+        return fail(c, DDM_ERR_INVALID, "n or m out of range");
+    if (!r->sub_lo || !r->sub_hi || !r->upd_lo || !r->upd_hi)
+        return fail(c, DDM_ERR_INVALID, "coordinate pointer arrays must not be NULL");
+    for (int k = 0; k < r->d; ++k) {
+        if (r->n > 0 && (!r->sub_lo[k] || !r->sub_hi[k]))
+            return fail(c, DDM_ERR_INVALID, "NULL subscription coordinates");
+        if (r->m > 0 && (!r->upd_lo[k] || !r->upd_hi[k]))
+            return fail(c, DDM_ERR_INVALID, "NULL update coordinates");
+    }
+    return DDM_OK;
+}
+
+enum class Mode { Count, Match, Debug };
+
+// Stage boundary k (0..DDM_STAGES): records an event when profiling.
+void mark(ddm_ctx* c, int k) {
+    if (c->prof) cudaEventRecord(c->ev[k], c->stream);
+}
+
+struct DebugOut {
+    uint32_t *who, *subset, *updset, *sub_cnt, *upd_cnt;
+};
+
+// Lays out every buffer of one plain call.  With base == nullptr only sizes.
+struct Plan {
+    int64_t n, m, E;
+    int d;
+    // zeroed region
+    uint32_t* hist;
+    uint32_t* sort_lb;
+    unsigned long long* scan_status;
+    unsigned long long* off_status;
+    uint32_t* cursor_b;
+    uint32_t* big_count;
+    size_t zero_bytes;
+    // the rest
+    uint32_t *keys0, *keys1, *vals0, *vals1;
+    Records rec;
+    uint32_t *cnt, *cnt_a, *upd_cnt, *big_list;
+    unsigned long long* off;
+    uint2 *subK, *updK;
+    size_t total;
+
+    void layout(char* base, int d_, int64_t n_, int64_t m_, Mode mode) {
+        d = d_; n = n_; m = m_; E = 2 * (n + m);
+        Carve cv;
+        cv.base = base;
+        hist = cv.take<uint32_t>(4 * RADIX);
+        sort_lb = cv.take<uint32_t>(sort_lookback_words<uint32_t>(E, 4));
+        scan_status = cv.take<unsigned long long>(3 * (ceil_div(E, SCAN_TILE) + 1) + 1);
+        off_status = cv.take<unsigned long long>(ceil_div(n, OFF_TILE) + 2);
+        cursor_b = cv.take<uint32_t>(mode == Mode::Match ? n : 0);
+        big_count = cv.take<uint32_t>(2);
+        zero_bytes = (cv.off + 255) & ~(size_t)255;
+        keys0 = cv.take<uint32_t>(E);
+        keys1 = cv.take<uint32_t>(E);
+        vals0 = cv.take<uint32_t>(E);
+        vals1 = cv.take<uint32_t>(E);
+        rec.s_pos_lo = cv.take<uint32_t>(n); rec.s_pos_hi = cv.take<uint32_t>(n);
+        rec.s_A = cv.take<uint32_t>(n); rec.s_B = cv.take<uint32_t>(n); rec.s_C = cv.take<uint32_t>(n);
+        rec.u_pos_lo = cv.take<uint32_t>(m); rec.u_pos_hi = cv.take<uint32_t>(m);
+        rec.u_A = cv.take<uint32_t>(m); rec.u_B = cv.take<uint32_t>(m); rec.u_C = cv.take<uint32_t>(m);
+        rec.sub_order = cv.take<uint32_t>(n);
+        rec.upd_order = cv.take<uint32_t>(m);
+        rec.windows = nullptr;
+        rec.win_shift = 0;
+        rec.dbg_who = rec.dbg_subset = rec.dbg_updset = nullptr;
+        cnt = cv.take<uint32_t>(n);
+        cnt_a = cv.take<uint32_t>(d > 1 ? n : 0);
+        upd_cnt = nullptr;
+        big_list = cv.take<uint32_t>(mode == Mode::Match ? n : 0);
+        off = cv.take<unsigned long long>(n + 1);
+        subK = cv.take<uint2>(d > 1 ? (size_t)(d - 1) * n : 0);
+        updK = cv.take<uint2>(d > 1 ? (size_t)(d - 1) * m : 0);
+        total = cv.off + 256;
+    }
+};
+
+int id_bits(int64_t m) {
+    int b = 1;
+    while (b < 31 && ((int64_t)1 << b) < m) ++b;
+    return b;
+}
+
+// Enqueues the whole pipeline for one instance whose coordinates are device
+// pointers.  Does not synchronize.
+int enqueue_plain(ddm_ctx* c, const ddm_regions* r, Mode mode, int32_t* pairs, uint64_t cap,
+                  const DebugOut* dbg) {
+    Plan pl;
+    pl.layout(nullptr, r->d, r->n, r->m, mode);
+    int rc = ensure(c, &c->ws, &c->ws_size, pl.total);
+    if (rc) return rc;
+    pl.layout(c->ws, r->d, r->n, r->m, mode);
+    cudaStream_t s = c->stream;
+    CK(cudaMemsetAsync(c->dstat, 0, sizeof(DevStatus), s));
+    CK(cudaMemsetAsync(c->ws, 0, pl.zero_bytes, s));
+    c->stats.calls++;
+    mark(c, 0);
+    if (pl.E == 0) {
+        for (int k = 1; k <= DDM_STAGES; ++k) mark(c, k);
+        return DDM_OK;
+    }
+    uint64_t& L = c->stats.launches;
+    L += launch_keybuild_d0(r->sub_lo[0], r->sub_hi[0], r->upd_lo[0], r->upd_hi[0], pl.n, pl.m,
+                            pl.keys0, pl.vals0, pl.hist, c->dstat, s);
+    mark(c, 1);
+    L += launch_radix_sort<uint32_t>(pl.keys0, pl.vals0, pl.keys1, pl.vals1, pl.E, 4, pl.hist,
+                                     pl.sort_lb, true, c->dstat, s);
+    mark(c, 2);
+    Records rec = pl.rec;
+    if (dbg) {
+        rec.dbg_who = dbg->who;
+        rec.dbg_subset = dbg->subset;
+        rec.dbg_updset = dbg->updset;
+        if (!rec.dbg_who || !rec.dbg_subset || !rec.dbg_updset)
+            rec.dbg_who = rec.dbg_subset = rec.dbg_updset = nullptr;
+    }
+    L += launch_sweep_scan(pl.vals0, pl.E, pl.n, pl.m, rec, pl.scan_status, c->dstat, s);
+    mark(c, 3);
+
+    EmitArgs a{};
+    a.d = r->d; a.n = pl.n; a.m = pl.m;
+    for (int k = 0; k < r->d; ++k) {
+        a.dims.sub_lo[k] = r->sub_lo[k]; a.dims.sub_hi[k] = r->sub_hi[k];
+        a.dims.upd_lo[k] = r->upd_lo[k]; a.dims.upd_hi[k] = r->upd_hi[k];
+    }
+    a.rec = rec;
+    a.cnt = pl.cnt; a.off = pl.off; a.cnt_a = pl.cnt_a; a.cursor_b = pl.cursor_b;
+    a.subK = pl.subK; a.updK = pl.updK;
+    a.pairs = pairs; a.cap = cap;
+    a.big_list = pl.big_list; a.big_count = pl.big_count;
+    a.id_bits = id_bits(pl.m);
+    a.inst_sub_base = a.inst_upd_base = nullptr;
+    a.num_inst = 0;
+
+    if (r->d == 1) {
+        L += launch_rank_count(rec, pl.n, pl.m, pl.cnt, dbg ? dbg->upd_cnt : nullptr, c->dstat, s);
+    } else {
+        L += launch_permute_keys(a, c->dstat, s);
+        L += launch_filter_count(a, c->dstat, s);
+    }
+    mark(c, 4);
+    if (dbg && dbg->sub_cnt && pl.n > 0)
+        CK(cudaMemcpyAsync(dbg->sub_cnt, pl.cnt, pl.n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    L += launch_offsets(pl.cnt, pl.n, pl.off, mode == Mode::Match ? cap : ~0ull, pl.off_status,
+                        c->dstat, s);
+    mark(c, 5);
+    if (mode == Mode::Match) L += launch_emit_ranges(a, c->dstat, s);
+    mark(c, 6);
+    if (mode == Mode::Match) L += launch_segment_sort(a, c->dstat, s);
+    mark(c, 7);
+    mark(c, 8);
+    CK(cudaGetLastError());
+    return DDM_OK;
+}
+
+// Reads the device status and maps it to a return code.
+int finish(ddm_ctx* c, uint64_t* K_out) {
+    CK(cudaMemcpyAsync(c->hstat, c->dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (c->prof) {
+        for (int k = 0; k < DDM_STAGES; ++k) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, c->ev[k], c->ev[k + 1]) != cudaSuccess) {
+                cudaGetLastError();
+                ms = 0.f;
+            }
+            c->stats.stage_ms[k] = ms;
+        }
+    }
+    const DevStatus& h = *c->hstat;
+    if (K_out) *K_out = h.K;
+    switch (h.error) {
+        case DDM_OK: c->err.clear(); return DDM_OK;
+        case DDM_ERR_INVALID:
+            return fail(c, DDM_ERR_INVALID, "input has NaN coordinates or lo > hi");
+        case DDM_ERR_CAPACITY:
+            return fail(c, DDM_ERR_CAPACITY, "output capacity too small for " +
+                                                 std::to_string(h.K) + " pairs");
+        case DDM_ERR_DEVICE_TIMEOUT:
+            return fail(c, DDM_ERR_DEVICE_TIMEOUT,
+                        "a device-side wait timed out (stage " + std::to_string(h.detail) + ")");
+        default:
+            return fail(c, DDM_ERR_INTERNAL,
+                        "device consistency check failed (stage " + std::to_string(h.detail) + ")");
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int ddm_create(ddm_ctx** out, int device, void* cuda_stream, size_t mem_budget_bytes) {
+    if (!out) return DDM_ERR_INVALID;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return DDM_ERR_CUDA;
+    }
+    ddm_ctx* c = new ddm_ctx();
+    c->device = device;
+    c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    c->budget = mem_budget_bytes;
+    DeviceGuard g(device);
+    if (cudaMalloc(&c->dstat, sizeof(DevStatus)) != cudaSuccess ||
+        cudaMallocHost(&c->hstat, sizeof(DevStatus)) != cudaSuccess) {
+        cudaGetLastError();
+        if (c->dstat) cudaFree(c->dstat);
+        delete c;
+        return DDM_ERR_NOMEM;
+    }
+    memset(c->hstat, 0, sizeof(DevStatus));
+    *out = c;
+    return DDM_OK;
+}
+
+int ddm_destroy(ddm_ctx* c) {
+    if (!c) return DDM_OK;
+    DeviceGuard g(c->device);
+    cudaStreamSynchronize(c->stream);
+    for (auto& e : c->ev)
+        if (e) cudaEventDestroy(e);
+    if (c->ws) cudaFree(c->ws);
+    if (c->io) cudaFree(c->io);
+    if (c->out) cudaFree(c->out);
+    if (c->dstat) cudaFree(c->dstat);
+    if (c->hstat) cudaFreeHost(c->hstat);
+    delete c;
+    return DDM_OK;
+}
+
+const char* ddm_last_error(const ddm_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int ddm_set_profiling(ddm_ctx* c, int enable) {
+    if (!c) return DDM_ERR_INVALID;
+    DeviceGuard g(c->device);
+    if (enable && !c->ev[0]) {
+        for (auto& e : c->ev) CK(cudaEventCreate(&e));
+    }
+    c->prof = enable != 0;
+    return DDM_OK;
+}
+
+int ddm_get_stats(const ddm_ctx* c, ddm_stats* out) {
+    if (!c || !out) return DDM_ERR_INVALID;
+    *out = c->stats;
+    return DDM_OK;
+}
+
+int ddm_count(ddm_ctx* c, const ddm_regions* r, uint64_t* K_out) {
+    if (!c) return DDM_ERR_INVALID;
+    int rc = check_regions(c, r);
+    if (rc) return rc;
+    DeviceGuard g(c->device);
+    rc = enqueue_plain(c, r, Mode::Count, nullptr, 0, nullptr);
+    if (rc) return rc;
+    return finish(c, K_out);
+}
+
+int ddm_match(ddm_ctx* c, const ddm_regions* r, int32_t* pairs, uint64_t cap, uint64_t* K_out) {
+    if (!c) return DDM_ERR_INVALID;
+    int rc = check_regions(c, r);
+    if (rc) return rc;
+    if (!pairs && cap > 0) return fail(c, DDM_ERR_INVALID, "pairs is NULL but cap > 0");
+    DeviceGuard g(c->device);
+    rc = enqueue_plain(c, r, Mode::Match, pairs, cap, nullptr);
+    if (rc) return rc;
+    return finish(c, K_out);
+}
+
+int ddm_match_host(ddm_ctx* c, const ddm_regions* r, int32_t* pairs, uint64_t cap,
+                   uint64_t* K_out) {
+    if (!c) return DDM_ERR_INVALID;
+    int rc = check_regions(c, r);
+    if (rc) return rc;
+    if (!pairs && cap > 0) return fail(c, DDM_ERR_INVALID, "pairs is NULL but cap > 0");
+    DeviceGuard g(c->device);
+    const int d = r->d;
+    const int64_t n = r->n, m = r->m;
+    const float* const* src[4] = {r->sub_lo, r->sub_hi, r->upd_lo, r->upd_hi};
+    // Stage the coordinates into the io buffer.
+    Carve sizing;
+    for (int a = 0; a < 4; ++a)
+        for (int k = 0; k < d; ++k) sizing.take<float>(a < 2 ? n : m);
+    rc = ensure(c, &c->io, &c->io_size, sizing.off + 256);
+    if (rc) return rc;
+    Carve cv;
+    cv.base = c->io;
+    std::vector<const float*> dp(4 * d);
+    for (int a = 0; a < 4; ++a) {
+        const int64_t cnt = a < 2 ? n : m;
+        for (int k = 0; k < d; ++k) {
+            float* dst = cv.take<float>(cnt);
+            if (cnt > 0)
+                CK(cudaMemcpyAsync(dst, src[a][k], cnt * sizeof(float), cudaMemcpyHostToDevice,
+                                   c->stream));
+            dp[a * d + k] = dst;
+        }
+    }
+    ddm_regions dr = *r;
+    dr.sub_lo = &dp[0];
+    dr.sub_hi = &dp[d];
+    dr.upd_lo = &dp[2 * d];
+    dr.upd_hi = &dp[3 * d];
+    // Count first, so that the device output buffer can be sized to K.
+    uint64_t K = 0;
+    rc = enqueue_plain(c, &dr, Mode::Count, nullptr, 0, nullptr);
+    if (rc) return rc;
+    rc = finish(c, &K);
+    if (rc) return rc;
+    if (K_out) *K_out = K;
+    if (K > cap) return fail(c, DDM_ERR_CAPACITY, "output capacity too small for " +
+                                                      std::to_string(K) + " pairs");
+    if (K == 0) return DDM_OK;
+    rc = ensure(c, &c->out, &c->out_size, 2 * K * sizeof(int32_t));
+    if (rc) return rc;
+    int32_t* dpairs = reinterpret_cast<int32_t*>(c->out);
+    rc = enqueue_plain(c, &dr, Mode::Match, dpairs, K, nullptr);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(pairs, dpairs, 2 * K * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    return finish(c, K_out);
+}
+
+int ddm_debug_sweep(ddm_ctx* c, const ddm_regions* r, uint32_t* sorted_who,
+                    uint32_t* subset_size, uint32_t* updset_size, uint32_t* sub_count,
+                    uint32_t* upd_count) {
+    if (!c) return DDM_ERR_INVALID;
+    int rc = check_regions(c, r);
+    if (rc) return rc;
+    DeviceGuard g(c->device);
+    ddm_regions r1 = *r;
+    r1.d = 1;
+    DebugOut dbg{sorted_who, subset_size, updset_size, sub_count, upd_count};
+    rc = enqueue_plain(c, &r1, Mode::Debug, nullptr, 0, &dbg);
+    if (rc) return rc;
+    return finish(c, nullptr);
+}
+
+}  // extern "C"

@@ -1,0 +1,54 @@
+// a6 pair emission and a7 filter on dimensions 1..d-1: interfaces.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "sweep.cuh"
+
+namespace ddm {
+
+// Coordinates of all dimensions (device pointers), passed by value to kernels.
+struct DimPtrs {
+    const float* sub_lo[DDM_MAX_DIMS];
+    const float* sub_hi[DDM_MAX_DIMS];
+    const float* upd_lo[DDM_MAX_DIMS];
+    const float* upd_hi[DDM_MAX_DIMS];
+};
+
+struct EmitArgs {
+    int d;
+    int64_t n, m;
+    DimPtrs dims;
+    Records rec;
+    uint32_t* cnt;                  // per-subscription match counts
+    const unsigned long long* off;  // n + 1 segment offsets
+    uint32_t* cnt_a;                // d > 1: class (a) survivors per subscription
+    uint32_t* cursor_b;             // per-subscription class (b) write cursor (zeroed)
+    uint2* subK;                    // (d-1) x n keys of dims 1.., in sub_order layout
+    uint2* updK;                    // (d-1) x m keys of dims 1.., in upd_order layout
+    int32_t* pairs;                 // 2 * cap ints
+    unsigned long long cap;
+    uint32_t* big_list;             // subscriptions whose segment needs the block sort
+    uint32_t* big_count;            // [0] = list length, [1] = work counter (zeroed)
+    int id_bits;                    // bits of the largest update id (radix passes)
+    // Batched mode: ids are written local to their instance (see batch code).
+    const int64_t* inst_sub_base;   // NULL in plain mode
+    const int64_t* inst_upd_base;
+    int num_inst;
+};
+
+// d > 1: permute keys of dims 1..d-1 into sub_order / upd_order layout and
+// validate those dimensions (no NaN, lo <= hi).
+int launch_permute_keys(const EmitArgs& a, DevStatus* st, cudaStream_t s);
+
+// d > 1 count pass: cnt[i] = survivors of the filter among S_i's dim-0 matches.
+int launch_filter_count(const EmitArgs& a, DevStatus* st, cudaStream_t s);
+
+// Write pass: every match of S_i lands in out[off_i .. off_i + cnt_i), in any
+// order, followed by the per-segment sort by update id.
+int launch_emit_ranges(const EmitArgs& a, DevStatus* st, cudaStream_t s);
+int launch_segment_sort(const EmitArgs& a, DevStatus* st, cudaStream_t s);
+
+}  // namespace ddm

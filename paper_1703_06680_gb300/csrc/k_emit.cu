@@ -1,0 +1,364 @@
+// a6: pair emission by symmetric range expansion, then a per-segment sort.
+// a7: filter of dimensions 1..d-1 (count mode and write mode).
+//
+// Paper: Algorithm 4 reports, at each upper endpoint, the extent against the
+// opposite active set; Section 3 extends d = 1 matching to d dimensions by
+// testing the other projections (Algorithm 1 per dimension, logical "and").
+//
+// Decomposition used here.  With lowers before uppers at equal coordinates,
+// S_i and U_j intersect along dimension 0 iff exactly one of
+//   (a) pos(S_i.lo) < pos(U_j.lo) < pos(S_i.hi)   -- U_j starts inside S_i
+//   (b) pos(U_j.lo) < pos(S_i.lo) < pos(U_j.hi)   -- S_i starts inside U_j
+// holds.  The class-(a) partners of S_i are the updates of lower-endpoint
+// rank A_i .. B_i-1 (a contiguous run of upd_order), and the class-(b)
+// partners of U_j are the subscriptions of lower-endpoint rank A_j .. B_j-1
+// (a contiguous run of sub_order).  Both sides therefore expand contiguous
+// ranges, and the total work is the output size (plus the filtered-out
+// candidates when d > 1).  Class (a) pairs go to the front of S_i's output
+// segment in range order, class (b) pairs behind them through an atomic
+// cursor; a per-segment sort by update id then fixes the order, so the result
+// is deterministic.
+#include "emit.cuh"
+
+namespace ddm {
+
+constexpr int EMIT_BLOCK = 256;
+constexpr int WARP_SORT_MAX = 512;
+constexpr int BIG_BLOCK = 256;
+constexpr int BIG_ITEMS = 4;
+
+__device__ __forceinline__ int find_inst(const int64_t* base, int num, int64_t id) {
+    int lo = 0, hi = num;  // base[0] = 0 <= id < base[num]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (base[mid] <= id) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------------------
+// a7 set-up: keys of dims 1..d-1 in rank order, with validation.
+// ---------------------------------------------------------------------------
+__global__ void k_permute_keys(EmitArgs a, DevStatus* st) {
+    bool bad = false;
+    const int64_t total = a.n + a.m;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < total;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const bool upd = r >= a.n;
+        const int64_t rank = upd ? r - a.n : r;
+        const uint32_t id = upd ? a.rec.upd_order[rank] : a.rec.sub_order[rank];
+        for (int k = 1; k < a.d; ++k) {
+            const float lo = upd ? a.dims.upd_lo[k][id] : a.dims.sub_lo[k][id];
+            const float hi = upd ? a.dims.upd_hi[k][id] : a.dims.sub_hi[k][id];
+            bad |= is_nan_bits(lo) || is_nan_bits(hi) || !(lo <= hi);
+            const uint2 kk = make_uint2(float_key(lo), float_key(hi));
+            if (upd) a.updK[(int64_t)(k - 1) * a.m + rank] = kk;
+            else a.subK[(int64_t)(k - 1) * a.n + rank] = kk;
+        }
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) raise_error(st, DDM_ERR_INVALID, 7);
+}
+
+// Keys of one extent in dims 1..d-1, held in registers.
+struct OwnKeys {
+    uint32_t lo[DDM_MAX_DIMS - 1], hi[DDM_MAX_DIMS - 1];
+};
+
+__device__ __forceinline__ OwnKeys own_keys(const EmitArgs& a, bool upd, int64_t id) {
+    OwnKeys o;
+#pragma unroll
+    for (int k = 1; k < DDM_MAX_DIMS; ++k) {
+        if (k < a.d) {
+            o.lo[k - 1] = float_key(upd ? a.dims.upd_lo[k][id] : a.dims.sub_lo[k][id]);
+            o.hi[k - 1] = float_key(upd ? a.dims.upd_hi[k][id] : a.dims.sub_hi[k][id]);
+        }
+    }
+    return o;
+}
+
+// Algorithm 1 on integer keys for dims 1..d-1; `other` is in rank layout.
+__device__ __forceinline__ bool pass_filter(const EmitArgs& a, const OwnKeys& o,
+                                            const uint2* other, int64_t stride, int64_t rank) {
+    bool ok = true;
+#pragma unroll
+    for (int k = 1; k < DDM_MAX_DIMS; ++k) {
+        if (k < a.d) {
+            const uint2 u = other[(int64_t)(k - 1) * stride + rank];
+            ok &= (o.lo[k - 1] <= u.y) && (u.x <= o.hi[k - 1]);
+        }
+    }
+    return ok;
+}
+
+__device__ __forceinline__ void put_pair(const EmitArgs& a, unsigned long long pos, int32_t i,
+                                         int32_t j, DevStatus* st) {
+    if (pos >= a.cap) {
+        raise_error(st, DDM_ERR_INTERNAL, 6);
+        return;
+    }
+    reinterpret_cast<int2*>(a.pairs)[pos] = make_int2(i, j);
+}
+
+// ---------------------------------------------------------------------------
+// Class (a): one warp per subscription, UloOrder[A_i .. B_i).
+// WRITE = false: count survivors (d > 1 only).
+// ---------------------------------------------------------------------------
+template <bool WRITE, bool FILTER>
+__global__ void __launch_bounds__(EMIT_BLOCK) k_class_a(EmitArgs a, DevStatus* st) {
+    if (read_error(st)) return;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t warps = (int64_t)gridDim.x * (EMIT_BLOCK / 32);
+    for (int64_t i = ((int64_t)blockIdx.x * EMIT_BLOCK + threadIdx.x) >> 5; i < a.n; i += warps) {
+        const uint32_t A = a.rec.s_A[i], B = a.rec.s_B[i];
+        if (A > B || B > (uint64_t)a.m) {  // guard against an upstream fault
+            if (lane == 0) raise_error(st, DDM_ERR_INTERNAL, 8);
+            continue;
+        }
+        OwnKeys o;
+        if (FILTER) o = own_keys(a, false, i);
+        unsigned long long base = WRITE ? a.off[i] : 0ull;
+        int32_t out_i = (int32_t)i, sub_off_j = 0;
+        if (WRITE && a.inst_sub_base) {
+            const int b = find_inst(a.inst_sub_base, a.num_inst, i);
+            out_i = (int32_t)(i - a.inst_sub_base[b]);
+            sub_off_j = (int32_t)a.inst_upd_base[b];
+        }
+        uint32_t running = 0;
+        for (uint32_t k0 = A; k0 < B; k0 += 32) {
+            const uint32_t k = k0 + lane;
+            bool pass = k < B;
+            if (FILTER && pass) pass = pass_filter(a, o, a.updK, a.m, k);
+            const unsigned bal = __ballot_sync(0xffffffffu, pass);
+            if (WRITE && pass) {
+                const int32_t j = (int32_t)a.rec.upd_order[k] - sub_off_j;
+                put_pair(a, base + running + __popc(bal & lt), out_i, j, st);
+            }
+            running += __popc(bal);
+        }
+        if (!WRITE && lane == 0) {
+            a.cnt_a[i] = running;
+            a.cnt[i] = running;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Class (b): one warp per update, SloOrder[A_j .. B_j).
+// ---------------------------------------------------------------------------
+template <bool WRITE, bool FILTER>
+__global__ void __launch_bounds__(EMIT_BLOCK) k_class_b(EmitArgs a, DevStatus* st) {
+    if (read_error(st)) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (EMIT_BLOCK / 32);
+    for (int64_t j = ((int64_t)blockIdx.x * EMIT_BLOCK + threadIdx.x) >> 5; j < a.m; j += warps) {
+        const uint32_t A = a.rec.u_A[j], B = a.rec.u_B[j];
+        if (A > B || B > (uint64_t)a.n) {  // guard against an upstream fault
+            if (lane == 0) raise_error(st, DDM_ERR_INTERNAL, 9);
+            continue;
+        }
+        OwnKeys o;
+        if (FILTER) o = own_keys(a, true, j);
+        int32_t out_j = (int32_t)j;
+        int64_t sub_base = 0;
+        if (WRITE && a.inst_upd_base) {
+            const int b = find_inst(a.inst_upd_base, a.num_inst, j);
+            out_j = (int32_t)(j - a.inst_upd_base[b]);
+            sub_base = a.inst_sub_base[b];
+        }
+        for (uint32_t r = A + lane; r < B; r += 32) {
+            if (FILTER && !pass_filter(a, o, a.subK, a.n, r)) continue;
+            const uint32_t i = a.rec.sub_order[r];
+            if (!WRITE) {
+                atomicAdd(&a.cnt[i], 1u);
+            } else {
+                const uint32_t ca = FILTER ? a.cnt_a[i] : a.rec.s_B[i] - a.rec.s_A[i];
+                const uint32_t p = atomicAdd(&a.cursor_b[i], 1u);
+                put_pair(a, a.off[i] + ca + p, (int32_t)(i - sub_base), out_j, st);
+            }
+        }
+    }
+}
+
+static unsigned warp_grid(int64_t items) {
+    int64_t g = ceil_div((uint64_t)items, EMIT_BLOCK / 32);
+    return (unsigned)(g < 1 ? 1 : (g > 152 * 32 ? 152 * 32 : g));
+}
+
+int launch_permute_keys(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
+    const int64_t total = a.n + a.m;
+    if (a.d <= 1 || total == 0) return 0;
+    int64_t g = ceil_div((uint64_t)total, 256 * 4);
+    k_permute_keys<<<(unsigned)(g < 1 ? 1 : (g > 152 * 16 ? 152 * 16 : g)), 256, 0, s>>>(a, st);
+    return 1;
+}
+
+int launch_filter_count(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
+    int launches = 0;
+    if (a.n > 0) k_class_a<false, true><<<warp_grid(a.n), EMIT_BLOCK, 0, s>>>(a, st), ++launches;
+    if (a.m > 0) k_class_b<false, true><<<warp_grid(a.m), EMIT_BLOCK, 0, s>>>(a, st), ++launches;
+    return launches;
+}
+
+int launch_emit_ranges(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
+    int launches = 0;
+    if (a.d > 1) {
+        if (a.n > 0) k_class_a<true, true><<<warp_grid(a.n), EMIT_BLOCK, 0, s>>>(a, st), ++launches;
+        if (a.m > 0) k_class_b<true, true><<<warp_grid(a.m), EMIT_BLOCK, 0, s>>>(a, st), ++launches;
+    } else {
+        if (a.n > 0) k_class_a<true, false><<<warp_grid(a.n), EMIT_BLOCK, 0, s>>>(a, st), ++launches;
+        if (a.m > 0) k_class_b<true, false><<<warp_grid(a.m), EMIT_BLOCK, 0, s>>>(a, st), ++launches;
+    }
+    return launches;
+}
+
+// ---------------------------------------------------------------------------
+// Per-segment sort by update id.  Segments of up to WARP_SORT_MAX pairs are
+// sorted by one warp (bitonic network in shared memory); longer ones are
+// queued for k_segsort_big.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(EMIT_BLOCK) k_segsort_warp(EmitArgs a, DevStatus* st) {
+    __shared__ uint32_t buf_all[EMIT_BLOCK / 32][WARP_SORT_MAX];
+    if (read_error(st)) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t* buf = buf_all[warp];
+    const int64_t warps = (int64_t)gridDim.x * (EMIT_BLOCK / 32);
+    for (int64_t i = ((int64_t)blockIdx.x * EMIT_BLOCK + threadIdx.x) >> 5; i < a.n; i += warps) {
+        const uint32_t c = a.cnt[i];
+        if (c < 2) continue;
+        if (c > WARP_SORT_MAX) {
+            if (lane == 0) a.big_list[atomicAdd(&a.big_count[0], 1u)] = (uint32_t)i;
+            continue;
+        }
+        int32_t* seg = a.pairs + 2 * a.off[i];
+        uint32_t P = 2;
+        while (P < c) P <<= 1;
+        for (uint32_t k = lane; k < P; k += 32) buf[k] = k < c ? (uint32_t)seg[2 * k + 1] : 0xFFFFFFFFu;
+        __syncwarp();
+        for (uint32_t size = 2; size <= P; size <<= 1) {
+            for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+                for (uint32_t t = lane; t < P / 2; t += 32) {
+                    const uint32_t lo = 2 * stride * (t / stride) + (t % stride);
+                    const uint32_t hi = lo + stride;
+                    const bool up = (lo & size) == 0;
+                    const uint32_t x = buf[lo], y = buf[hi];
+                    if ((x > y) == up) { buf[lo] = y; buf[hi] = x; }
+                }
+                __syncwarp();
+            }
+        }
+        for (uint32_t k = lane; k < c; k += 32) seg[2 * k + 1] = (int32_t)buf[k];
+        __syncwarp();
+    }
+}
+
+// One block per long segment: LSD radix sort of the update-id column, 8 bits
+// per pass, using the segment's own subscription-id column as the ping-pong
+// buffer; the subscription ids are rewritten at the end.  Stable ranking as in
+// the onesweep pass (match_any within a warp, warp-ordered chunks).
+__global__ void __launch_bounds__(BIG_BLOCK) k_segsort_big(EmitArgs a, DevStatus* st) {
+    constexpr int WARPS = BIG_BLOCK / 32;
+    constexpr int CHUNK = BIG_BLOCK * BIG_ITEMS;
+    __shared__ uint32_t hist[256];
+    __shared__ uint32_t bucket[256];
+    __shared__ uint32_t whist[WARPS][256];
+    __shared__ uint32_t seg_id;
+    if (read_error(st)) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int passes = (a.id_bits + 7) / 8;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) {
+            uint32_t t = atomicAdd(&a.big_count[1], 1u);
+            seg_id = t < a.big_count[0] ? a.big_list[t] : 0xFFFFFFFFu;
+        }
+        __syncthreads();
+        if (seg_id == 0xFFFFFFFFu) return;
+        const uint32_t i = seg_id;
+        const uint32_t c = a.cnt[i];
+        int32_t* seg = a.pairs + 2 * a.off[i];
+        for (int p = 0; p < passes; ++p) {
+            const int src = (p & 1) ? 0 : 1, dst = 1 - src;  // column offsets
+            const int shift = 8 * p;
+            hist[tid] = 0;
+            __syncthreads();
+            for (uint32_t k = tid; k < c; k += BIG_BLOCK)
+                atomicAdd(&hist[((uint32_t)seg[2 * k + src] >> shift) & 0xFF], 1u);
+            __syncthreads();
+            if (warp == 0) {
+                uint32_t run = 0;
+                for (int b0 = 0; b0 < 256; b0 += 32) {
+                    uint32_t v = hist[b0 + lane], x = v;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                        if (lane >= o) x += y;
+                    }
+                    bucket[b0 + lane] = run + x - v;
+                    run += __shfl_sync(0xffffffffu, x, 31);
+                }
+            }
+            __syncthreads();
+            for (uint32_t c0 = 0; c0 < c; c0 += CHUNK) {
+                for (int t = tid; t < WARPS * 256; t += BIG_BLOCK) (&whist[0][0])[t] = 0;
+                __syncthreads();
+                uint32_t val[BIG_ITEMS], dg[BIG_ITEMS], rk[BIG_ITEMS];
+                const uint32_t wb = c0 + warp * 32 * BIG_ITEMS;
+#pragma unroll
+                for (int it = 0; it < BIG_ITEMS; ++it) {
+                    const uint32_t k = wb + it * 32 + lane;
+                    val[it] = k < c ? (uint32_t)seg[2 * k + src] : 0xFFFFFFFFu;
+                    dg[it] = (val[it] >> shift) & 0xFF;
+                    const unsigned peers = __match_any_sync(0xffffffffu, dg[it]);
+                    const uint32_t cc = whist[warp][dg[it]];
+                    __syncwarp();
+                    if (lane == __ffs(peers) - 1) whist[warp][dg[it]] = cc + __popc(peers);
+                    __syncwarp();
+                    rk[it] = cc + __popc(peers & lt);
+                }
+                __syncthreads();
+                {   // per digit: exclusive prefix over warps, chunk total
+                    uint32_t run = 0;
+#pragma unroll
+                    for (int w = 0; w < WARPS; ++w) {
+                        uint32_t x = whist[w][tid];
+                        whist[w][tid] = run;
+                        run += x;
+                    }
+                    hist[tid] = run;  // chunk count of digit tid (tail items sit in digit 255 last)
+                }
+                __syncthreads();
+#pragma unroll
+                for (int it = 0; it < BIG_ITEMS; ++it) {
+                    const uint32_t k = wb + it * 32 + lane;
+                    if (k < c) {
+                        const uint32_t pos = bucket[dg[it]] + whist[warp][dg[it]] + rk[it];
+                        seg[2 * pos + dst] = (int32_t)val[it];
+                    }
+                }
+                __syncthreads();
+                bucket[tid] += hist[tid];
+                __syncthreads();
+            }
+            __syncthreads();
+        }
+        // Result is in column (passes odd ? 0 : 1); move it to column 1 and
+        // restore the subscription ids in column 0.
+        int32_t out_i = (int32_t)i;
+        if (a.inst_sub_base) out_i = (int32_t)(i - a.inst_sub_base[find_inst(a.inst_sub_base, a.num_inst, i)]);
+        for (uint32_t k = tid; k < c; k += BIG_BLOCK) {
+            if (passes & 1) seg[2 * k + 1] = seg[2 * k];
+            seg[2 * k] = out_i;
+        }
+    }
+}
+
+int launch_segment_sort(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
+    if (a.n == 0) return 0;
+    k_segsort_warp<<<warp_grid(a.n), EMIT_BLOCK, 0, s>>>(a, st);
+    k_segsort_big<<<152 * 2, BIG_BLOCK, 0, s>>>(a, st);
+    return 2;
+}
+
+}  // namespace ddm

@@ -1,0 +1,252 @@
+// a3: sweep scan over the sorted endpoint stream.
+// a4: exact per-extent match counts by rank arithmetic.
+// a5: exclusive scan of the counts into output offsets.
+//
+// Paper: Algorithm 4 sweeps the sorted endpoints keeping the active sets
+// SubSet and UpdSet (an extent is active between its lower and upper
+// endpoint, Section 3 "Sort-Based Matching"); Section 4 computes the state at
+// segment boundaries with a prefix computation (inclusive / exclusive scans,
+// "Prefix computations") and Algorithm 6.  Here the sweep keeps only the
+// SIZES of the active sets, as four running counts (S lowers, U lowers,
+// S uppers, U uppers seen so far), computed for every position at once by a
+// single-pass scan with decoupled look-back -- the GPU form of the paper's
+// master combine of per-segment Sadd/Sdel/Uadd/Udel.
+//
+// Counting (a4).  With lowers before uppers at equal coordinates, S_i and U_j
+// intersect iff pos(U_j.lo) < pos(S_i.hi) and pos(S_i.lo) < pos(U_j.hi).
+// The updates with pos(lo) < pos(S_i.hi) number B_i = cUlo(pos S_i.hi); those
+// among them that fail the second condition are exactly the updates whose
+// upper endpoint precedes S_i's lower one, C_i = cUhi(pos S_i.lo) (an update
+// whose upper precedes S_i.lo also has its lower before S_i.hi).  Hence
+// |{j : S_i and U_j intersect}| = B_i - C_i, and symmetrically for updates.
+#include "sweep.cuh"
+
+namespace ddm {
+
+// Packed per-thread counts: S lower [0,21), U lower [21,42), S upper [42,63).
+__device__ __forceinline__ unsigned long long kind_inc(uint32_t kind) {
+    return kind == KIND_SLO ? 1ull : kind == KIND_ULO ? (1ull << 21)
+                                   : kind == KIND_SHI ? (1ull << 42) : 0ull;
+}
+
+__global__ void __launch_bounds__(SCAN_BLOCK)
+k_sweep_scan(const uint32_t* __restrict__ vals, uint32_t E, uint32_t n, uint32_t m,
+             Records rec, unsigned long long* __restrict__ status,
+             uint32_t* __restrict__ tile_counter, DevStatus* st) {
+    __shared__ unsigned long long warp_sum[SCAN_BLOCK / 32];
+    __shared__ unsigned long long tile_prefix[3];
+    __shared__ uint32_t tile_id_s;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) tile_id_s = atomicAdd(tile_counter, 1u);
+    __syncthreads();
+    const uint32_t tile = tile_id_s;
+    const uint64_t base = (uint64_t)tile * SCAN_TILE + (uint64_t)tid * SCAN_ITEMS;
+
+    uint32_t v[SCAN_ITEMS];
+    if (base + SCAN_ITEMS <= E) {
+        const uint4* p4 = reinterpret_cast<const uint4*>(vals + base);
+        uint4 a = p4[0], b = p4[1];
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < SCAN_ITEMS; ++k) v[k] = base + k < E ? vals[base + k] : 0xFFFFFFFFu;
+    }
+    unsigned long long mine = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k)
+        if (base + k < E) mine += kind_inc(v[k] >> 30);
+
+    // Block-wide exclusive scan of the packed counts.
+    unsigned long long x = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sum[warp] = x;
+    __syncthreads();
+    unsigned long long wexcl = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < SCAN_BLOCK / 32; ++w) {
+        unsigned long long t = warp_sum[w];
+        if (w < warp) wexcl += t;
+        total += t;
+    }
+    unsigned long long excl = wexcl + x - mine;
+
+    // Publish the tile aggregate, one look-back word per counter, then look back.
+    if (warp < 3) {
+        const unsigned long long agg = (total >> (21 * warp)) & ((1ull << 21) - 1);
+        const uint64_t stride = gridDim.x + 1ull;
+        unsigned long long* word = status + (uint64_t)warp * stride + tile;
+        if (lane == 0) st_release_u64(word, (tile == 0 ? LB64_INC : LB64_AGG) | agg);
+        unsigned long long pre = tile == 0 ? 0ull
+                                           : warp_lookback_u64(status + (uint64_t)warp * stride,
+                                                               tile, st, 3);
+        if (lane == 0) {
+            if (tile != 0) st_release_u64(word, LB64_INC | (pre + agg));
+            tile_prefix[warp] = pre;
+        }
+    }
+    __syncthreads();
+
+    // Walk this thread's items with exact exclusive counts.
+    uint32_t cSlo = (uint32_t)(tile_prefix[0] + (excl & ((1ull << 21) - 1)));
+    uint32_t cUlo = (uint32_t)(tile_prefix[1] + ((excl >> 21) & ((1ull << 21) - 1)));
+    uint32_t cShi = (uint32_t)(tile_prefix[2] + ((excl >> 42) & ((1ull << 21) - 1)));
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        const uint64_t p64 = base + k;
+        if (p64 >= E) break;
+        const uint32_t p = (uint32_t)p64;
+        const uint32_t kind = v[k] >> 30, id = v[k] & ID_MASK;
+        const uint32_t cUhi = p - cSlo - cUlo - cShi;
+        // Guard: a payload or rank out of range means an upstream fault; skip it.
+        if (id >= ((kind & 1u) ? m : n) || cSlo > n || cUlo > m) {
+            raise_error(st, DDM_ERR_INTERNAL, 3);
+            continue;
+        }
+        if (rec.windows && (p & ((1u << rec.win_shift) - 1)) == 0)
+            rec.windows[p >> rec.win_shift] = make_uint4(cSlo, cUlo, cUhi, p);
+        switch (kind) {
+            case KIND_SLO:
+                rec.s_pos_lo[id] = p; rec.s_A[id] = cUlo; rec.s_C[id] = cUhi;
+                if (cSlo < n) rec.sub_order[cSlo] = id;
+                ++cSlo;
+                break;
+            case KIND_ULO:
+                rec.u_pos_lo[id] = p; rec.u_A[id] = cSlo; rec.u_C[id] = cShi;
+                if (cUlo < m) rec.upd_order[cUlo] = id;
+                ++cUlo;
+                break;
+            case KIND_SHI:
+                rec.s_pos_hi[id] = p; rec.s_B[id] = cUlo;
+                ++cShi;
+                break;
+            default:
+                rec.u_pos_hi[id] = p; rec.u_B[id] = cSlo;
+                break;
+        }
+        if (rec.dbg_who) {
+            const uint32_t cUhi_after = p + 1 - cSlo - cUlo - cShi;
+            rec.dbg_who[p] = v[k];
+            rec.dbg_subset[p] = cSlo - cShi;
+            rec.dbg_updset[p] = cUlo - cUhi_after;
+        }
+    }
+}
+
+int launch_sweep_scan(const uint32_t* vals, uint64_t E, int64_t n, int64_t m, const Records& rec,
+                       unsigned long long* status, DevStatus* st, cudaStream_t s) {
+    if (E == 0) return 0;
+    const uint64_t tiles = ceil_div(E, SCAN_TILE);
+    // layout: 3 counters x (tiles + 1) words; the last word of counter 0's row
+    // region doubles as the tile counter.
+    uint32_t* counter = reinterpret_cast<uint32_t*>(status + 3 * (tiles + 1));
+    k_sweep_scan<<<(unsigned)tiles, SCAN_BLOCK, 0, s>>>(vals, (uint32_t)E, (uint32_t)n,
+                                                        (uint32_t)m, rec, status, counter, st);
+    return 1;
+}
+
+// ---------------------------------------------------------------------------
+// a4
+// ---------------------------------------------------------------------------
+__global__ void k_rank_count(const uint32_t* __restrict__ B, const uint32_t* __restrict__ C,
+                             int64_t count, uint32_t* __restrict__ cnt, DevStatus* st) {
+    if (read_error(st)) return;
+    bool bad = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t b = B[i], c = C[i];
+        bad |= b < c;
+        cnt[i] = b - c;
+    }
+    if (bad) raise_error(st, DDM_ERR_INTERNAL, 4);
+}
+
+int launch_rank_count(const Records& rec, int64_t n, int64_t m, uint32_t* cnt,
+                       uint32_t* upd_cnt, DevStatus* st, cudaStream_t s) {
+    auto grid = [](int64_t c) {
+        int64_t g = ceil_div((uint64_t)c, 256ull * 4);
+        return (unsigned)(g < 1 ? 1 : (g > 152 * 16 ? 152 * 16 : g));
+    };
+    int launches = 0;
+    if (n > 0) k_rank_count<<<grid(n), 256, 0, s>>>(rec.s_B, rec.s_C, n, cnt, st), ++launches;
+    if (upd_cnt && m > 0)
+        k_rank_count<<<grid(m), 256, 0, s>>>(rec.u_B, rec.u_C, m, upd_cnt, st), ++launches;
+    return launches;
+}
+
+// ---------------------------------------------------------------------------
+// a5
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(OFF_BLOCK)
+k_offsets(const uint32_t* __restrict__ cnt, uint32_t n, unsigned long long* __restrict__ off,
+          unsigned long long cap, unsigned long long* __restrict__ status,
+          uint32_t* __restrict__ tile_counter, DevStatus* st) {
+    __shared__ unsigned long long warp_sum[OFF_BLOCK / 32];
+    __shared__ unsigned long long tile_prefix;
+    __shared__ uint32_t tile_id_s;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) tile_id_s = atomicAdd(tile_counter, 1u);
+    __syncthreads();
+    const uint32_t tile = tile_id_s;
+    const uint64_t base = (uint64_t)tile * OFF_TILE + (uint64_t)tid * OFF_ITEMS;
+    uint32_t c[OFF_ITEMS];
+    unsigned long long mine = 0;
+#pragma unroll
+    for (int k = 0; k < OFF_ITEMS; ++k) {
+        c[k] = base + k < n ? cnt[base + k] : 0u;
+        mine += c[k];
+    }
+    unsigned long long x = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sum[warp] = x;
+    __syncthreads();
+    unsigned long long wexcl = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < OFF_BLOCK / 32; ++w) {
+        unsigned long long t = warp_sum[w];
+        if (w < warp) wexcl += t;
+        total += t;
+    }
+    if (warp == 0) {
+        unsigned long long* word = status + tile;
+        if (lane == 0) st_release_u64(word, (tile == 0 ? LB64_INC : LB64_AGG) | total);
+        unsigned long long pre = tile == 0 ? 0ull : warp_lookback_u64(status, tile, st, 5);
+        if (lane == 0) {
+            if (tile != 0) st_release_u64(word, LB64_INC | (pre + total));
+            tile_prefix = pre;
+        }
+    }
+    __syncthreads();
+    unsigned long long run = tile_prefix + wexcl + x - mine;
+#pragma unroll
+    for (int k = 0; k < OFF_ITEMS; ++k) {
+        if (base + k < n) off[base + k] = run;
+        run += c[k];
+    }
+    // The thread holding the last element also writes off[n] and K.
+    if (base < n && base + OFF_ITEMS >= n) {
+        off[n] = run;
+        st->K = run;
+        if (run > cap) raise_error(st, DDM_ERR_CAPACITY, 5);
+    }
+}
+
+int launch_offsets(const uint32_t* cnt, int64_t n, unsigned long long* off, uint64_t cap,
+                    unsigned long long* status, DevStatus* st, cudaStream_t s) {
+    if (n == 0) return 0;
+    const uint64_t tiles = ceil_div((uint64_t)n, OFF_TILE);
+    uint32_t* counter = reinterpret_cast<uint32_t*>(status + tiles);
+    k_offsets<<<(unsigned)tiles, OFF_BLOCK, 0, s>>>(cnt, (uint32_t)n, off, cap, status, counter,
+                                                    st);
+    return 1;
+}
+
+}  // namespace ddm

@@ -1,0 +1,188 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Results are integer pair lists, so the bar is bit-exact equality of the
+sorted (sub, upd) lists.  Full-size workloads are compared in full where the
+oracle finishes in seconds, and on sampled subscriptions (oracle brute force
+row by row) plus exact properties where it does not.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.gpu_util import gpu_pairs, oracle_row, segment_of, to_dev
+from tests.helpers import special_value_instance, tiny_grid_instance
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_1703_06680_gb300 as ddm
+    ddm.build_library()
+    c = ddm.Context(0)
+    yield c
+    c.close()
+
+
+def assert_parity(ctx, reg, want=None):
+    if want is None:
+        want = oracle.sbm(reg)
+    got = gpu_pairs(ctx, reg)
+    assert got.shape == want.shape, (got.shape, want.shape)
+    assert np.array_equal(got, want)
+    assert ctx.count(*to_dev(reg)) == len(want)
+
+
+# --- the workloads --------------------------------------------------------------
+
+def test_small_1d(ctx):
+    assert_parity(ctx, synth.small_1d())
+
+
+@pytest.mark.parametrize("alpha", [0.01, 1.0, 100.0])
+def test_large_1d_full(ctx, alpha):
+    assert_parity(ctx, synth.large_1d(alpha))
+
+
+@pytest.mark.parametrize("d,alpha", [(2, 1.0), (2, 100.0), (3, 1.0), (3, 100.0)])
+def test_nd_reduced_full(ctx, d, alpha):
+    # N = 1e5: the oracle finishes in seconds; many tiles and ragged tails
+    assert_parity(ctx, synth.large_nd(d, alpha, N=100_003))
+
+
+def test_d2_alpha1_full_size(ctx):
+    assert_parity(ctx, synth.large_nd(2, 1.0))
+
+
+@pytest.mark.parametrize("d,alpha", [(2, 100.0), (3, 1.0), (3, 100.0)])
+def test_nd_full_size_sampled(ctx, d, alpha):
+    import torch
+    reg = synth.large_nd(d, alpha)
+    t = to_dev(reg)
+    K = ctx.count(*t)
+    pairs = ctx.match(*t, cap=K)
+    assert pairs.shape[0] == K
+    # lexicographically sorted, no duplicates
+    key = pairs[:, 0].long() * (1 << 32) + pairs[:, 1].long()
+    assert bool((key[1:] > key[:-1]).all())
+    # swapping the roles of S and U gives the same count
+    assert ctx.count(t[2], t[3], t[0], t[1]) == K
+    # per-subscription rows against the oracle's brute force
+    rng = np.random.default_rng(d * 1000 + int(alpha))
+    for i in rng.choice(reg.n, size=48, replace=False).tolist():
+        assert np.array_equal(segment_of(pairs, i), oracle_row(reg, i)), i
+    del pairs
+    torch.cuda.empty_cache()
+
+
+# --- the sweep stages (a1-a4) against the oracle's Algorithm 4 trace --------------
+
+def test_sweep_stages_match_oracle_trace(ctx):
+    reg = synth.make_regions(1, 30_011, 29_989, 40.0, 99)  # dense float32 ties near 1e6
+    who, ss, us, sc, uc = [x.cpu().numpy().astype(np.int64) for x in ctx.debug_sweep(*to_dev(reg))]
+    kind, ids, oss, ous = oracle.sweep_trace(reg)
+    assert np.array_equal(who >> 30, kind.astype(np.int64))
+    assert np.array_equal(who & ((1 << 30) - 1), ids.astype(np.int64))
+    assert np.array_equal(ss, oss) and np.array_equal(us, ous)
+    pairs = oracle.sbm(reg)
+    assert np.array_equal(sc, oracle.per_sub_counts(pairs, reg.n))
+    assert np.array_equal(uc, oracle.per_upd_counts(pairs, reg.m))
+
+
+# --- adversarial and edge cases ------------------------------------------------------
+
+def test_tiny_grid_instances(ctx):
+    rng = np.random.default_rng(11)
+    for s in range(300):
+        d = 1 + s % 3
+        reg = tiny_grid_instance(rng, d, int(rng.integers(0, 70)), int(rng.integers(0, 70)))
+        assert_parity(ctx, reg)
+
+
+def test_special_values(ctx):
+    rng = np.random.default_rng(12)
+    for s in range(100):
+        reg = special_value_instance(rng, 1 + s % 3, int(rng.integers(1, 300)),
+                                     int(rng.integers(1, 300)))
+        assert_parity(ctx, reg)
+
+
+@pytest.mark.parametrize("n,m", [(0, 10), (10, 0), (0, 0), (1, 1), (4097, 1), (1, 4097),
+                                 (2049, 2047)])
+def test_empty_and_ragged(ctx, n, m):
+    reg = synth.make_regions(1, n, m, 5000.0, 5 + n + m) if n + m else \
+        synth.Regions(*(np.zeros((1, 0), np.float32) for _ in range(4)))
+    assert_parity(ctx, reg)
+
+
+def test_all_identical_long_segments(ctx):
+    # every pair matches: 3000 x 2500 pairs, segments far above one warp's sort
+    reg = synth.Regions(np.full((1, 3000), 1.0, np.float32), np.full((1, 3000), 2.0, np.float32),
+                        np.full((1, 2500), 2.0, np.float32), np.full((1, 2500), 3.0, np.float32))
+    assert_parity(ctx, reg)
+
+
+def test_one_huge_interval(ctx):
+    reg = synth.large_1d(1.0, N=200_000)
+    reg.sub_lo[0, 17] = -1.0
+    reg.sub_hi[0, 17] = 2.0e6
+    reg.upd_lo[0, 5] = -np.inf
+    reg.upd_hi[0, 5] = np.inf
+    assert_parity(ctx, reg)
+
+
+def test_mixed_lengths_2d(ctx):
+    rng = np.random.default_rng(13)
+    n, m = 20_000, 30_000
+    def ext(c):
+        lo = (rng.random((2, c)) * 1e5).astype(np.float32)
+        side = np.exp(rng.normal(4.0, 2.0, size=(2, c))).astype(np.float32)
+        return lo, (lo + side).astype(np.float32)
+    reg = synth.Regions(*ext(n), *ext(m))
+    assert_parity(ctx, reg)
+
+
+@pytest.mark.parametrize("where", ["nan_dim0", "reversed_dim0", "nan_dim1", "reversed_dim2"])
+def test_invalid_input(ctx, where):
+    import paper_1703_06680_gb300 as ddm
+    reg = synth.make_regions(3, 100, 100, 1e4, 3)
+    if where == "nan_dim0":
+        reg.upd_lo[0, 7] = np.nan
+    elif where == "reversed_dim0":
+        reg.sub_lo[0, 3] = reg.sub_hi[0, 3] + 1
+    elif where == "nan_dim1":
+        reg.sub_hi[1, 9] = np.nan
+    else:
+        reg.upd_lo[2, 0] = reg.upd_hi[2, 0] + 5
+    t = to_dev(reg)
+    with pytest.raises(ddm.DDMError) as e:
+        ctx.count(*t)
+    assert e.value.code == -1
+    with pytest.raises(ddm.DDMError):
+        ctx.match(*t, cap=10_000)
+    # the context stays usable
+    assert_parity(ctx, synth.make_regions(1, 50, 60, 1e4, 4))
+
+
+def test_capacity_error_reports_K(ctx):
+    import paper_1703_06680_gb300 as ddm
+    reg = synth.small_1d()
+    want = oracle.sbm(reg)
+    with pytest.raises(ddm.CapacityError) as e:
+        ctx.match(*to_dev(reg), cap=len(want) - 1)
+    assert e.value.K == len(want)
+
+
+def test_host_buffers_match_device(ctx):
+    reg = synth.large_1d(1.0, N=300_000)
+    want = oracle.sbm(reg)
+    got = ctx.match_host(reg.sub_lo, reg.sub_hi, reg.upd_lo, reg.upd_hi, cap=len(want) + 5)
+    assert np.array_equal(got, want)
+
+
+def test_deterministic(ctx):
+    reg = synth.large_nd(2, 100.0, N=60_000)
+    a = gpu_pairs(ctx, reg)
+    b = gpu_pairs(ctx, reg)
+    assert np.array_equal(a, b)
