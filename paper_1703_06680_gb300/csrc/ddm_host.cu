@@ -143,7 +143,22 @@ struct Plan {
     unsigned long long* off_status;
     uint32_t* cursor_b;
     uint32_t* big_count;
+    // window path (d = 1, match)
+    bool window;
+    int win_shift;
+    uint32_t num_win;
+    uint32_t* lw_fill;
+    uint32_t* num_flagged;
+    unsigned long long* lw_total;
+    unsigned long long* win_status;
     size_t zero_bytes;
+    uint4* windows;
+    uint32_t* lw_size;
+    unsigned long long* lw_off;
+    uint2* lw;
+    uint4* urank;
+    unsigned long long lw_cap;
+    uint8_t* flag;
     // the rest
     uint32_t *keys0, *keys1, *vals0, *vals1;
     Records rec;
@@ -162,15 +177,29 @@ struct Plan {
         off_status = cv.take<unsigned long long>(ceil_div(n, OFF_TILE) + 2);
         cursor_b = cv.take<uint32_t>(mode == Mode::Match ? n : 0);
         big_count = cv.take<uint32_t>(2);
+        window = mode == Mode::Match && d == 1;
+        win_shift = 8;
+        num_win = window ? (uint32_t)ceil_div(E, 1ull << win_shift) : 0;
+        lw_fill = cv.take<uint32_t>(num_win);
+        num_flagged = cv.take<uint32_t>(1);
+        lw_total = cv.take<unsigned long long>(1);
+        win_status = cv.take<unsigned long long>(window ? ceil_div(num_win, OFF_TILE) + 2 : 0);
         zero_bytes = (cv.off + 255) & ~(size_t)255;
+        windows = cv.take<uint4>(window ? num_win + 1 : 0);
+        lw_size = cv.take<uint32_t>(num_win);
+        lw_off = cv.take<unsigned long long>(window ? num_win + 1 : 0);
+        lw_cap = window ? (unsigned long long)E + 4096 : 0;
+        lw = cv.take<uint2>(lw_cap);
+        urank = cv.take<uint4>(window ? m : 0);
+        flag = cv.take<uint8_t>(window ? n : 0);
         keys0 = cv.take<uint32_t>(E);
         keys1 = cv.take<uint32_t>(E);
         vals0 = cv.take<uint32_t>(E);
         vals1 = cv.take<uint32_t>(E);
-        rec.s_pos_lo = cv.take<uint32_t>(n); rec.s_pos_hi = cv.take<uint32_t>(n);
-        rec.s_A = cv.take<uint32_t>(n); rec.s_B = cv.take<uint32_t>(n); rec.s_C = cv.take<uint32_t>(n);
-        rec.u_pos_lo = cv.take<uint32_t>(m); rec.u_pos_hi = cv.take<uint32_t>(m);
-        rec.u_A = cv.take<uint32_t>(m); rec.u_B = cv.take<uint32_t>(m); rec.u_C = cv.take<uint32_t>(m);
+        rec.s_lo = cv.take<uint4>(n);
+        rec.s_hi = cv.take<uint2>(n);
+        rec.u_lo = cv.take<uint4>(m);
+        rec.u_hi = cv.take<uint2>(m);
         rec.sub_order = cv.take<uint32_t>(n);
         rec.upd_order = cv.take<uint32_t>(m);
         rec.windows = nullptr;
@@ -219,6 +248,10 @@ int enqueue_plain(ddm_ctx* c, const ddm_regions* r, Mode mode, int32_t* pairs, u
                                      pl.sort_lb, true, c->dstat, s);
     mark(c, 2);
     Records rec = pl.rec;
+    if (pl.window) {
+        rec.windows = pl.windows;
+        rec.win_shift = pl.win_shift;
+    }
     if (dbg) {
         rec.dbg_who = dbg->who;
         rec.dbg_subset = dbg->subset;
@@ -243,6 +276,21 @@ int enqueue_plain(ddm_ctx* c, const ddm_regions* r, Mode mode, int32_t* pairs, u
     a.id_bits = id_bits(pl.m);
     a.inst_sub_base = a.inst_upd_base = nullptr;
     a.num_inst = 0;
+    a.flag = nullptr;
+    a.num_flagged = pl.num_flagged;
+    if (pl.window) {
+        a.flag = pl.flag;
+        a.windows = pl.windows;
+        a.win_shift = pl.win_shift;
+        a.num_win = pl.num_win;
+        a.lw_size = pl.lw_size;
+        a.lw_off = pl.lw_off;
+        a.lw_fill = pl.lw_fill;
+        a.lw = pl.lw;
+        a.urank = pl.urank;
+        a.lw_cap = pl.lw_cap;
+    }
+    a.vals = pl.vals0;
 
     if (r->d == 1) {
         L += launch_rank_count(rec, pl.n, pl.m, pl.cnt, dbg ? dbg->upd_cnt : nullptr, c->dstat, s);
@@ -253,9 +301,16 @@ int enqueue_plain(ddm_ctx* c, const ddm_regions* r, Mode mode, int32_t* pairs, u
     mark(c, 4);
     if (dbg && dbg->sub_cnt && pl.n > 0)
         CK(cudaMemcpyAsync(dbg->sub_cnt, pl.cnt, pl.n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
-    L += launch_offsets(pl.cnt, pl.n, pl.off, mode == Mode::Match ? cap : ~0ull, pl.off_status,
-                        c->dstat, s);
+    L += launch_offsets(pl.cnt, pl.n, pl.off, mode == Mode::Match ? cap : ~0ull,
+                        &c->dstat->K, pl.off_status, c->dstat, s);
     mark(c, 5);
+    if (pl.window) {
+        L += launch_window_sizes(a, c->dstat, s);
+        L += launch_offsets(pl.lw_size, pl.num_win, pl.lw_off, ~0ull, pl.lw_total,
+                            pl.win_status, c->dstat, s);
+        L += launch_tile_active(a, c->dstat, s);
+        L += launch_emit_window(a, c->dstat, s);
+    }
     if (mode == Mode::Match) L += launch_emit_ranges(a, c->dstat, s);
     mark(c, 6);
     if (mode == Mode::Match) L += launch_segment_sort(a, c->dstat, s);

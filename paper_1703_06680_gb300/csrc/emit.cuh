@@ -37,7 +37,27 @@ struct EmitArgs {
     const int64_t* inst_sub_base;   // NULL in plain mode
     const int64_t* inst_upd_base;
     int num_inst;
+    // Window path (d = 1): subscriptions it could not serve are flagged and
+    // left to the range path; flag == NULL means "every subscription".
+    uint8_t* flag;
+    uint32_t* num_flagged;          // device counter; range path skipped when 0
+    // Window lists: active updates at each window boundary.
+    const uint4* windows;           // (cSlo, cUlo, cUhi, p) at p = w << win_shift, numWin + 1
+    int win_shift;
+    uint32_t num_win;
+    uint32_t* lw_size;              // capped list sizes (0 when a list overflows)
+    unsigned long long* lw_off;     // list offsets (exclusive scan of lw_size), numWin + 1
+    uint32_t* lw_fill;              // per-window fill cursor (zeroed)
+    uint2* lw;                      // list storage {id, pos(U.hi)}, lw_cap entries
+    uint4* urank;                   // {id, pos(lo), pos(hi), 0} by lower-endpoint rank, m
+    unsigned long long lw_cap;
+    const uint32_t* vals;           // sorted endpoint stream (payloads)
 };
+
+// Window path for d = 1.
+int launch_window_sizes(const EmitArgs& a, DevStatus* st, cudaStream_t s);
+int launch_tile_active(const EmitArgs& a, DevStatus* st, cudaStream_t s);
+int launch_emit_window(const EmitArgs& a, DevStatus* st, cudaStream_t s);
 
 // d > 1: permute keys of dims 1..d-1 into sub_order / upd_order layout and
 // validate those dimensions (no NaN, lo <= hi).

@@ -106,11 +106,13 @@ __device__ __forceinline__ void put_pair(const EmitArgs& a, unsigned long long p
 template <bool WRITE, bool FILTER>
 __global__ void __launch_bounds__(EMIT_BLOCK) k_class_a(EmitArgs a, DevStatus* st) {
     if (read_error(st)) return;
+    if (a.flag && *(volatile uint32_t*)a.num_flagged == 0u) return;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int64_t warps = (int64_t)gridDim.x * (EMIT_BLOCK / 32);
     for (int64_t i = ((int64_t)blockIdx.x * EMIT_BLOCK + threadIdx.x) >> 5; i < a.n; i += warps) {
-        const uint32_t A = a.rec.s_A[i], B = a.rec.s_B[i];
+        if (a.flag && !a.flag[i]) continue;
+        const uint32_t A = a.rec.s_lo[i].y, B = a.rec.s_hi[i].y;
         if (A > B || B > (uint64_t)a.m) {  // guard against an upstream fault
             if (lane == 0) raise_error(st, DDM_ERR_INTERNAL, 8);
             continue;
@@ -149,10 +151,11 @@ __global__ void __launch_bounds__(EMIT_BLOCK) k_class_a(EmitArgs a, DevStatus* s
 template <bool WRITE, bool FILTER>
 __global__ void __launch_bounds__(EMIT_BLOCK) k_class_b(EmitArgs a, DevStatus* st) {
     if (read_error(st)) return;
+    if (a.flag && *(volatile uint32_t*)a.num_flagged == 0u) return;
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (EMIT_BLOCK / 32);
     for (int64_t j = ((int64_t)blockIdx.x * EMIT_BLOCK + threadIdx.x) >> 5; j < a.m; j += warps) {
-        const uint32_t A = a.rec.u_A[j], B = a.rec.u_B[j];
+        const uint32_t A = a.rec.u_lo[j].y, B = a.rec.u_hi[j].y;
         if (A > B || B > (uint64_t)a.n) {  // guard against an upstream fault
             if (lane == 0) raise_error(st, DDM_ERR_INTERNAL, 9);
             continue;
@@ -169,10 +172,11 @@ __global__ void __launch_bounds__(EMIT_BLOCK) k_class_b(EmitArgs a, DevStatus* s
         for (uint32_t r = A + lane; r < B; r += 32) {
             if (FILTER && !pass_filter(a, o, a.subK, a.n, r)) continue;
             const uint32_t i = a.rec.sub_order[r];
+            if (a.flag && !a.flag[i]) continue;
             if (!WRITE) {
                 atomicAdd(&a.cnt[i], 1u);
             } else {
-                const uint32_t ca = FILTER ? a.cnt_a[i] : a.rec.s_B[i] - a.rec.s_A[i];
+                const uint32_t ca = FILTER ? a.cnt_a[i] : a.rec.s_hi[i].y - a.rec.s_lo[i].y;
                 const uint32_t p = atomicAdd(&a.cursor_b[i], 1u);
                 put_pair(a, a.off[i] + ca + p, (int32_t)(i - sub_base), out_j, st);
             }
@@ -180,9 +184,10 @@ __global__ void __launch_bounds__(EMIT_BLOCK) k_class_b(EmitArgs a, DevStatus* s
     }
 }
 
+// One warp per item, grid-stride; at most 8 blocks of 256 threads per SM.
 static unsigned warp_grid(int64_t items) {
     int64_t g = ceil_div((uint64_t)items, EMIT_BLOCK / 32);
-    return (unsigned)(g < 1 ? 1 : (g > 152 * 32 ? 152 * 32 : g));
+    return (unsigned)(g < 1 ? 1 : (g > 152 * 8 ? 152 * 8 : g));
 }
 
 int launch_permute_keys(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
@@ -220,10 +225,12 @@ int launch_emit_ranges(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
 __global__ void __launch_bounds__(EMIT_BLOCK) k_segsort_warp(EmitArgs a, DevStatus* st) {
     __shared__ uint32_t buf_all[EMIT_BLOCK / 32][WARP_SORT_MAX];
     if (read_error(st)) return;
+    if (a.flag && *(volatile uint32_t*)a.num_flagged == 0u) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t* buf = buf_all[warp];
     const int64_t warps = (int64_t)gridDim.x * (EMIT_BLOCK / 32);
     for (int64_t i = ((int64_t)blockIdx.x * EMIT_BLOCK + threadIdx.x) >> 5; i < a.n; i += warps) {
+        if (a.flag && !a.flag[i]) continue;
         const uint32_t c = a.cnt[i];
         if (c < 2) continue;
         if (c > WARP_SORT_MAX) {
@@ -357,7 +364,7 @@ __global__ void __launch_bounds__(BIG_BLOCK) k_segsort_big(EmitArgs a, DevStatus
 int launch_segment_sort(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
     if (a.n == 0) return 0;
     k_segsort_warp<<<warp_grid(a.n), EMIT_BLOCK, 0, s>>>(a, st);
-    k_segsort_big<<<152 * 2, BIG_BLOCK, 0, s>>>(a, st);
+    k_segsort_big<<<152, BIG_BLOCK, 0, s>>>(a, st);
     return 2;
 }
 

@@ -99,28 +99,102 @@ __device__ __forceinline__ uint32_t digit_of(KeyT k, int shift) {
     return (uint32_t)(k >> shift) & (RADIX - 1);
 }
 
+
+// Warp-parallel look-back over the per-digit tile counts.  Warp w resolves
+// digits 32w .. 32w+31 together: in one step lane l reads the 32 words of
+// predecessor tile p - l (eight 16-byte loads), and for every digit the warp
+// sums the published values back to the nearest inclusive prefix.  A step
+// thus covers 32 predecessor tiles, so even when every tile of the sort runs
+// in the same wave the chain of L2 round trips stays short.  Returns the
+// exclusive prefix of digit 32w + lane.  Each word carries its own flag, so
+// plain volatile loads suffice.  Waits are bounded (SPIN_LIMIT).
+__device__ __forceinline__ uint32_t warp_lookback_digits(const uint32_t* lookback, uint32_t tile,
+                                                         int warp, int lane, DevStatus* st) {
+    uint32_t my_prefix = 0;
+    if (tile == 0) return 0;
+    uint32_t done = 0;  // bit dd: digit 32w+dd found its inclusive prefix
+    int64_t p = (int64_t)tile - 1;
+    uint32_t it = 0;
+    while (done != 0xffffffffu) {
+        const int64_t q = p - lane;
+        uint32_t v[32];
+        if (q >= 0) {
+            const uint4* src = reinterpret_cast<const uint4*>(lookback + (uint64_t)q * RADIX + 32 * warp);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const uint4 x = __ldcv(src + k);
+                v[4 * k] = x.x; v[4 * k + 1] = x.y; v[4 * k + 2] = x.z; v[4 * k + 3] = x.w;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 32; ++k) v[k] = LB32_INC;  // before tile 0: prefix 0
+        }
+        // A window is usable for a digit when every word up to its nearest
+        // inclusive prefix is published.
+        bool ready = true;
+#pragma unroll
+        for (int dd = 0; dd < 32; ++dd) {
+            if (done & (1u << dd)) continue;
+            const unsigned inc = __ballot_sync(0xffffffffu, (v[dd] >> 30) == 2u);
+            const unsigned zero = __ballot_sync(0xffffffffu, (v[dd] >> 30) == 0u);
+            const unsigned need = inc ? (0xffffffffu >> (31 - (__ffs(inc) - 1))) : 0xffffffffu;
+            if (zero & need) ready = false;
+        }
+        if (!ready) {
+            if (++it > SPIN_LIMIT) {
+                raise_error(st, DDM_ERR_DEVICE_TIMEOUT, 2);
+                return my_prefix;
+            }
+            backoff(it);
+            continue;
+        }
+#pragma unroll
+        for (int dd = 0; dd < 32; ++dd) {
+            if (done & (1u << dd)) continue;
+            const unsigned inc = __ballot_sync(0xffffffffu, (v[dd] >> 30) == 2u);
+            const int stop = inc ? __ffs(inc) - 1 : 31;
+            uint32_t x = lane <= stop ? (v[dd] & LB32_VAL) : 0u;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (lane == dd) my_prefix += x;
+            if (inc) done |= 1u << dd;
+        }
+        p -= 32;
+    }
+    return my_prefix;
+}
+
 template <typename KeyT, int ITEMS>
 struct SortSmem {
     static constexpr int TILE = SORT_BLOCK * ITEMS;
-    union {
-        KeyT keys[TILE];
-        uint32_t vals[TILE];
-    } x;
-    uint32_t whist[SORT_BLOCK / 32][RADIX];  // per-warp digit counters
-    uint32_t tile_start[RADIX];              // exclusive scan of tile counts over digits
-    uint32_t gbase[RADIX];                   // global output base of each digit
+    KeyT keys[TILE];                          // keys staged in digit-major tile order
+    uint32_t vals[TILE];                      // values, same order
+    uint32_t whist[SORT_BLOCK / 32][RADIX];   // per-warp digit counters
+    uint32_t tile_start[RADIX];               // exclusive scan of tile counts over digits
+    uint32_t gbase[RADIX];                    // global output base of each digit
     uint32_t warp_tmp[16];
     uint32_t tile_id;
 };
 
+// Stable rank of each lane's digit among the lanes of its warp holding the same
+// digit: the peer mask is built from one ballot per digit bit (warp multisplit).
+__device__ __forceinline__ unsigned digit_peers(uint32_t d) {
+    unsigned peers = 0xffffffffu;
+#pragma unroll
+    for (int bit = 0; bit < RADIX_BITS; ++bit) {
+        const unsigned b = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
+        peers &= ((d >> bit) & 1u) ? b : ~b;
+    }
+    return peers;
+}
+
 template <typename KeyT, int ITEMS>
-__global__ void __launch_bounds__(SORT_BLOCK)
+__global__ void __launch_bounds__(SORT_BLOCK, 3)
 k_onesweep(const KeyT* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
            KeyT* __restrict__ keys_out, uint32_t* __restrict__ vals_out, uint32_t E, int shift,
            const uint32_t* __restrict__ hist_pass, uint32_t* __restrict__ lookback,
            uint32_t* __restrict__ tile_counter, int write_keys, DevStatus* st) {
     using Smem = SortSmem<KeyT, ITEMS>;
-    constexpr int TILE = Smem::TILE;
     constexpr int WARPS = SORT_BLOCK / 32;
     __shared__ Smem sm;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -129,105 +203,77 @@ k_onesweep(const KeyT* __restrict__ keys_in, const uint32_t* __restrict__ vals_i
     for (int t = tid; t < WARPS * RADIX; t += SORT_BLOCK) (&sm.whist[0][0])[t] = 0;
     __syncthreads();
     const uint32_t tile = sm.tile_id;
-    const uint64_t tile_base = (uint64_t)tile * TILE;
+    const uint64_t tile_base = (uint64_t)tile * Smem::TILE;
 
-    // Warp-striped load: warp w owns TILE/WARPS consecutive keys of the tile.
+    // Warp-striped load: warp w owns 32*ITEMS consecutive keys of the tile.
     KeyT key[ITEMS];
     uint32_t dig[ITEMS], rank[ITEMS];
     const uint64_t wbase = tile_base + (uint64_t)warp * (32 * ITEMS);
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
-        uint64_t e = wbase + (uint64_t)i * 32 + lane;
+        const uint64_t e = wbase + (uint64_t)i * 32 + lane;
         key[i] = e < E ? keys_in[e] : ~(KeyT)0;  // tail: all-ones key, digit 255, last in order
         dig[i] = digit_of(key[i], shift);
     }
-
     // Stable ranking inside the warp: items in (i, lane) order.
     const unsigned lt = (1u << lane) - 1u;
     uint32_t* wh = sm.whist[warp];
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
-        const unsigned peers = __match_any_sync(0xffffffffu, dig[i]);
+        const unsigned peers = digit_peers(dig[i]);
         const int leader = __ffs(peers) - 1;
-        const uint32_t c = wh[dig[i]];
-        __syncwarp();
-        if (lane == leader) wh[dig[i]] = c + __popc(peers);
-        __syncwarp();
+        uint32_t c = 0;
+        if (lane == leader) {
+            c = wh[dig[i]];
+            wh[dig[i]] = c + __popc(peers);
+        }
+        c = __shfl_sync(0xffffffffu, c, leader);
         rank[i] = c + __popc(peers & lt);
+        __syncwarp();
     }
     __syncthreads();
 
-    // Per digit (thread = digit): tile count and exclusive prefix over warps.
+    // Per digit (thread = digit): tile count, exclusive prefix over warps,
+    // digit starts inside the tile and in the global output.
     const int b = tid;
     uint32_t cnt = 0;
 #pragma unroll
     for (int w = 0; w < WARPS; ++w) {
-        uint32_t c = sm.whist[w][b];
+        const uint32_t c = sm.whist[w][b];
         sm.whist[w][b] = cnt;
         cnt += c;
     }
-    // Publish the tile count, then look back for the prefix of earlier tiles.
     uint32_t* my_lb = lookback + (uint64_t)tile * RADIX + b;
-    if (tile == 0) {
-        st_release_u32(my_lb, LB32_INC | cnt);
-    } else {
-        st_release_u32(my_lb, LB32_AGG | cnt);
-    }
-    uint32_t prefix = 0;
-    for (int64_t p = (int64_t)tile - 1; p >= 0; --p) {
-        const uint32_t* q = lookback + (uint64_t)p * RADIX + b;
-        uint32_t v;
-        uint32_t it = 0;
-        while (((v = ld_acquire_u32(q)) >> 30) == 0u) {
-            if (++it > SPIN_LIMIT) {
-                raise_error(st, DDM_ERR_DEVICE_TIMEOUT, 2);
-                v = LB32_INC;
-                break;
-            }
-            backoff(it);
-        }
-        prefix += v & LB32_VAL;
-        if ((v >> 30) == 2u) break;
-    }
-    if (tile != 0) st_release_u32(my_lb, LB32_INC | (prefix + cnt));
-
-    // Global base per digit: exclusive scan of the global histogram + prefix.
+    st_release_u32(my_lb, (tile == 0 ? LB32_INC : LB32_AGG) | cnt);
     const uint32_t gexcl = block_excl_scan_256(hist_pass[b], sm.warp_tmp);
-    sm.gbase[b] = gexcl + prefix;
-    const uint32_t tstart = block_excl_scan_256(cnt, sm.warp_tmp + 0);
-    sm.tile_start[b] = tstart;
+    sm.tile_start[b] = block_excl_scan_256(cnt, sm.warp_tmp);
     __syncthreads();
 
-    // Exchange through shared memory into digit-major order, then write out
-    // runs of equal digits to consecutive global positions (coalesced).
-    uint32_t slot[ITEMS];
+    // Stage keys and values in digit-major order before the look-back, so the
+    // look-back runs with few live registers.
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
-        slot[i] = sm.tile_start[dig[i]] + sm.whist[warp][dig[i]] + rank[i];
-        sm.x.keys[slot[i]] = key[i];
+        const uint32_t slot = sm.tile_start[dig[i]] + sm.whist[warp][dig[i]] + rank[i];
+        sm.keys[slot] = key[i];
+        const uint64_t e = wbase + (uint64_t)i * 32 + lane;
+        sm.vals[slot] = e < E ? vals_in[e] : 0u;
     }
+    const uint32_t prefix = warp_lookback_digits(lookback, tile, warp, lane, st);
+    if (tile != 0) st_release_u32(my_lb, LB32_INC | (prefix + cnt));
+    sm.gbase[b] = gexcl + prefix;
     __syncthreads();
-    uint32_t opos[ITEMS];
-#pragma unroll
+
+    // Runs of equal digits go to consecutive global positions (coalesced).
+#pragma unroll 4
     for (int i = 0; i < ITEMS; ++i) {
         const int s = tid + i * SORT_BLOCK;
-        const KeyT k = sm.x.keys[s];
+        const KeyT k = sm.keys[s];
         const uint32_t d = digit_of(k, shift);
-        opos[i] = sm.gbase[d] + (uint32_t)(s - sm.tile_start[d]);
-        if (write_keys && opos[i] < E) keys_out[opos[i]] = k;
-    }
-    __syncthreads();
-    // Values follow the same permutation.
-#pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-        uint64_t e = wbase + (uint64_t)i * 32 + lane;
-        sm.x.vals[slot[i]] = e < E ? vals_in[e] : 0u;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-        const int s = tid + i * SORT_BLOCK;
-        if (opos[i] < E) vals_out[opos[i]] = sm.x.vals[s];
+        const uint32_t pos = sm.gbase[d] + (uint32_t)(s - sm.tile_start[d]);
+        if (pos < E) {
+            if (write_keys) keys_out[pos] = k;
+            vals_out[pos] = sm.vals[s];
+        }
     }
 }
 

@@ -111,23 +111,26 @@ k_sweep_scan(const uint32_t* __restrict__ vals, uint32_t E, uint32_t n, uint32_t
             rec.windows[p >> rec.win_shift] = make_uint4(cSlo, cUlo, cUhi, p);
         switch (kind) {
             case KIND_SLO:
-                rec.s_pos_lo[id] = p; rec.s_A[id] = cUlo; rec.s_C[id] = cUhi;
+                rec.s_lo[id] = make_uint4(p, cUlo, cUhi, cSlo);
                 if (cSlo < n) rec.sub_order[cSlo] = id;
                 ++cSlo;
                 break;
             case KIND_ULO:
-                rec.u_pos_lo[id] = p; rec.u_A[id] = cSlo; rec.u_C[id] = cShi;
+                rec.u_lo[id] = make_uint4(p, cSlo, cShi, cUlo);
                 if (cUlo < m) rec.upd_order[cUlo] = id;
                 ++cUlo;
                 break;
             case KIND_SHI:
-                rec.s_pos_hi[id] = p; rec.s_B[id] = cUlo;
+                rec.s_hi[id] = make_uint2(p, cUlo);
                 ++cShi;
                 break;
             default:
-                rec.u_pos_hi[id] = p; rec.u_B[id] = cSlo;
+                rec.u_hi[id] = make_uint2(p, cSlo);
                 break;
         }
+        if (rec.windows && p + 1 == E)  // closing entry at position E
+            rec.windows[(E + (1u << rec.win_shift) - 1) >> rec.win_shift] =
+                make_uint4(cSlo, cUlo, E - cSlo - cUlo - cShi, E);
         if (rec.dbg_who) {
             const uint32_t cUhi_after = p + 1 - cSlo - cUlo - cShi;
             rec.dbg_who[p] = v[k];
@@ -152,13 +155,13 @@ int launch_sweep_scan(const uint32_t* vals, uint64_t E, int64_t n, int64_t m, co
 // ---------------------------------------------------------------------------
 // a4
 // ---------------------------------------------------------------------------
-__global__ void k_rank_count(const uint32_t* __restrict__ B, const uint32_t* __restrict__ C,
+__global__ void k_rank_count(const uint4* __restrict__ lo, const uint2* __restrict__ hi,
                              int64_t count, uint32_t* __restrict__ cnt, DevStatus* st) {
     if (read_error(st)) return;
     bool bad = false;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t b = B[i], c = C[i];
+        const uint32_t b = hi[i].y, c = lo[i].z;
         bad |= b < c;
         cnt[i] = b - c;
     }
@@ -172,9 +175,9 @@ int launch_rank_count(const Records& rec, int64_t n, int64_t m, uint32_t* cnt,
         return (unsigned)(g < 1 ? 1 : (g > 152 * 16 ? 152 * 16 : g));
     };
     int launches = 0;
-    if (n > 0) k_rank_count<<<grid(n), 256, 0, s>>>(rec.s_B, rec.s_C, n, cnt, st), ++launches;
+    if (n > 0) k_rank_count<<<grid(n), 256, 0, s>>>(rec.s_lo, rec.s_hi, n, cnt, st), ++launches;
     if (upd_cnt && m > 0)
-        k_rank_count<<<grid(m), 256, 0, s>>>(rec.u_B, rec.u_C, m, upd_cnt, st), ++launches;
+        k_rank_count<<<grid(m), 256, 0, s>>>(rec.u_lo, rec.u_hi, m, upd_cnt, st), ++launches;
     return launches;
 }
 
@@ -183,8 +186,9 @@ int launch_rank_count(const Records& rec, int64_t n, int64_t m, uint32_t* cnt,
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(OFF_BLOCK)
 k_offsets(const uint32_t* __restrict__ cnt, uint32_t n, unsigned long long* __restrict__ off,
-          unsigned long long cap, unsigned long long* __restrict__ status,
-          uint32_t* __restrict__ tile_counter, DevStatus* st) {
+          unsigned long long cap, unsigned long long* total_out,
+          unsigned long long* __restrict__ status, uint32_t* __restrict__ tile_counter,
+          DevStatus* st) {
     __shared__ unsigned long long warp_sum[OFF_BLOCK / 32];
     __shared__ unsigned long long tile_prefix;
     __shared__ uint32_t tile_id_s;
@@ -234,18 +238,19 @@ k_offsets(const uint32_t* __restrict__ cnt, uint32_t n, unsigned long long* __re
     // The thread holding the last element also writes off[n] and K.
     if (base < n && base + OFF_ITEMS >= n) {
         off[n] = run;
-        st->K = run;
+        *total_out = run;
         if (run > cap) raise_error(st, DDM_ERR_CAPACITY, 5);
     }
 }
 
 int launch_offsets(const uint32_t* cnt, int64_t n, unsigned long long* off, uint64_t cap,
-                    unsigned long long* status, DevStatus* st, cudaStream_t s) {
+                   unsigned long long* total, unsigned long long* status, DevStatus* st,
+                   cudaStream_t s) {
     if (n == 0) return 0;
     const uint64_t tiles = ceil_div((uint64_t)n, OFF_TILE);
     uint32_t* counter = reinterpret_cast<uint32_t*>(status + tiles);
-    k_offsets<<<(unsigned)tiles, OFF_BLOCK, 0, s>>>(cnt, (uint32_t)n, off, cap, status, counter,
-                                                    st);
+    k_offsets<<<(unsigned)tiles, OFF_BLOCK, 0, s>>>(cnt, (uint32_t)n, off, cap, total, status,
+                                                    counter, st);
     return 1;
 }
 

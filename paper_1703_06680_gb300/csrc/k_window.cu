@@ -1,0 +1,249 @@
+// a6 (d = 1): fused window emission -- candidate set per window of the sorted
+// stream, sorted once by update id, filtered per subscription in id order, so
+// every output segment is written already sorted.
+//
+// Paper: Algorithm 5 splits the sorted endpoint list T into segments and gives
+// each processor the active sets at its segment's start (SubSet[p] and
+// UpdSet[p], computed by Algorithm 6 and the prefix recurrence of Section 4).
+// Here a segment is a window of 2^win_shift stream positions, one thread block
+// each.  The block starts from UpdSet at the window boundary -- the list L_w
+// of updates with pos(lo) < w*T <= pos(hi), built by k_tile_active from the
+// scan's counts, exactly the paper's UpdSet[p] -- and adds the updates whose
+// lower endpoint lies between the boundary and the farthest upper endpoint of
+// the window's subscriptions.  That union W contains every partner of every
+// subscription starting in the window: a partner U of S either starts before
+// the boundary (then it is still active there, because it ends after S
+// starts) or starts before S ends.  W is sorted by update id in shared memory;
+// each subscription then keeps the members with pos(U.lo) < pos(S.hi) and
+// pos(S.lo) < pos(U.hi) (the closed-interval test of Algorithm 1 in stream
+// positions) and writes them in that order.
+//
+// Subscriptions spanning more than LONG_SPAN positions, and windows whose
+// boundary list exceeds LCAP entries (or the list storage), are flagged and
+// served by the range path (k_emit.cu) followed by the per-segment sort.
+#include "emit.cuh"
+
+namespace ddm {
+
+constexpr int WIN_BLOCK = 256;
+constexpr uint32_t LCAP = 1024;       // active updates per window boundary
+constexpr uint32_t WCAP = 2048;       // candidates per window
+constexpr uint32_t LONG_SPAN = 512;   // positions; longer subscriptions use the range path
+constexpr int MAX_WIN_SHIFT = 8;      // windows of at most 256 positions
+constexpr int NBUCKET = 256;          // buckets of the per-window id sort
+constexpr int WITEMS = WCAP / WIN_BLOCK;
+
+__global__ void k_window_sizes(EmitArgs a) {
+    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < a.num_win;
+         w += gridDim.x * blockDim.x) {
+        const uint4 t = a.windows[w];
+        const uint32_t s = t.y - t.z;  // updates with pos(lo) < wT <= pos(hi)
+        a.lw_size[w] = s <= LCAP ? s : 0u;
+    }
+}
+
+// Rank-ordered update table: urank[r] = {id, pos(lo), pos(hi)} of the update
+// with the r-th lower endpoint, so that windows read candidates contiguously.
+__global__ void k_rank_table(EmitArgs a) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < a.m;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t id = a.rec.upd_order[r];
+        a.urank[r] = make_uint4(id, a.rec.u_lo[id].x, a.rec.u_hi[id].x, 0u);
+    }
+}
+
+__device__ __forceinline__ bool list_fits(const EmitArgs& a, uint32_t w, uint32_t s) {
+    return s <= LCAP && a.lw_off[w] + s <= a.lw_cap;
+}
+
+// L_w: every update U contributes {id, pos(U.hi)} to the boundaries w*T with
+// pos(U.lo) < w*T <= pos(U.hi).
+__global__ void k_tile_active(EmitArgs a, DevStatus* st) {
+    if (read_error(st)) return;
+    const int S = a.win_shift;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < a.m;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t pl = a.rec.u_lo[j].x, ph = a.rec.u_hi[j].x;
+        const uint32_t w1 = min(ph >> S, a.num_win - 1);
+        for (uint32_t w = (pl >> S) + 1; w <= w1; ++w) {
+            const uint4 t = a.windows[w];
+            const uint32_t s = t.y - t.z;
+            if (!list_fits(a, w, s)) continue;
+            const uint32_t slot = atomicAdd(&a.lw_fill[w], 1u);
+            if (slot < s) a.lw[a.lw_off[w] + slot] = make_uint2((uint32_t)j, ph);
+            else raise_error(st, DDM_ERR_INTERNAL, 10);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(WIN_BLOCK) k_emit_window(EmitArgs a, DevStatus* st) {
+    constexpr uint32_t MAXSUB = 1u << MAX_WIN_SHIFT;
+    __shared__ unsigned long long skey[WCAP];  // (update id << 32) | pos(U.lo)
+    __shared__ uint32_t spay[WCAP];            // pos(U.hi)
+    __shared__ uint32_t s_id[MAXSUB], s_lo[MAXSUB], s_hi[MAXSUB], s_cnt[MAXSUB];
+    __shared__ unsigned long long s_off[MAXSUB];
+    __shared__ uint32_t bcnt[NBUCKET], bstart[NBUCKET], warp_tmp[16];
+    __shared__ uint32_t s_pmax, s_nreg;
+    if (read_error(st)) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t w = blockIdx.x;
+    const int S = a.win_shift;
+    const uint4 t0 = a.windows[w], t1 = a.windows[w + 1];
+    const uint32_t r0 = t0.x, ns = t1.x - t0.x;  // subscriptions starting in this window
+    if (ns == 0) return;
+    if (ns > MAXSUB) {
+        if (tid == 0) raise_error(st, DDM_ERR_INTERNAL, 11);
+        return;
+    }
+    if (tid == 0) { s_pmax = 0; s_nreg = 0; }
+    bcnt[tid] = 0;
+    __syncthreads();
+    for (uint32_t k = tid; k < ns; k += WIN_BLOCK) {
+        const uint32_t i = a.rec.sub_order[r0 + k];
+        const uint32_t pl = a.rec.s_lo[i].x, ph = a.rec.s_hi[i].x;
+        s_id[k] = i; s_lo[k] = pl; s_hi[k] = ph;
+        s_off[k] = a.off[i];
+        s_cnt[k] = a.cnt[i];
+        if (ph - pl <= LONG_SPAN) atomicMax(&s_pmax, ph);
+    }
+    __syncthreads();
+    const uint32_t lw_n = t0.y - t0.z;
+    const uint32_t wend = min(max((s_pmax >> S) + 1, w + 1), a.num_win);
+    const uint32_t u0 = t0.y, nlow = a.windows[wend].y - u0;
+    const uint32_t W = lw_n + nlow;
+    const bool overflow = !list_fits(a, w, lw_n) || W > WCAP;
+    // Flags: 1 = served by the range path.
+    for (uint32_t k = tid; k < ns; k += WIN_BLOCK) {
+        const bool lng = overflow || (s_hi[k] - s_lo[k] > LONG_SPAN);
+        a.flag[s_id[k]] = lng ? 1 : 0;
+        if (lng) atomicAdd(a.num_flagged, 1u);
+        else atomicAdd(&s_nreg, 1u);
+    }
+    if (overflow) return;
+
+    // Candidate set W (boundary list, then updates starting in [wT, wend*T)),
+    // held in registers: WITEMS per thread.
+    const int bshift = a.id_bits > 8 ? a.id_bits - 8 : 0;
+    unsigned long long key[WITEMS];
+    uint32_t pay[WITEMS], bk[WITEMS], rk[WITEMS];
+#pragma unroll
+    for (int it = 0; it < WITEMS; ++it) {
+        const uint32_t k = tid + it * WIN_BLOCK;
+        if (k < W) {
+            uint32_t id, pl;
+            if (k < lw_n) {
+                const uint2 e = a.lw[a.lw_off[w] + k];
+                id = e.x; pl = 0u; pay[it] = e.y;  // starts before the window: pos(lo) < any pos(S.hi)
+            } else {
+                const uint4 e = a.urank[u0 + k - lw_n];
+                id = e.x; pl = e.y; pay[it] = e.z;
+            }
+            key[it] = ((unsigned long long)id << 32) | pl;
+            bk[it] = id >> bshift;
+            rk[it] = atomicAdd(&bcnt[bk[it]], 1u);
+        }
+    }
+    __syncthreads();
+    // Bucket sort by the high id bits: bucket starts by a block scan, then the
+    // exact position inside a bucket by counting smaller keys among its members.
+    {
+        const uint32_t c = bcnt[tid];
+        uint32_t x = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_tmp[warp] = x;
+        __syncthreads();
+        uint32_t before = 0;
+#pragma unroll
+        for (int q = 0; q < WIN_BLOCK / 32; ++q) before += q < warp ? warp_tmp[q] : 0u;
+        bstart[tid] = before + x - c;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < WITEMS; ++it) {
+        const uint32_t k = tid + it * WIN_BLOCK;
+        if (k < W) skey[bstart[bk[it]] + rk[it]] = key[it];
+    }
+    __syncthreads();
+    uint32_t fin[WITEMS];
+#pragma unroll
+    for (int it = 0; it < WITEMS; ++it) {
+        const uint32_t k = tid + it * WIN_BLOCK;
+        if (k < W) {
+            const uint32_t s0 = bstart[bk[it]], c = bcnt[bk[it]];
+            uint32_t f = s0;
+            for (uint32_t q = s0; q < s0 + c; ++q) f += skey[q] < key[it];
+            fin[it] = f;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < WITEMS; ++it) {
+        const uint32_t k = tid + it * WIN_BLOCK;
+        if (k < W) {
+            skey[fin[it]] = key[it];
+            spay[fin[it]] = pay[it];
+        }
+    }
+    __syncthreads();
+    if (s_nreg == 0) return;
+
+    // One warp per subscription: keep the members of W it intersects.
+    const unsigned lt = (1u << lane) - 1u;
+    int2* out = reinterpret_cast<int2*>(a.pairs);
+    for (uint32_t k = warp; k < ns; k += WIN_BLOCK / 32) {
+        const uint32_t pl = s_lo[k], ph = s_hi[k];
+        if (ph - pl > LONG_SPAN) continue;
+        const int32_t i = (int32_t)s_id[k];
+        const unsigned long long base = s_off[k];
+        const uint32_t c = s_cnt[k];
+        uint32_t running = 0;
+        for (uint32_t k0 = 0; k0 < W; k0 += 32) {
+            const uint32_t kk = k0 + lane;
+            bool pass = false;
+            unsigned long long kv = 0;
+            if (kk < W) {
+                kv = skey[kk];
+                pass = (uint32_t)kv < ph && spay[kk] > pl;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, pass);
+            if (pass) {
+                const uint32_t r = running + __popc(bal & lt);
+                if (r < c) out[base + r] = make_int2(i, (int32_t)(kv >> 32));
+            }
+            running += __popc(bal);
+        }
+        if (lane == 0 && running != c) raise_error(st, DDM_ERR_INTERNAL, 12);
+    }
+}
+
+static unsigned grid_for(uint64_t items, unsigned per_block, unsigned cap) {
+    uint64_t g = ceil_div(items, per_block);
+    return (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+int launch_window_sizes(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
+    (void)st;
+    if (a.num_win == 0) return 0;
+    k_window_sizes<<<grid_for(a.num_win, 256, 152 * 8), 256, 0, s>>>(a);
+    return 1;
+}
+
+int launch_tile_active(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
+    if (a.m == 0 || a.num_win == 0) return 0;
+    k_rank_table<<<grid_for(a.m, 256, 152 * 16), 256, 0, s>>>(a);
+    k_tile_active<<<grid_for(a.m, 256, 152 * 16), 256, 0, s>>>(a, st);
+    return 2;
+}
+
+int launch_emit_window(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
+    if (a.num_win == 0 || a.n == 0) return 0;
+    if (a.win_shift > MAX_WIN_SHIFT) return -1;
+    k_emit_window<<<a.num_win, WIN_BLOCK, 0, s>>>(a, st);
+    return 1;
+}
+
+}  // namespace ddm

@@ -18,13 +18,18 @@ constexpr int OFF_TILE = OFF_BLOCK * OFF_ITEMS;
 // Per-region rank records written by the sweep scan.  Position p is an
 // index into the sorted endpoint stream; cSlo(p), cUlo(p), cShi(p), cUhi(p)
 // count the S lowers, U lowers, S uppers and U uppers strictly before p.
-//   S_i: pos_lo, pos_hi, A = cUlo(pos_lo), B = cUlo(pos_hi), C = cUhi(pos_lo)
-//   U_j: pos_lo, pos_hi, A = cSlo(pos_lo), B = cSlo(pos_hi), C = cShi(pos_lo)
+// Each endpoint event writes ONE packed record (a single scattered store):
+//   s_lo[i] = {pos(S_i.lo), A = cUlo(pos lo), C = cUhi(pos lo), cSlo(pos lo)}
+//   s_hi[i] = {pos(S_i.hi), B = cUlo(pos hi)}
+//   u_lo[j] = {pos(U_j.lo), A = cSlo(pos lo), C = cShi(pos lo), cUlo(pos lo)}
+//   u_hi[j] = {pos(U_j.hi), B = cSlo(pos hi)}
 // sub_order[r] (upd_order[r]) is the id of the subscription (update) whose
 // lower endpoint is the r-th S (U) lower endpoint of the stream.
 struct Records {
-    uint32_t *s_pos_lo, *s_pos_hi, *s_A, *s_B, *s_C;
-    uint32_t *u_pos_lo, *u_pos_hi, *u_A, *u_B, *u_C;
+    uint4* s_lo;
+    uint2* s_hi;
+    uint4* u_lo;
+    uint2* u_hi;
     uint32_t *sub_order, *upd_order;
     uint4* windows;       // (cSlo, cUlo, cUhi, p) at p = w << win_shift, or NULL
     int win_shift;
@@ -39,9 +44,11 @@ int launch_sweep_scan(const uint32_t* vals, uint64_t E, int64_t n, int64_t m, co
 int launch_rank_count(const Records& rec, int64_t n, int64_t m, uint32_t* cnt,
                        uint32_t* upd_cnt, DevStatus* st, cudaStream_t s);
 
-// off[i] = sum_{i' < i} cnt[i'] (u64), off[n] = K, st->K = K; raises
-// DDM_ERR_CAPACITY when K > cap.  Status words: ceil(n / OFF_TILE) + 1 u64, zeroed.
+// off[i] = sum_{i' < i} cnt[i'] (u64), off[n] = *total = the sum; raises
+// DDM_ERR_CAPACITY when the sum exceeds cap.  Status words: ceil(n / OFF_TILE)
+// + 2 u64, zeroed.  *total must be zero on entry (it is left 0 when n == 0).
 int launch_offsets(const uint32_t* cnt, int64_t n, unsigned long long* off, uint64_t cap,
-                    unsigned long long* status, DevStatus* st, cudaStream_t s);
+                   unsigned long long* total, unsigned long long* status, DevStatus* st,
+                   cudaStream_t s);
 
 }  // namespace ddm

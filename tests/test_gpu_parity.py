@@ -80,7 +80,8 @@ def test_nd_full_size_sampled(ctx, d, alpha):
 
 def test_sweep_stages_match_oracle_trace(ctx):
     reg = synth.make_regions(1, 30_011, 29_989, 40.0, 99)  # dense float32 ties near 1e6
-    who, ss, us, sc, uc = [x.cpu().numpy().astype(np.int64) for x in ctx.debug_sweep(*to_dev(reg))]
+    who, ss, us, sc, uc = [x.cpu().numpy().view(np.uint32).astype(np.int64)
+                           for x in ctx.debug_sweep(*to_dev(reg))]
     kind, ids, oss, ous = oracle.sweep_trace(reg)
     assert np.array_equal(who >> 30, kind.astype(np.int64))
     assert np.array_equal(who & ((1 << 30) - 1), ids.astype(np.int64))
