@@ -137,8 +137,7 @@ struct Plan {
     int64_t n, m, E;
     int d;
     // zeroed region
-    uint32_t* hist;
-    uint32_t* sort_lb;
+    SortScratch sort;
     unsigned long long* scan_status;
     unsigned long long* off_status;
     uint32_t* cursor_b;
@@ -171,8 +170,8 @@ struct Plan {
         d = d_; n = n_; m = m_; E = 2 * (n + m);
         Carve cv;
         cv.base = base;
-        hist = cv.take<uint32_t>(4 * RADIX);
-        sort_lb = cv.take<uint32_t>(sort_lookback_words<uint32_t>(E, 4));
+        sort.status = cv.take<unsigned long long>(4 * sort_status_stride(E));
+        sort.total = cv.take<unsigned long long>(1);
         scan_status = cv.take<unsigned long long>(3 * (ceil_div(E, SCAN_TILE) + 1) + 1);
         off_status = cv.take<unsigned long long>(ceil_div(n, OFF_TILE) + 2);
         cursor_b = cv.take<uint32_t>(mode == Mode::Match ? n : 0);
@@ -192,6 +191,8 @@ struct Plan {
         lw = cv.take<uint2>(lw_cap);
         urank = cv.take<uint4>(window ? m : 0);
         flag = cv.take<uint8_t>(window ? n : 0);
+        sort.tile_hist = cv.take<uint32_t>(sort_tiles<uint32_t>(E) * RADIX);
+        sort.offs = cv.take<unsigned long long>(sort_tiles<uint32_t>(E) * RADIX + 1);
         keys0 = cv.take<uint32_t>(E);
         keys1 = cv.take<uint32_t>(E);
         vals0 = cv.take<uint32_t>(E);
@@ -242,10 +243,10 @@ int enqueue_plain(ddm_ctx* c, const ddm_regions* r, Mode mode, int32_t* pairs, u
     }
     uint64_t& L = c->stats.launches;
     L += launch_keybuild_d0(r->sub_lo[0], r->sub_hi[0], r->upd_lo[0], r->upd_hi[0], pl.n, pl.m,
-                            pl.keys0, pl.vals0, pl.hist, c->dstat, s);
+                            pl.keys0, pl.vals0, c->dstat, s);
     mark(c, 1);
-    L += launch_radix_sort<uint32_t>(pl.keys0, pl.vals0, pl.keys1, pl.vals1, pl.E, 4, pl.hist,
-                                     pl.sort_lb, true, c->dstat, s);
+    L += launch_radix_sort<uint32_t>(pl.keys0, pl.vals0, pl.keys1, pl.vals1, pl.E, 4, pl.sort,
+                                     true, c->dstat, s);
     mark(c, 2);
     Records rec = pl.rec;
     if (pl.window) {

@@ -27,7 +27,7 @@ namespace ddm {
 
 constexpr int WIN_BLOCK = 256;
 constexpr uint32_t LCAP = 1024;       // active updates per window boundary
-constexpr uint32_t WCAP = 2048;       // candidates per window
+constexpr uint32_t WCAP = 1024;       // candidates per window
 constexpr uint32_t LONG_SPAN = 512;   // positions; longer subscriptions use the range path
 constexpr int MAX_WIN_SHIFT = 8;      // windows of at most 256 positions
 constexpr int NBUCKET = 256;          // buckets of the per-window id sort
@@ -188,32 +188,31 @@ __global__ void __launch_bounds__(WIN_BLOCK) k_emit_window(EmitArgs a, DevStatus
             spay[fin[it]] = pay[it];
         }
     }
+    // Pad W to whole warps with entries that no subscription keeps
+    // (pos(lo) = 0xffffffff is never below a pos(S.hi)).
+    const uint32_t Wpad = (W + 31) & ~31u;
+    for (uint32_t k = W + tid; k < Wpad; k += WIN_BLOCK) {
+        skey[k] = ~0ull;
+        spay[k] = 0u;
+    }
     __syncthreads();
     if (s_nreg == 0) return;
 
     // One warp per subscription: keep the members of W it intersects.
     const unsigned lt = (1u << lane) - 1u;
-    int2* out = reinterpret_cast<int2*>(a.pairs);
     for (uint32_t k = warp; k < ns; k += WIN_BLOCK / 32) {
         const uint32_t pl = s_lo[k], ph = s_hi[k];
         if (ph - pl > LONG_SPAN) continue;
         const int32_t i = (int32_t)s_id[k];
-        const unsigned long long base = s_off[k];
+        int2* seg = reinterpret_cast<int2*>(a.pairs) + s_off[k];
         const uint32_t c = s_cnt[k];
         uint32_t running = 0;
-        for (uint32_t k0 = 0; k0 < W; k0 += 32) {
-            const uint32_t kk = k0 + lane;
-            bool pass = false;
-            unsigned long long kv = 0;
-            if (kk < W) {
-                kv = skey[kk];
-                pass = (uint32_t)kv < ph && spay[kk] > pl;
-            }
+        for (uint32_t kk = lane; kk < Wpad; kk += 32) {
+            const unsigned long long kv = skey[kk];
+            const bool pass = (uint32_t)kv < ph && spay[kk] > pl;
             const unsigned bal = __ballot_sync(0xffffffffu, pass);
-            if (pass) {
-                const uint32_t r = running + __popc(bal & lt);
-                if (r < c) out[base + r] = make_int2(i, (int32_t)(kv >> 32));
-            }
+            const uint32_t r = running + __popc(bal & lt);
+            if (pass && r < c) seg[r] = make_int2(i, (int32_t)(kv >> 32));
             running += __popc(bal);
         }
         if (lane == 0 && running != c) raise_error(st, DDM_ERR_INTERNAL, 12);
