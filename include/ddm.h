@@ -118,6 +118,29 @@ int ddm_match_host(ddm_ctx *ctx, const ddm_regions *regions, int32_t *pairs, uin
                    uint64_t *K_out);
 
 /*
+ * ddm_count without any allocation.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory -- code that
+ * runs where cudaMalloc is unavailable or forbidden (a host callback, a
+ * custom allocator that owns all device memory, a simulation loop that must
+ * not allocate after start-up).  It needs no context: it runs on the CURRENT
+ * device and on `cuda_stream` (NULL = legacy default stream), and returns the
+ * same K as ddm_count for the same DEVICE coordinates.
+ *
+ * All scratch lives in one fixed 24 MiB __device__ array inside the library,
+ * held by every GPU that loads the library until the process exits.  The call
+ * makes no cudaMalloc/cudaFree and no other allocation.  Limit: n + m <=
+ * DDM_NOALLOC_MAX_REGIONS; larger instances (and bad arguments) return
+ * DDM_ERR_INVALID without touching the GPU.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress); make that
+ * first call before any stream capture.  All calls share the array: calls
+ * that overlap on the GPU (two streams, two threads) race and give wrong
+ * results, so serialise them.  Synchronous: returns after the stream has
+ * finished the work.  Errors as for ddm_count.
+ */
+#define DDM_NOALLOC_MAX_REGIONS ((int64_t)1 << 17)
+int ddm_count_noalloc(const ddm_regions *regions, void *cuda_stream, uint64_t *K_out);
+
+/*
  * Counters and per-stage timing.  With profiling enabled (ddm_set_profiling),
  * every call records CUDA events on the context's stream at the stage
  * boundaries, and stage_ms[] holds the device time of each stage of the last

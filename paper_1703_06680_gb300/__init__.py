@@ -6,6 +6,6 @@ Matching for Data Distribution Management on Shared-Memory Multiprocessors"
 (DS-RT 2017).  The computation lives in the CUDA library declared by
 include/ddm.h; this package is its thin Python binding.
 """
-from ._lib import (CapacityError, Context, DDMError, LIB_PATH, SIGNATURES,  # noqa: F401
-                   load_library)
+from ._lib import (CapacityError, Context, DDMError, LIB_PATH, NOALLOC_MAX_REGIONS,  # noqa: F401
+                   SIGNATURES, count_noalloc, load_library)
 from .build import build as build_library  # noqa: F401

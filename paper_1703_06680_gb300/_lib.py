@@ -72,6 +72,7 @@ SIGNATURES = {
     "ddm_match_host": (ctypes.c_int, [_P, _RP, _P, ctypes.c_uint64, _U64P]),
     "ddm_debug_sweep": (ctypes.c_int, [_P, _RP, _P, _P, _P, _P, _P]),
     "ddm_set_profiling": (ctypes.c_int, [_P, ctypes.c_int]),
+    "ddm_count_noalloc": (ctypes.c_int, [_RP, _P, _U64P]),
     "ddm_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(Stats)]),
 }
 
@@ -138,6 +139,31 @@ def _pack_host(sub_lo, sub_hi, upd_lo, upd_hi):
     p = _Packed(d, n, m, ptrs)
     p.keep = arrs
     return p
+
+
+NOALLOC_MAX_REGIONS = 1 << 17
+
+
+def count_noalloc(sub_lo, sub_hi, upd_lo, upd_hi, stream=None) -> int:
+    """ddm_count_noalloc: exact K without any allocation (no context needed).
+
+    For callers that cannot allocate device memory.  Runs on the current CUDA
+    device; n + m must not exceed NOALLOC_MAX_REGIONS.  Calls that overlap on
+    the GPU share the library's fixed scratch and race: serialise them.
+    """
+    lib = load_library()
+    torch = _torch()
+    p = _pack_device(sub_lo, sub_hi, upd_lo, upd_hi)
+    if p.s.n + p.s.m > NOALLOC_MAX_REGIONS:
+        raise DDMError(DDM_ERR_INVALID, f"n + m = {p.s.n + p.s.m} exceeds the no-allocation "
+                                        f"limit of {NOALLOC_MAX_REGIONS} regions")
+    if stream is None:
+        stream = torch.cuda.current_stream(sub_lo.device)
+    K = ctypes.c_uint64(0)
+    rc = lib.ddm_count_noalloc(p.ref, ctypes.c_void_p(stream.cuda_stream), ctypes.byref(K))
+    if rc != DDM_OK:
+        raise DDMError(rc, "ddm_count_noalloc failed")
+    return int(K.value)
 
 
 class Context:
