@@ -86,19 +86,6 @@ __device__ __forceinline__ uint32_t digit_of(KeyT k, int shift) {
     return (uint32_t)(k >> shift) & (RADIX - 1);
 }
 
-// Lanes of the warp holding the same digit (warp multisplit: one ballot per
-// digit bit).  The mask equals what __match_any_sync returns, built from
-// cheap ballots.
-__device__ __forceinline__ unsigned digit_peers(uint32_t d) {
-    unsigned peers = 0xffffffffu;
-#pragma unroll
-    for (int bit = 0; bit < RADIX_BITS; ++bit) {
-        const unsigned b = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
-        peers &= ((d >> bit) & 1u) ? b : ~b;
-    }
-    return peers;
-}
-
 // Upsweep: digit histogram of one tile, stored digit-major
 // (tile_hist[d * tiles + tile]) so that one flat exclusive scan yields every
 // (digit, tile) output base: all smaller digits first, then earlier tiles.
@@ -112,13 +99,10 @@ k_upsweep(const KeyT* __restrict__ keys, uint32_t E, int shift, uint32_t* __rest
     __syncthreads();
     const uint32_t tile = blockIdx.x;
     const uint64_t wbase = (uint64_t)tile * (SORT_BLOCK * ITEMS) + (uint64_t)warp * (32 * ITEMS);
-#pragma unroll 4
+#pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
         const uint64_t e = wbase + (uint64_t)i * 32 + lane;
-        const bool valid = e < E;
-        const uint32_t d = valid ? digit_of(keys[e], shift) : 0u;
-        const unsigned peers = digit_peers(d) & __ballot_sync(0xffffffffu, valid);
-        if (valid && lane == __ffs(peers) - 1) atomicAdd(&h[d], (uint32_t)__popc(peers));
+        if (e < E) atomicAdd(&h[digit_of(keys[e], shift)], 1u);
     }
     __syncthreads();
     tile_hist[(uint64_t)tid * tiles + tile] = h[tid];
@@ -128,7 +112,10 @@ template <typename KeyT, int ITEMS>
 struct SortSmem {
     static constexpr int TILE = SORT_BLOCK * ITEMS;
     KeyT keys[TILE];                          // keys staged in digit-major tile order
-    uint32_t vals[TILE];                      // values, same order
+    union {
+        uint32_t vals[TILE];                  // values, same order (after ranking)
+        uint32_t peers[SORT_BLOCK / 32][RADIX];  // per-warp lane masks (during ranking)
+    } u;
     uint32_t whist[SORT_BLOCK / 32][RADIX];   // per-warp digit counters
     uint32_t tile_start[RADIX];               // exclusive scan of tile counts over digits
     uint32_t gbase[RADIX];                    // global output base of each digit
@@ -148,7 +135,10 @@ k_downsweep(const KeyT* __restrict__ keys_in, const uint32_t* __restrict__ vals_
     constexpr int WARPS = SORT_BLOCK / 32;
     __shared__ Smem sm;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int t = tid; t < WARPS * RADIX; t += SORT_BLOCK) (&sm.whist[0][0])[t] = 0;
+    for (int t = tid; t < WARPS * RADIX; t += SORT_BLOCK) {
+        (&sm.whist[0][0])[t] = 0;
+        (&sm.u.peers[0][0])[t] = 0;
+    }
     const uint32_t tile = blockIdx.x;
     sm.gbase[tid] = (uint32_t)base[(uint64_t)tid * tiles + tile];
     __syncthreads();
@@ -163,15 +153,23 @@ k_downsweep(const KeyT* __restrict__ keys_in, const uint32_t* __restrict__ vals_
         key[i] = e < E ? keys_in[e] : ~(KeyT)0;  // tail: all-ones key, digit 255, last in order
         dig[i] = digit_of(key[i], shift);
     }
-    // Stable ranking inside the warp: items in (i, lane) order.
+    // Stable ranking inside the warp, items in (i, lane) order: the lanes
+    // holding the same digit find each other through a per-warp mask word per
+    // digit in shared memory (atomicOr of the lane bit); the lowest such lane
+    // advances the warp's counter for that digit and clears the mask.
     const unsigned lt = (1u << lane) - 1u;
     uint32_t* wh = sm.whist[warp];
+    uint32_t* pm = sm.u.peers[warp];
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
-        const unsigned peers = digit_peers(dig[i]);
+        atomicOr(&pm[dig[i]], 1u << lane);
+        __syncwarp();
+        const unsigned peers = pm[dig[i]];
+        __syncwarp();
         const int leader = __ffs(peers) - 1;
         uint32_t c = 0;
         if (lane == leader) {
+            pm[dig[i]] = 0u;
             c = wh[dig[i]];
             wh[dig[i]] = c + __popc(peers);
         }
@@ -197,7 +195,7 @@ k_downsweep(const KeyT* __restrict__ keys_in, const uint32_t* __restrict__ vals_
         const uint32_t slot = sm.tile_start[dig[i]] + sm.whist[warp][dig[i]] + rank[i];
         sm.keys[slot] = key[i];
         const uint64_t e = wbase + (uint64_t)i * 32 + lane;
-        sm.vals[slot] = e < E ? vals_in[e] : 0u;
+        sm.u.vals[slot] = e < E ? vals_in[e] : 0u;
     }
     __syncthreads();
     // Runs of equal digits go to consecutive global positions (coalesced).
@@ -209,7 +207,7 @@ k_downsweep(const KeyT* __restrict__ keys_in, const uint32_t* __restrict__ vals_
         const uint32_t pos = sm.gbase[d] + (uint32_t)(s - sm.tile_start[d]);
         if (pos < E) {
             if (write_keys) keys_out[pos] = k;
-            vals_out[pos] = sm.vals[s];
+            vals_out[pos] = sm.u.vals[s];
         }
     }
 }

@@ -45,9 +45,11 @@ k_sweep_scan(const uint32_t* __restrict__ vals, uint32_t E, uint32_t n, uint32_t
     uint32_t v[SCAN_ITEMS];
     if (base + SCAN_ITEMS <= E) {
         const uint4* p4 = reinterpret_cast<const uint4*>(vals + base);
-        uint4 a = p4[0], b = p4[1];
-        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+#pragma unroll
+        for (int q = 0; q < SCAN_ITEMS / 4; ++q) {
+            const uint4 a = p4[q];
+            v[4 * q] = a.x; v[4 * q + 1] = a.y; v[4 * q + 2] = a.z; v[4 * q + 3] = a.w;
+        }
     } else {
 #pragma unroll
         for (int k = 0; k < SCAN_ITEMS; ++k) v[k] = base + k < E ? vals[base + k] : 0xFFFFFFFFu;
@@ -184,11 +186,17 @@ int launch_rank_count(const Records& rec, int64_t n, int64_t m, uint32_t* cnt,
 // ---------------------------------------------------------------------------
 // a5
 // ---------------------------------------------------------------------------
+// Padded shared-memory index (one extra word every 32) against bank conflicts
+// when a thread walks its own run of OFF_ITEMS consecutive elements.
+__device__ __forceinline__ int pad32(int i) { return i + (i >> 5); }
+
 __global__ void __launch_bounds__(OFF_BLOCK)
 k_offsets(const uint32_t* __restrict__ cnt, uint32_t n, unsigned long long* __restrict__ off,
           unsigned long long cap, unsigned long long* total_out,
           unsigned long long* __restrict__ status, uint32_t* __restrict__ tile_counter,
           DevStatus* st) {
+    __shared__ uint32_t s_in[OFF_TILE + OFF_TILE / 32];
+    __shared__ unsigned long long s_out[OFF_TILE + OFF_TILE / 32];
     __shared__ unsigned long long warp_sum[OFF_BLOCK / 32];
     __shared__ unsigned long long tile_prefix;
     __shared__ uint32_t tile_id_s;
@@ -196,12 +204,19 @@ k_offsets(const uint32_t* __restrict__ cnt, uint32_t n, unsigned long long* __re
     if (tid == 0) tile_id_s = atomicAdd(tile_counter, 1u);
     __syncthreads();
     const uint32_t tile = tile_id_s;
-    const uint64_t base = (uint64_t)tile * OFF_TILE + (uint64_t)tid * OFF_ITEMS;
+    const uint64_t tbase = (uint64_t)tile * OFF_TILE;
+    // Coalesced load (striped), then each thread takes OFF_ITEMS consecutive values.
+#pragma unroll
+    for (int k = 0; k < OFF_ITEMS; ++k) {
+        const int i = k * OFF_BLOCK + tid;
+        s_in[pad32(i)] = tbase + i < n ? cnt[tbase + i] : 0u;
+    }
+    __syncthreads();
     uint32_t c[OFF_ITEMS];
     unsigned long long mine = 0;
 #pragma unroll
     for (int k = 0; k < OFF_ITEMS; ++k) {
-        c[k] = base + k < n ? cnt[base + k] : 0u;
+        c[k] = s_in[pad32(tid * OFF_ITEMS + k)];
         mine += c[k];
     }
     unsigned long long x = mine;
@@ -232,11 +247,18 @@ k_offsets(const uint32_t* __restrict__ cnt, uint32_t n, unsigned long long* __re
     unsigned long long run = tile_prefix + wexcl + x - mine;
 #pragma unroll
     for (int k = 0; k < OFF_ITEMS; ++k) {
-        if (base + k < n) off[base + k] = run;
+        s_out[pad32(tid * OFF_ITEMS + k)] = run;
         run += c[k];
     }
-    // The thread holding the last element also writes off[n] and K.
-    if (base < n && base + OFF_ITEMS >= n) {
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < OFF_ITEMS; ++k) {
+        const int i = k * OFF_BLOCK + tid;
+        if (tbase + i < n) off[tbase + i] = s_out[pad32(i)];
+    }
+    // The thread holding the last element also writes off[n] and the total.
+    const uint64_t mybase = tbase + (uint64_t)tid * OFF_ITEMS;
+    if (mybase < n && mybase + OFF_ITEMS >= n) {
         off[n] = run;
         *total_out = run;
         if (run > cap) raise_error(st, DDM_ERR_CAPACITY, 5);

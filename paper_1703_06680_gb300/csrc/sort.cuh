@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "sweep.cuh"
 
 namespace ddm {
 
@@ -35,7 +36,7 @@ struct SortScratch {
 // Status words of one pass's flat scan (sized for the 64-bit-key tiling, the
 // larger of the two).
 inline size_t sort_status_stride(uint64_t E) {
-    return (size_t)ceil_div(sort_tiles<unsigned long long>(E) * RADIX, 4096) + 2;
+    return (size_t)ceil_div(sort_tiles<unsigned long long>(E) * RADIX, OFF_TILE) + 2;
 }
 
 // Dimension-0 key build for one instance: validates every extent of dim 0

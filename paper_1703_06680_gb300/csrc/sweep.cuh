@@ -9,10 +9,10 @@
 namespace ddm {
 
 constexpr int SCAN_BLOCK = 256;
-constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_ITEMS = 32;
 constexpr int SCAN_TILE = SCAN_BLOCK * SCAN_ITEMS;
 constexpr int OFF_BLOCK = 256;
-constexpr int OFF_ITEMS = 16;
+constexpr int OFF_ITEMS = 8;
 constexpr int OFF_TILE = OFF_BLOCK * OFF_ITEMS;
 
 // Per-region rank records written by the sweep scan.  Position p is an
