@@ -89,74 +89,113 @@ __device__ __forceinline__ uint32_t digit_of(KeyT k, int shift) {
 // Upsweep: digit histogram of one tile, stored digit-major
 // (tile_hist[d * tiles + tile]) so that one flat exclusive scan yields every
 // (digit, tile) output base: all smaller digits first, then earlier tiles.
+// A full tile arrives in shared memory by one TMA bulk copy.
 template <typename KeyT, int ITEMS>
 __global__ void __launch_bounds__(SORT_BLOCK)
 k_upsweep(const KeyT* __restrict__ keys, uint32_t E, int shift, uint32_t* __restrict__ tile_hist,
-          uint32_t tiles) {
+          uint32_t tiles, DevStatus* st) {
+    constexpr int TILE = SORT_BLOCK * ITEMS;
+    __shared__ alignas(128) KeyT sk[TILE];
     __shared__ uint32_t h[RADIX];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    h[tid] = 0;
-    __syncthreads();
+    __shared__ alignas(8) uint64_t bar;
+    const int tid = threadIdx.x;
     const uint32_t tile = blockIdx.x;
-    const uint64_t wbase = (uint64_t)tile * (SORT_BLOCK * ITEMS) + (uint64_t)warp * (32 * ITEMS);
+    const uint64_t base = (uint64_t)tile * TILE;
+    const bool full = base + TILE <= E;
+    h[tid] = 0;
+    if (tid == 0 && full) mbar_init(&bar, 1);
+    __syncthreads();
+    if (full) {
+        if (tid == 0) {
+            mbar_expect_tx(&bar, TILE * sizeof(KeyT));
+            tma_load_1d(sk, keys + base, TILE * sizeof(KeyT), &bar);
+        }
+        mbar_wait_bounded(&bar, 0, st, 13);
 #pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-        const uint64_t e = wbase + (uint64_t)i * 32 + lane;
-        if (e < E) atomicAdd(&h[digit_of(keys[e], shift)], 1u);
+        for (int i = 0; i < ITEMS; ++i) atomicAdd(&h[digit_of(sk[i * SORT_BLOCK + tid], shift)], 1u);
+    } else {
+        for (int i = 0; i < ITEMS; ++i) {
+            const uint64_t e = base + i * SORT_BLOCK + tid;
+            if (e < E) atomicAdd(&h[digit_of(keys[e], shift)], 1u);
+        }
     }
     __syncthreads();
     tile_hist[(uint64_t)tid * tiles + tile] = h[tid];
 }
 
+// Shared memory of one downsweep tile (dynamic, > 48 KB).
 template <typename KeyT, int ITEMS>
-struct SortSmem {
+struct DownSmem {
     static constexpr int TILE = SORT_BLOCK * ITEMS;
-    KeyT keys[TILE];                          // keys staged in digit-major tile order
+    KeyT keys[TILE];                          // raw tile, then keys in digit-major order
+    uint32_t vals_raw[TILE];                  // raw tile values
     union {
-        uint32_t vals[TILE];                  // values, same order (after ranking)
+        uint32_t vals[TILE];                  // values in digit-major order (after ranking)
         uint32_t peers[SORT_BLOCK / 32][RADIX];  // per-warp lane masks (during ranking)
     } u;
     uint32_t whist[SORT_BLOCK / 32][RADIX];   // per-warp digit counters
     uint32_t tile_start[RADIX];               // exclusive scan of tile counts over digits
     uint32_t gbase[RADIX];                    // global output base of each digit
     uint32_t warp_tmp[16];
+    uint64_t bar;
 };
 
-// Downsweep: stable rank of every key inside its tile (warp multisplit, then
-// warp-ordered prefix), exchange through shared memory into digit-major
-// order, and write runs of equal digits to consecutive output positions
-// starting at the scanned (digit, tile) base.
+// Downsweep: the tile arrives by TMA bulk copies (keys and values); stable
+// rank of every key inside the tile (per-warp peer masks, warp-ordered
+// prefix); exchange through shared memory into digit-major order; runs of
+// equal digits are written to consecutive output positions starting at the
+// scanned (digit, tile) base.
 template <typename KeyT, int ITEMS>
 __global__ void __launch_bounds__(SORT_BLOCK, 3)
 k_downsweep(const KeyT* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
             KeyT* __restrict__ keys_out, uint32_t* __restrict__ vals_out, uint32_t E, int shift,
-            const unsigned long long* __restrict__ base, uint32_t tiles, int write_keys) {
-    using Smem = SortSmem<KeyT, ITEMS>;
+            const unsigned long long* __restrict__ base, uint32_t tiles, int write_keys,
+            DevStatus* st) {
+    using Smem = DownSmem<KeyT, ITEMS>;
+    constexpr int TILE = Smem::TILE;
     constexpr int WARPS = SORT_BLOCK / 32;
-    __shared__ Smem sm;
+    extern __shared__ __align__(128) unsigned char dsm[];
+    Smem& sm = *reinterpret_cast<Smem*>(dsm);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t tile = blockIdx.x;
+    const uint64_t tbase = (uint64_t)tile * TILE;
+    const bool full = tbase + TILE <= E;
+    if (tid == 0 && full) mbar_init(&sm.bar, 1);
     for (int t = tid; t < WARPS * RADIX; t += SORT_BLOCK) {
         (&sm.whist[0][0])[t] = 0;
         (&sm.u.peers[0][0])[t] = 0;
     }
-    const uint32_t tile = blockIdx.x;
     sm.gbase[tid] = (uint32_t)base[(uint64_t)tid * tiles + tile];
     __syncthreads();
+    if (full) {
+        if (tid == 0) {
+            mbar_expect_tx(&sm.bar, TILE * (sizeof(KeyT) + sizeof(uint32_t)));
+            tma_load_1d(sm.keys, keys_in + tbase, TILE * sizeof(KeyT), &sm.bar);
+            tma_load_1d(sm.vals_raw, vals_in + tbase, TILE * sizeof(uint32_t), &sm.bar);
+        }
+        mbar_wait_bounded(&sm.bar, 0, st, 14);
+    } else {
+        for (int i = tid; i < TILE; i += SORT_BLOCK) {
+            const uint64_t e = tbase + i;
+            sm.keys[i] = e < E ? keys_in[e] : ~(KeyT)0;  // tail: all-ones key, digit 255, last
+            sm.vals_raw[i] = e < E ? vals_in[e] : 0u;
+        }
+        __syncthreads();
+    }
 
-    // Warp-striped load: warp w owns 32*ITEMS consecutive keys of the tile.
+    // Warp-striped view: warp w owns 32*ITEMS consecutive keys of the tile.
     KeyT key[ITEMS];
     uint32_t dig[ITEMS], rank[ITEMS];
-    const uint64_t wbase = (uint64_t)tile * Smem::TILE + (uint64_t)warp * (32 * ITEMS);
+    const int wofs = warp * (32 * ITEMS);
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
-        const uint64_t e = wbase + (uint64_t)i * 32 + lane;
-        key[i] = e < E ? keys_in[e] : ~(KeyT)0;  // tail: all-ones key, digit 255, last in order
+        key[i] = sm.keys[wofs + i * 32 + lane];
         dig[i] = digit_of(key[i], shift);
     }
     // Stable ranking inside the warp, items in (i, lane) order: the lanes
     // holding the same digit find each other through a per-warp mask word per
-    // digit in shared memory (atomicOr of the lane bit); the lowest such lane
-    // advances the warp's counter for that digit and clears the mask.
+    // digit (atomicOr of the lane bit); the lowest such lane advances the
+    // warp's counter for that digit and clears the mask.
     const unsigned lt = (1u << lane) - 1u;
     uint32_t* wh = sm.whist[warp];
     uint32_t* pm = sm.u.peers[warp];
@@ -194,8 +233,7 @@ k_downsweep(const KeyT* __restrict__ keys_in, const uint32_t* __restrict__ vals_
     for (int i = 0; i < ITEMS; ++i) {
         const uint32_t slot = sm.tile_start[dig[i]] + sm.whist[warp][dig[i]] + rank[i];
         sm.keys[slot] = key[i];
-        const uint64_t e = wbase + (uint64_t)i * 32 + lane;
-        sm.u.vals[slot] = e < E ? vals_in[e] : 0u;
+        sm.u.vals[slot] = sm.vals_raw[wofs + i * 32 + lane];
     }
     __syncthreads();
     // Runs of equal digits go to consecutive global positions (coalesced).
@@ -222,16 +260,26 @@ int launch_radix_sort(KeyT* keys0, uint32_t* vals0, KeyT* keys1, uint32_t* vals1
     KeyT* kb[2] = {keys0, keys1};
     uint32_t* vb[2] = {vals0, vals1};
     const uint64_t cells = tiles * RADIX;
+    const int smem = (int)sizeof(DownSmem<KeyT, ITEMS>);
+    // The dynamic shared-memory opt-in is per device; set it once for each.
+    static unsigned long long attr_set = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !(attr_set & (1ull << dev))) {
+        cudaFuncSetAttribute(k_downsweep<KeyT, ITEMS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem);
+        if (dev >= 0 && dev < 64) attr_set |= 1ull << dev;
+    }
     int launches = 0;
     for (int p = 0; p < passes; ++p) {
         const int write_keys = !(skip_last_keys && p == passes - 1);
         k_upsweep<KeyT, ITEMS><<<(unsigned)tiles, SORT_BLOCK, 0, s>>>(
-            kb[p & 1], (uint32_t)E, 8 * p, sc.tile_hist, (uint32_t)tiles);
+            kb[p & 1], (uint32_t)E, 8 * p, sc.tile_hist, (uint32_t)tiles, st);
         launches += 1 + launch_offsets(sc.tile_hist, (int64_t)cells, sc.offs, ~0ull, sc.total,
                                        sc.status + (size_t)p * sort_status_stride(E), st, s);
-        k_downsweep<KeyT, ITEMS><<<(unsigned)tiles, SORT_BLOCK, 0, s>>>(
+        k_downsweep<KeyT, ITEMS><<<(unsigned)tiles, SORT_BLOCK, smem, s>>>(
             kb[p & 1], vb[p & 1], kb[(p + 1) & 1], vb[(p + 1) & 1], (uint32_t)E, 8 * p, sc.offs,
-            (uint32_t)tiles, write_keys);
+            (uint32_t)tiles, write_keys, st);
         ++launches;
     }
     return launches;
