@@ -160,6 +160,63 @@ int ddm_set_profiling(ddm_ctx *ctx, int enable);
 int ddm_get_stats(const ddm_ctx *ctx, ddm_stats *out);
 
 /*
+ * Batched matching: `num` independent instances inst[0..num-1] (a HOST array
+ * of descriptors whose coordinate pointers are DEVICE memory), all with the
+ * same d, matched together in one pass of the pipeline.  The instances are
+ * concatenated on the device and the instance number becomes the high bits of
+ * the 64-bit sort key, so one sort, one scan, one count and one emission serve
+ * all of them, with no per-instance launches.  Instance b's pairs, with ids
+ * local to instance b and sorted lexicographically, occupy pairs[2*o[b] ..
+ * 2*o[b+1]) where o = inst_offsets, a HOST array of num + 1 values (o[0] = 0,
+ * o[num] = K).  `pairs` is DEVICE memory for 2 * cap int32; with pairs == NULL
+ * only the counts (inst_offsets and K) are computed.  Capacity rule as in
+ * ddm_match.  Limits: 0 <= num <= DDM_MAX_BATCH; the instances' regions
+ * together obey DDM_MAX_REGIONS.  Synchronous.
+ */
+#define DDM_MAX_BATCH (1 << 20)
+int ddm_match_batch(ddm_ctx *ctx, int num, const ddm_regions *inst, int32_t *pairs, uint64_t cap,
+                    uint64_t *inst_offsets, uint64_t *K_out);
+
+/*
+ * Served mode: a session keeps one simulation's extents RESIDENT on the device
+ * across timesteps, together with its own pipeline workspace (the sorted
+ * endpoint stream and rank records of the last step stay there), so a request
+ * for the next timestep moves no coordinates between host and device.
+ *
+ *   ddm_session_create   copies `initial` (DEVICE coordinate pointers) into
+ *                        session-owned device memory on `device`.
+ *   ddm_session_regions  a view of the resident coordinates (device pointers,
+ *                        valid until the session is destroyed).
+ *   ddm_session_drift    moves every extent by delta ~ N(0, sigma) per
+ *                        dimension (lo and hi by the same delta; rounding keeps
+ *                        lo <= hi); the draws are a counter-based SplitMix64
+ *                        stream (seed, step), reproducible bit for bit.
+ *   ddm_session_count    runs the pipeline up to the exact K (sort, sweep scan,
+ *                        counts, offsets) and keeps that state; returns K.
+ *   ddm_session_emit     after ddm_session_count: writes the K sorted pairs into
+ *                        `pairs` (DEVICE, 2 * cap int32) from the kept state,
+ *                        without sorting again.  K > cap -> DDM_ERR_CAPACITY.
+ *
+ * Between count and emit a caller can reserve exactly 8 K bytes of output
+ * (admission by memory).  Every call takes the CUDA stream to run on (NULL =
+ * legacy default stream) and is synchronous.  A session must not be used by
+ * two threads at once; different sessions may run concurrently on different
+ * streams.  The paper has no serving layer: dynamic extents are its future
+ * work (Section 6, "Conclusions"; Pan et al. 2011).
+ */
+typedef struct ddm_session ddm_session;
+int ddm_session_create(ddm_session **out, int device, const ddm_regions *initial,
+                       size_t mem_budget_bytes);
+int ddm_session_destroy(ddm_session *s);
+const ddm_regions *ddm_session_regions(const ddm_session *s);
+const char *ddm_session_last_error(const ddm_session *s);
+int ddm_session_drift(ddm_session *s, void *cuda_stream, uint64_t seed, uint64_t step,
+                      double sigma);
+int ddm_session_count(ddm_session *s, void *cuda_stream, uint64_t *K_out);
+int ddm_session_emit(ddm_session *s, void *cuda_stream, int32_t *pairs, uint64_t cap,
+                     uint64_t *K_out);
+
+/*
  * Diagnostic view of the sweep stages for dimension 0 (the sorted endpoint
  * list T of Algorithm 4 and the active-set sizes it maintains), for tests.
  * All outputs are DEVICE memory, E = 2(n+m) entries unless noted:

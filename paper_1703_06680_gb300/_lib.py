@@ -73,6 +73,14 @@ SIGNATURES = {
     "ddm_debug_sweep": (ctypes.c_int, [_P, _RP, _P, _P, _P, _P, _P]),
     "ddm_set_profiling": (ctypes.c_int, [_P, ctypes.c_int]),
     "ddm_count_noalloc": (ctypes.c_int, [_RP, _P, _U64P]),
+    "ddm_match_batch": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_uint64, _P, _U64P]),
+    "ddm_session_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _RP, ctypes.c_size_t]),
+    "ddm_session_destroy": (ctypes.c_int, [_P]),
+    "ddm_session_regions": (_RP, [_P]),
+    "ddm_session_last_error": (ctypes.c_char_p, [_P]),
+    "ddm_session_drift": (ctypes.c_int, [_P, _P, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double]),
+    "ddm_session_count": (ctypes.c_int, [_P, _P, _U64P]),
+    "ddm_session_emit": (ctypes.c_int, [_P, _P, _P, ctypes.c_uint64, _U64P]),
     "ddm_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(Stats)]),
 }
 
@@ -262,6 +270,36 @@ class Context:
         self._check(rc, K.value)
         return out[:K.value]
 
+    def match_batch(self, instances, cap: int | None = None, count_only: bool = False):
+        """ddm_match_batch over a list of (sub_lo, sub_hi, upd_lo, upd_hi) CUDA tensors.
+
+        Returns (pairs, inst_offsets): pairs is a (K, 2) int32 CUDA tensor whose rows
+        inst_offsets[b]:inst_offsets[b+1] are instance b's sorted pairs (local ids);
+        inst_offsets is a numpy uint64 array of len(instances) + 1.  With
+        count_only=True no pairs are written and pairs is None.
+        """
+        torch = _torch()
+        packs = [_pack_device(*inst) for inst in instances]
+        num = len(packs)
+        arr = (_Regions * max(num, 1))(*[p.s for p in packs])
+        offs = np.zeros(num + 1, np.uint64)
+        K = ctypes.c_uint64(0)
+        if count_only:
+            rc = self._lib.ddm_match_batch(self._h, num, ctypes.cast(arr, ctypes.c_void_p), None, 0,
+                                           ctypes.c_void_p(offs.ctypes.data), ctypes.byref(K))
+            self._check(rc, K.value)
+            return None, offs
+        if cap is None:
+            _, o = self.match_batch(instances, count_only=True)
+            cap = int(o[-1])
+        dev = instances[0][0].device if num else torch.device("cuda", self.device)
+        out = torch.empty((max(cap, 1), 2), dtype=torch.int32, device=dev)
+        rc = self._lib.ddm_match_batch(self._h, num, ctypes.cast(arr, ctypes.c_void_p),
+                                       ctypes.c_void_p(out.data_ptr()), cap,
+                                       ctypes.c_void_p(offs.ctypes.data), ctypes.byref(K))
+        self._check(rc, K.value)
+        return out[:K.value], offs
+
     def debug_sweep(self, sub_lo, sub_hi, upd_lo, upd_hi):
         """ddm_debug_sweep: (sorted_who, subset_size, updset_size, sub_count, upd_count)."""
         torch = _torch()
@@ -274,3 +312,84 @@ class Context:
         self._check(rc)
         self.stream.synchronize()
         return tuple(o[:k] for o, k in zip(outs, (E, E, E, n, m)))
+
+
+class Session:
+    """Resident state of one simulation (ddm_session_*): coordinates and pipeline
+    workspace stay on the device across timesteps."""
+
+    def __init__(self, sub_lo, sub_hi, upd_lo, upd_hi, device: int = 0, mem_budget: int = 0):
+        self._lib = load_library()
+        p = _pack_device(sub_lo, sub_hi, upd_lo, upd_hi)
+        self.d, self.n, self.m = p.s.d, p.s.n, p.s.m
+        self.device = device
+        h = ctypes.c_void_p()
+        rc = self._lib.ddm_session_create(ctypes.byref(h), device, p.ref, mem_budget)
+        if rc != DDM_OK:
+            raise DDMError(rc, "ddm_session_create failed")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.ddm_session_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, K=0):
+        if rc == DDM_OK:
+            return
+        msg = self._lib.ddm_session_last_error(self._h).decode(errors="replace")
+        if rc == DDM_ERR_CAPACITY:
+            raise CapacityError(rc, msg, int(K))
+        raise DDMError(rc, msg)
+
+    @staticmethod
+    def _stream(stream):
+        return ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+
+    def drift(self, seed: int, step: int, sigma: float, stream=None):
+        self._check(self._lib.ddm_session_drift(self._h, self._stream(stream), seed & (2**64 - 1),
+                                                step, float(sigma)))
+
+    def count(self, stream=None) -> int:
+        K = ctypes.c_uint64(0)
+        self._check(self._lib.ddm_session_count(self._h, self._stream(stream), ctypes.byref(K)))
+        return int(K.value)
+
+    def emit(self, out, stream=None) -> int:
+        """Writes the pairs of the last count() into `out` ((cap, 2) int32 CUDA tensor)."""
+        K = ctypes.c_uint64(0)
+        cap = out.shape[0]
+        rc = self._lib.ddm_session_emit(self._h, self._stream(stream),
+                                        ctypes.c_void_p(out.data_ptr() if cap else 0), cap,
+                                        ctypes.byref(K))
+        self._check(rc, K.value)
+        return int(K.value)
+
+    def coords(self):
+        """Copies of the resident coordinates as (d, count) float32 CUDA tensors."""
+        import torch
+        r = self._lib.ddm_session_regions(self._h).contents
+        out = []
+        for arr, count in ((r.sub_lo, self.n), (r.sub_hi, self.n), (r.upd_lo, self.m),
+                           (r.upd_hi, self.m)):
+            t = torch.empty((self.d, count), dtype=torch.float32, device=f"cuda:{self.device}")
+            for k in range(self.d):
+                if count:
+                    src = _DeviceView(arr[k], count)
+                    t[k].copy_(torch.as_tensor(src, device=f"cuda:{self.device}"))
+            out.append(t)
+        return out
+
+
+class _DeviceView:
+    """Minimal __cuda_array_interface__ over a device float32 pointer."""
+
+    def __init__(self, ptr, count):
+        self.__cuda_array_interface__ = {"shape": (count,), "typestr": "<f4",
+                                         "data": (int(ptr), True), "version": 3}

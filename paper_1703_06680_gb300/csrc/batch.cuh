@@ -1,0 +1,38 @@
+// a8 batched mode: interfaces.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace ddm {
+
+// Device copy of one instance's coordinate pointers (all dimensions).
+struct InstPtrs {
+    const float* sub_lo[DDM_MAX_DIMS];
+    const float* sub_hi[DDM_MAX_DIMS];
+    const float* upd_lo[DDM_MAX_DIMS];
+    const float* upd_hi[DDM_MAX_DIMS];
+};
+
+struct BatchArgs {
+    int d;
+    int num;                  // instances
+    int64_t n, m;             // totals
+    const InstPtrs* table;    // num entries (device)
+    const int64_t* n_base;    // num + 1 prefix sums of n_b (device)
+    const int64_t* m_base;    // num + 1 prefix sums of m_b (device)
+    float* sub_lo[DDM_MAX_DIMS];  // concatenated coordinates (device)
+    float* sub_hi[DDM_MAX_DIMS];
+    float* upd_lo[DDM_MAX_DIMS];
+    float* upd_hi[DDM_MAX_DIMS];
+};
+
+int launch_concat(const BatchArgs& b, cudaStream_t s);
+int launch_keybuild_batch(const BatchArgs& b, unsigned long long* keys, uint32_t* vals,
+                          DevStatus* st, cudaStream_t s);
+int launch_inst_offsets(const BatchArgs& b, const unsigned long long* off,
+                        unsigned long long* inst_off, cudaStream_t s);
+
+}  // namespace ddm

@@ -180,6 +180,16 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     return false;
 }
 
+// Instance of a global id in a batch: base[b] <= id < base[b + 1], base[0] = 0.
+__device__ __forceinline__ int inst_of(const int64_t* base, int num, int64_t id) {
+    int lo = 0, hi = num;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (base[mid] <= id) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
 __host__ __device__ __forceinline__ uint64_t ceil_div(uint64_t a, uint64_t b) {
     return (a + b - 1) / b;
 }

@@ -9,6 +9,8 @@
 #include <string>
 #include <vector>
 
+#include "batch.cuh"
+#include "drift.cuh"
 #include "emit.cuh"
 #include "sort.cuh"
 #include "sweep.cuh"
@@ -32,6 +34,7 @@ struct ddm_ctx {
     // counters and per-stage timing
     ddm_stats stats{};
     bool prof = false;
+    unsigned long long* last_inst_off = nullptr;  // device, batched calls
     cudaEvent_t ev[DDM_STAGES + 1] = {};
 };
 
@@ -132,10 +135,26 @@ struct DebugOut {
     uint32_t *who, *subset, *updset, *sub_cnt, *upd_cnt;
 };
 
-// Lays out every buffer of one plain call.  With base == nullptr only sizes.
+// One call's work: a plain instance (device coordinate pointers) or a batch
+// of instances (host array of descriptors, concatenated on the device).
+struct Job {
+    int d = 1;
+    int64_t n = 0, m = 0;
+    const ddm_regions* r = nullptr;     // plain: the instance
+    int num_inst = 0;                   // batch: number of instances (0 = plain)
+    const ddm_regions* inst = nullptr;  // batch: host descriptors
+};
+
+int ceil_log2(int64_t x) {
+    int b = 0;
+    while (((int64_t)1 << b) < x) ++b;
+    return b;
+}
+
+// Lays out every buffer of one call.  With base == nullptr only sizes.
 struct Plan {
     int64_t n, m, E;
-    int d;
+    int d, num_inst, passes;
     // zeroed region
     SortScratch sort;
     unsigned long long* scan_status;
@@ -159,18 +178,27 @@ struct Plan {
     unsigned long long lw_cap;
     uint8_t* flag;
     // the rest
-    uint32_t *keys0, *keys1, *vals0, *vals1;
+    void *keys0, *keys1;
+    uint32_t *vals0, *vals1;
     Records rec;
     uint32_t *cnt, *cnt_a, *upd_cnt, *big_list;
     unsigned long long* off;
     uint2 *subK, *updK;
+    // batch
+    InstPtrs* table;
+    int64_t *n_base, *m_base;
+    float* cat[4][DDM_MAX_DIMS];
+    unsigned long long* inst_off;
     size_t total;
 
-    void layout(char* base, int d_, int64_t n_, int64_t m_, Mode mode) {
-        d = d_; n = n_; m = m_; E = 2 * (n + m);
+    void layout(char* base, int d_, int64_t n_, int64_t m_, Mode mode, int num_inst_) {
+        d = d_; n = n_; m = m_; E = 2 * (n + m); num_inst = num_inst_;
+        const bool batch = num_inst > 0;
+        passes = batch ? (int)ceil_div(32 + ceil_log2(num_inst), RADIX_BITS) : 4;
+        const uint64_t stiles = batch ? sort_tiles<unsigned long long>(E) : sort_tiles<uint32_t>(E);
         Carve cv;
         cv.base = base;
-        sort.status = cv.take<unsigned long long>(4 * sort_status_stride(E));
+        sort.status = cv.take<unsigned long long>((size_t)passes * sort_status_stride(E));
         sort.total = cv.take<unsigned long long>(1);
         scan_status = cv.take<unsigned long long>(3 * (ceil_div(E, SCAN_TILE) + 1) + 1);
         off_status = cv.take<unsigned long long>(ceil_div(n, OFF_TILE) + 2);
@@ -191,10 +219,11 @@ struct Plan {
         lw = cv.take<uint2>(lw_cap);
         urank = cv.take<uint4>(window ? m : 0);
         flag = cv.take<uint8_t>(window ? n : 0);
-        sort.tile_hist = cv.take<uint32_t>(sort_tiles<uint32_t>(E) * RADIX);
-        sort.offs = cv.take<unsigned long long>(sort_tiles<uint32_t>(E) * RADIX + 1);
-        keys0 = cv.take<uint32_t>(E);
-        keys1 = cv.take<uint32_t>(E);
+        sort.tile_hist = cv.take<uint32_t>(stiles * RADIX);
+        sort.offs = cv.take<unsigned long long>(stiles * RADIX + 1);
+        const size_t ksz = batch ? 8 : 4;
+        keys0 = cv.take<char>(E * ksz);
+        keys1 = cv.take<char>(E * ksz);
         vals0 = cv.take<uint32_t>(E);
         vals1 = cv.take<uint32_t>(E);
         rec.s_lo = cv.take<uint4>(n);
@@ -213,6 +242,13 @@ struct Plan {
         off = cv.take<unsigned long long>(n + 1);
         subK = cv.take<uint2>(d > 1 ? (size_t)(d - 1) * n : 0);
         updK = cv.take<uint2>(d > 1 ? (size_t)(d - 1) * m : 0);
+        table = cv.take<InstPtrs>(num_inst);
+        n_base = cv.take<int64_t>(batch ? num_inst + 1 : 0);
+        m_base = cv.take<int64_t>(batch ? num_inst + 1 : 0);
+        for (int a = 0; a < 4; ++a)
+            for (int k = 0; k < DDM_MAX_DIMS; ++k)
+                cat[a][k] = cv.take<float>(batch && k < d ? (a < 2 ? n : m) : 0);
+        inst_off = cv.take<unsigned long long>(batch ? num_inst + 1 : 0);
         total = cv.off + 256;
     }
 };
@@ -223,31 +259,78 @@ int id_bits(int64_t m) {
     return b;
 }
 
-// Enqueues the whole pipeline for one instance whose coordinates are device
-// pointers.  Does not synchronize.
-int enqueue_plain(ddm_ctx* c, const ddm_regions* r, Mode mode, int32_t* pairs, uint64_t cap,
-                  const DebugOut* dbg) {
+// Which part of the pipeline to enqueue: everything, only the stages up to
+// and including the offsets scan (the exact K is then known), or only the
+// emission stages that follow, on the state the prefix left in the workspace.
+enum class Phase { All, Prefix, Suffix };
+
+// Enqueues the pipeline (or a phase of it) for one job.  Does not synchronize.
+int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
+            const DebugOut* dbg, Phase phase = Phase::All) {
     Plan pl;
-    pl.layout(nullptr, r->d, r->n, r->m, mode);
+    pl.layout(nullptr, job.d, job.n, job.m, mode, job.num_inst);
+    if (phase == Phase::Suffix && pl.total > c->ws_size)
+        return fail(c, DDM_ERR_INTERNAL, "emission phase without its prefix");
     int rc = ensure(c, &c->ws, &c->ws_size, pl.total);
     if (rc) return rc;
-    pl.layout(c->ws, r->d, r->n, r->m, mode);
+    pl.layout(c->ws, job.d, job.n, job.m, mode, job.num_inst);
     cudaStream_t s = c->stream;
-    CK(cudaMemsetAsync(c->dstat, 0, sizeof(DevStatus), s));
-    CK(cudaMemsetAsync(c->ws, 0, pl.zero_bytes, s));
-    c->stats.calls++;
-    mark(c, 0);
-    if (pl.E == 0) {
-        for (int k = 1; k <= DDM_STAGES; ++k) mark(c, k);
-        return DDM_OK;
+    const bool batch = job.num_inst > 0;
+    const bool do_prefix = phase != Phase::Suffix, do_suffix = phase != Phase::Prefix;
+    if (do_prefix) {
+        CK(cudaMemsetAsync(c->dstat, 0, sizeof(DevStatus), s));
+        CK(cudaMemsetAsync(c->ws, 0, pl.zero_bytes, s));
+        c->stats.calls++;
     }
     uint64_t& L = c->stats.launches;
-    L += launch_keybuild_d0(r->sub_lo[0], r->sub_hi[0], r->upd_lo[0], r->upd_hi[0], pl.n, pl.m,
-                            pl.keys0, pl.vals0, c->dstat, s);
-    mark(c, 1);
-    L += launch_radix_sort<uint32_t>(pl.keys0, pl.vals0, pl.keys1, pl.vals1, pl.E, 4, pl.sort,
-                                     true, c->dstat, s);
-    mark(c, 2);
+
+    // Coordinates of every dimension as device arrays over the job's ids.
+    DimPtrs dims{};
+    BatchArgs ba{};
+    if (batch) {
+        const int num = job.num_inst;
+        std::vector<InstPtrs> table(num);
+        std::vector<int64_t> nb(num + 1, 0), mb(num + 1, 0);
+        for (int b = 0; b < num; ++b) {
+            const ddm_regions& r = job.inst[b];
+            for (int k = 0; k < job.d; ++k) {
+                table[b].sub_lo[k] = r.sub_lo[k]; table[b].sub_hi[k] = r.sub_hi[k];
+                table[b].upd_lo[k] = r.upd_lo[k]; table[b].upd_hi[k] = r.upd_hi[k];
+            }
+            nb[b + 1] = nb[b] + r.n;
+            mb[b + 1] = mb[b] + r.m;
+        }
+        if (do_prefix) {
+            CK(cudaMemcpyAsync(pl.table, table.data(), num * sizeof(InstPtrs),
+                               cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(pl.n_base, nb.data(), (num + 1) * sizeof(int64_t),
+                               cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(pl.m_base, mb.data(), (num + 1) * sizeof(int64_t),
+                               cudaMemcpyHostToDevice, s));
+        }
+        ba.d = job.d; ba.num = num; ba.n = pl.n; ba.m = pl.m;
+        ba.table = pl.table; ba.n_base = pl.n_base; ba.m_base = pl.m_base;
+        for (int k = 0; k < job.d; ++k) {
+            ba.sub_lo[k] = pl.cat[0][k]; ba.sub_hi[k] = pl.cat[1][k];
+            ba.upd_lo[k] = pl.cat[2][k]; ba.upd_hi[k] = pl.cat[3][k];
+            dims.sub_lo[k] = pl.cat[0][k]; dims.sub_hi[k] = pl.cat[1][k];
+            dims.upd_lo[k] = pl.cat[2][k]; dims.upd_hi[k] = pl.cat[3][k];
+        }
+    } else {
+        for (int k = 0; k < job.d; ++k) {
+            dims.sub_lo[k] = job.r->sub_lo[k]; dims.sub_hi[k] = job.r->sub_hi[k];
+            dims.upd_lo[k] = job.r->upd_lo[k]; dims.upd_hi[k] = job.r->upd_hi[k];
+        }
+    }
+    if (pl.E == 0) {
+        if (do_prefix) {
+            for (int k = 0; k <= DDM_STAGES; ++k) mark(c, k);
+            if (batch) L += launch_inst_offsets(ba, pl.off, pl.inst_off, s);
+        }
+        c->last_inst_off = batch ? pl.inst_off : nullptr;
+        return DDM_OK;
+    }
+    uint32_t* vals_sorted = (pl.passes & 1) ? pl.vals1 : pl.vals0;
     Records rec = pl.rec;
     if (pl.window) {
         rec.windows = pl.windows;
@@ -260,23 +343,18 @@ int enqueue_plain(ddm_ctx* c, const ddm_regions* r, Mode mode, int32_t* pairs, u
         if (!rec.dbg_who || !rec.dbg_subset || !rec.dbg_updset)
             rec.dbg_who = rec.dbg_subset = rec.dbg_updset = nullptr;
     }
-    L += launch_sweep_scan(pl.vals0, pl.E, pl.n, pl.m, rec, pl.scan_status, c->dstat, s);
-    mark(c, 3);
-
     EmitArgs a{};
-    a.d = r->d; a.n = pl.n; a.m = pl.m;
-    for (int k = 0; k < r->d; ++k) {
-        a.dims.sub_lo[k] = r->sub_lo[k]; a.dims.sub_hi[k] = r->sub_hi[k];
-        a.dims.upd_lo[k] = r->upd_lo[k]; a.dims.upd_hi[k] = r->upd_hi[k];
-    }
+    a.d = job.d; a.n = pl.n; a.m = pl.m;
+    a.dims = dims;
     a.rec = rec;
     a.cnt = pl.cnt; a.off = pl.off; a.cnt_a = pl.cnt_a; a.cursor_b = pl.cursor_b;
     a.subK = pl.subK; a.updK = pl.updK;
     a.pairs = pairs; a.cap = cap;
     a.big_list = pl.big_list; a.big_count = pl.big_count;
     a.id_bits = id_bits(pl.m);
-    a.inst_sub_base = a.inst_upd_base = nullptr;
-    a.num_inst = 0;
+    a.inst_sub_base = batch ? pl.n_base : nullptr;
+    a.inst_upd_base = batch ? pl.m_base : nullptr;
+    a.num_inst = job.num_inst;
     a.flag = nullptr;
     a.num_flagged = pl.num_flagged;
     if (pl.window) {
@@ -291,9 +369,29 @@ int enqueue_plain(ddm_ctx* c, const ddm_regions* r, Mode mode, int32_t* pairs, u
         a.urank = pl.urank;
         a.lw_cap = pl.lw_cap;
     }
-    a.vals = pl.vals0;
-
-    if (r->d == 1) {
+    a.vals = vals_sorted;
+  if (do_prefix) {
+    mark(c, 0);
+    if (batch) {
+        L += launch_concat(ba, s);
+        L += launch_keybuild_batch(ba, (unsigned long long*)pl.keys0, pl.vals0, c->dstat, s);
+    } else {
+        L += launch_keybuild_d0(dims.sub_lo[0], dims.sub_hi[0], dims.upd_lo[0], dims.upd_hi[0],
+                                pl.n, pl.m, (uint32_t*)pl.keys0, pl.vals0, c->dstat, s);
+    }
+    mark(c, 1);
+    if (batch) {
+        L += launch_radix_sort<unsigned long long>(
+            (unsigned long long*)pl.keys0, pl.vals0, (unsigned long long*)pl.keys1, pl.vals1, pl.E,
+            pl.passes, pl.sort, true, c->dstat, s);
+    } else {
+        L += launch_radix_sort<uint32_t>((uint32_t*)pl.keys0, pl.vals0, (uint32_t*)pl.keys1,
+                                         pl.vals1, pl.E, pl.passes, pl.sort, true, c->dstat, s);
+    }
+    mark(c, 2);
+    L += launch_sweep_scan(vals_sorted, pl.E, pl.n, pl.m, rec, pl.scan_status, c->dstat, s);
+    mark(c, 3);
+    if (job.d == 1) {
         L += launch_rank_count(rec, pl.n, pl.m, pl.cnt, dbg ? dbg->upd_cnt : nullptr, c->dstat, s);
     } else {
         L += launch_permute_keys(a, c->dstat, s);
@@ -302,9 +400,13 @@ int enqueue_plain(ddm_ctx* c, const ddm_regions* r, Mode mode, int32_t* pairs, u
     mark(c, 4);
     if (dbg && dbg->sub_cnt && pl.n > 0)
         CK(cudaMemcpyAsync(dbg->sub_cnt, pl.cnt, pl.n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
-    L += launch_offsets(pl.cnt, pl.n, pl.off, mode == Mode::Match ? cap : ~0ull,
+    L += launch_offsets(pl.cnt, pl.n, pl.off,
+                        mode == Mode::Match && phase == Phase::All ? cap : ~0ull,
                         &c->dstat->K, pl.off_status, c->dstat, s);
+    if (batch) L += launch_inst_offsets(ba, pl.off, pl.inst_off, s);
     mark(c, 5);
+  }
+  if (do_suffix) {
     if (pl.window) {
         L += launch_window_sizes(a, c->dstat, s);
         L += launch_offsets(pl.lw_size, pl.num_win, pl.lw_off, ~0ull, pl.lw_total,
@@ -317,8 +419,17 @@ int enqueue_plain(ddm_ctx* c, const ddm_regions* r, Mode mode, int32_t* pairs, u
     if (mode == Mode::Match) L += launch_segment_sort(a, c->dstat, s);
     mark(c, 7);
     mark(c, 8);
+  }
     CK(cudaGetLastError());
+    c->last_inst_off = batch ? pl.inst_off : nullptr;
     return DDM_OK;
+}
+
+int enqueue_plain(ddm_ctx* c, const ddm_regions* r, Mode mode, int32_t* pairs, uint64_t cap,
+                  const DebugOut* dbg) {
+    Job job;
+    job.d = r->d; job.n = r->n; job.m = r->m; job.r = r;
+    return enqueue(c, job, mode, pairs, cap, dbg);
 }
 
 // Reads the device status and maps it to a return code.
@@ -470,9 +581,11 @@ int ddm_match_host(ddm_ctx* c, const ddm_regions* r, int32_t* pairs, uint64_t ca
     dr.sub_hi = &dp[d];
     dr.upd_lo = &dp[2 * d];
     dr.upd_hi = &dp[3 * d];
-    // Count first, so that the device output buffer can be sized to K.
+    // Run the pipeline up to the exact K, size the device output, then emit.
+    Job job;
+    job.d = dr.d; job.n = dr.n; job.m = dr.m; job.r = &dr;
     uint64_t K = 0;
-    rc = enqueue_plain(c, &dr, Mode::Count, nullptr, 0, nullptr);
+    rc = enqueue(c, job, Mode::Match, nullptr, 0, nullptr, Phase::Prefix);
     if (rc) return rc;
     rc = finish(c, &K);
     if (rc) return rc;
@@ -483,9 +596,183 @@ int ddm_match_host(ddm_ctx* c, const ddm_regions* r, int32_t* pairs, uint64_t ca
     rc = ensure(c, &c->out, &c->out_size, 2 * K * sizeof(int32_t));
     if (rc) return rc;
     int32_t* dpairs = reinterpret_cast<int32_t*>(c->out);
-    rc = enqueue_plain(c, &dr, Mode::Match, dpairs, K, nullptr);
+    rc = enqueue(c, job, Mode::Match, dpairs, K, nullptr, Phase::Suffix);
     if (rc) return rc;
     CK(cudaMemcpyAsync(pairs, dpairs, 2 * K * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    return finish(c, K_out);
+}
+
+int ddm_match_batch(ddm_ctx* c, int num, const ddm_regions* inst, int32_t* pairs, uint64_t cap,
+                    uint64_t* inst_offsets, uint64_t* K_out) {
+    if (!c) return DDM_ERR_INVALID;
+    if (num < 0 || num > DDM_MAX_BATCH) return fail(c, DDM_ERR_INVALID, "num out of range");
+    if (!inst_offsets) return fail(c, DDM_ERR_INVALID, "inst_offsets is NULL");
+    if (num > 0 && !inst) return fail(c, DDM_ERR_INVALID, "inst is NULL");
+    Job job;
+    job.num_inst = num;
+    job.inst = inst;
+    job.d = num > 0 ? inst[0].d : 1;
+    for (int b = 0; b < num; ++b) {
+        int rc = check_regions(c, &inst[b]);
+        if (rc) return rc;
+        if (inst[b].d != job.d) return fail(c, DDM_ERR_INVALID, "instances differ in d");
+        job.n += inst[b].n;
+        job.m += inst[b].m;
+        if (job.n + job.m > DDM_MAX_REGIONS)
+            return fail(c, DDM_ERR_INVALID, "the instances together exceed DDM_MAX_REGIONS");
+    }
+    inst_offsets[0] = 0;
+    if (num == 0) {
+        if (K_out) *K_out = 0;
+        return DDM_OK;
+    }
+    DeviceGuard g(c->device);
+    const Mode mode = pairs ? Mode::Match : Mode::Count;
+    int rc = enqueue(c, job, mode, pairs, pairs ? cap : 0, nullptr);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(inst_offsets, c->last_inst_off, (num + 1) * sizeof(uint64_t),
+                       cudaMemcpyDeviceToHost, c->stream));
+    return finish(c, K_out);
+}
+
+}  // extern "C"
+
+struct ddm_session {
+    ddm_ctx* ctx = nullptr;
+    float* coords = nullptr;  // device: sub_lo, sub_hi (d x n each), upd_lo, upd_hi (d x m)
+    const float* ptrs[4][DDM_MAX_DIMS] = {};
+    ddm_regions regions{};
+    bool counted = false;     // a pipeline prefix is held in the workspace
+    uint64_t K = 0;
+};
+
+namespace {
+
+Job session_job(const ddm_session* s) {
+    Job job;
+    job.d = s->regions.d; job.n = s->regions.n; job.m = s->regions.m;
+    job.r = &s->regions;
+    return job;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ddm_session_create(ddm_session** out, int device, const ddm_regions* initial,
+                       size_t mem_budget_bytes) {
+    if (!out) return DDM_ERR_INVALID;
+    *out = nullptr;
+    ddm_ctx* c = nullptr;
+    int rc = ddm_create(&c, device, nullptr, mem_budget_bytes);
+    if (rc) return rc;
+    rc = check_regions(c, initial);
+    if (rc) { ddm_destroy(c); return rc; }
+    DeviceGuard g(device);
+    ddm_session* s = new ddm_session();
+    s->ctx = c;
+    const int d = initial->d;
+    const int64_t n = initial->n, m = initial->m;
+    const size_t floats = (size_t)2 * d * (n + m);
+    if (floats > 0 && cudaMalloc(&s->coords, floats * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        ddm_destroy(c);
+        delete s;
+        return DDM_ERR_NOMEM;
+    }
+    const float* const* src[4] = {initial->sub_lo, initial->sub_hi, initial->upd_lo, initial->upd_hi};
+    float* p = s->coords;
+    for (int a = 0; a < 4; ++a) {
+        const int64_t cnt = a < 2 ? n : m;
+        for (int k = 0; k < d; ++k) {
+            if (cnt > 0 && cudaMemcpy(p, src[a][k], cnt * sizeof(float),
+                                      cudaMemcpyDeviceToDevice) != cudaSuccess) {
+                cudaGetLastError();
+                ddm_session_destroy(s);
+                return DDM_ERR_CUDA;
+            }
+            s->ptrs[a][k] = p;
+            p += cnt;
+        }
+    }
+    s->regions.d = d;
+    s->regions.n = n;
+    s->regions.m = m;
+    s->regions.sub_lo = s->ptrs[0];
+    s->regions.sub_hi = s->ptrs[1];
+    s->regions.upd_lo = s->ptrs[2];
+    s->regions.upd_hi = s->ptrs[3];
+    *out = s;
+    return DDM_OK;
+}
+
+int ddm_session_destroy(ddm_session* s) {
+    if (!s) return DDM_OK;
+    if (s->ctx) {
+        DeviceGuard g(s->ctx->device);
+        if (s->coords) cudaFree(s->coords);  // every session call is synchronous
+        ddm_destroy(s->ctx);
+    }
+    delete s;
+    return DDM_OK;
+}
+
+const ddm_regions* ddm_session_regions(const ddm_session* s) { return s ? &s->regions : nullptr; }
+
+const char* ddm_session_last_error(const ddm_session* s) {
+    return s && s->ctx ? s->ctx->err.c_str() : "null session";
+}
+
+int ddm_session_drift(ddm_session* s, void* stream, uint64_t seed, uint64_t step, double sigma) {
+    if (!s) return DDM_ERR_INVALID;
+    ddm_ctx* c = s->ctx;
+    DeviceGuard g(c->device);
+    c->stream = reinterpret_cast<cudaStream_t>(stream);
+    DriftArgs a{};
+    a.d = s->regions.d; a.n = s->regions.n; a.m = s->regions.m;
+    for (int k = 0; k < a.d; ++k) {
+        a.sub_lo[k] = const_cast<float*>(s->ptrs[0][k]);
+        a.sub_hi[k] = const_cast<float*>(s->ptrs[1][k]);
+        a.upd_lo[k] = const_cast<float*>(s->ptrs[2][k]);
+        a.upd_hi[k] = const_cast<float*>(s->ptrs[3][k]);
+    }
+    a.seed = seed; a.step = step; a.sigma = sigma;
+    c->stats.launches += launch_drift(a, c->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->stream));
+    s->counted = false;
+    return DDM_OK;
+}
+
+int ddm_session_count(ddm_session* s, void* stream, uint64_t* K_out) {
+    if (!s) return DDM_ERR_INVALID;
+    ddm_ctx* c = s->ctx;
+    DeviceGuard g(c->device);
+    c->stream = reinterpret_cast<cudaStream_t>(stream);
+    s->counted = false;
+    int rc = enqueue(c, session_job(s), Mode::Match, nullptr, 0, nullptr, Phase::Prefix);
+    if (rc) return rc;
+    uint64_t K = 0;
+    rc = finish(c, &K);
+    if (rc) return rc;
+    s->K = K;
+    s->counted = true;
+    if (K_out) *K_out = K;
+    return DDM_OK;
+}
+
+int ddm_session_emit(ddm_session* s, void* stream, int32_t* pairs, uint64_t cap, uint64_t* K_out) {
+    if (!s) return DDM_ERR_INVALID;
+    ddm_ctx* c = s->ctx;
+    if (!s->counted) return fail(c, DDM_ERR_INVALID, "ddm_session_emit needs ddm_session_count first");
+    if (K_out) *K_out = s->K;
+    if (s->K > cap) return fail(c, DDM_ERR_CAPACITY, "output capacity too small");
+    if (!pairs && s->K > 0) return fail(c, DDM_ERR_INVALID, "pairs is NULL");
+    DeviceGuard g(c->device);
+    c->stream = reinterpret_cast<cudaStream_t>(stream);
+    s->counted = false;  // the emission consumes the kept state
+    int rc = enqueue(c, session_job(s), Mode::Match, pairs, cap, nullptr, Phase::Suffix);
+    if (rc) return rc;
     return finish(c, K_out);
 }
 

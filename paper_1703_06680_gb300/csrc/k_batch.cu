@@ -1,0 +1,93 @@
+// a8: batched matching of many independent instances in one pipeline pass.
+//
+// The instances are concatenated on the device (subscriptions of all
+// instances first, then all updates, each instance's extents contiguous, ids
+// made global by the instance base).  The dimension-0 sort key of an endpoint
+// is (instance << 32) | key(coordinate): one LSD sort then groups the stream
+// by instance and orders each instance's endpoints exactly as a plain call
+// would, lowers before uppers at equal coordinates.  Stream positions of
+// different instances never interleave, so the sweep scan, the rank counts
+// and the emission need no segment flags: every count at a position of
+// instance b already includes all of instances 0..b-1, and ranges such as
+// upd_order[A_i .. B_i) stay inside the instance.  The emission writes ids
+// local to the instance.
+#include "batch.cuh"
+
+namespace ddm {
+
+// Gather every instance's coordinates into the concatenated arrays.
+__global__ void k_concat(BatchArgs b) {
+    const int64_t R = b.n + b.m;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < R;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const bool upd = r >= b.n;
+        const int64_t g = upd ? r - b.n : r;
+        const int inst = inst_of(upd ? b.m_base : b.n_base, b.num, g);
+        const int64_t local = g - (upd ? b.m_base[inst] : b.n_base[inst]);
+        const InstPtrs& ip = b.table[inst];
+        for (int k = 0; k < b.d; ++k) {
+            if (upd) {
+                b.upd_lo[k][g] = ip.upd_lo[k][local];
+                b.upd_hi[k][g] = ip.upd_hi[k][local];
+            } else {
+                b.sub_lo[k][g] = ip.sub_lo[k][local];
+                b.sub_hi[k][g] = ip.sub_hi[k][local];
+            }
+        }
+    }
+}
+
+// Instance-tagged dimension-0 keys in [S lo | U lo | S hi | U hi] layout.
+__global__ void k_keybuild_batch(BatchArgs b, unsigned long long* __restrict__ keys,
+                                 uint32_t* __restrict__ vals, DevStatus* st) {
+    const int64_t R = b.n + b.m;
+    bool bad = false;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < R;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const bool upd = r >= b.n;
+        const int64_t id = upd ? r - b.n : r;
+        const int inst = inst_of(upd ? b.m_base : b.n_base, b.num, id);
+        const float lo = upd ? b.upd_lo[0][id] : b.sub_lo[0][id];
+        const float hi = upd ? b.upd_hi[0][id] : b.sub_hi[0][id];
+        bad |= is_nan_bits(lo) || is_nan_bits(hi) || !(lo <= hi);
+        const unsigned long long tag = (unsigned long long)inst << 32;
+        keys[r] = tag | float_key(lo);
+        keys[R + r] = tag | float_key(hi);
+        vals[r] = payload(upd ? KIND_ULO : KIND_SLO, (uint32_t)id);
+        vals[R + r] = payload(upd ? KIND_UHI : KIND_SHI, (uint32_t)id);
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) raise_error(st, DDM_ERR_INVALID, 15);
+}
+
+// inst_off[b] = first output pair of instance b = off[n_base[b]].
+__global__ void k_inst_offsets(BatchArgs b, const unsigned long long* __restrict__ off,
+                               unsigned long long* __restrict__ inst_off) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= b.num; i += gridDim.x * blockDim.x)
+        inst_off[i] = b.n == 0 ? 0ull : off[b.n_base[i]];  // off[] exists only when n > 0
+}
+
+static unsigned grid_for(uint64_t items) {
+    const uint64_t g = ceil_div(items, 256ull * 4);
+    return (unsigned)(g < 1 ? 1 : (g > 152 * 16 ? 152 * 16 : g));
+}
+
+int launch_concat(const BatchArgs& b, cudaStream_t s) {
+    if (b.n + b.m == 0) return 0;
+    k_concat<<<grid_for(b.n + b.m), 256, 0, s>>>(b);
+    return 1;
+}
+
+int launch_keybuild_batch(const BatchArgs& b, unsigned long long* keys, uint32_t* vals,
+                          DevStatus* st, cudaStream_t s) {
+    if (b.n + b.m == 0) return 0;
+    k_keybuild_batch<<<grid_for(b.n + b.m), 256, 0, s>>>(b, keys, vals, st);
+    return 1;
+}
+
+int launch_inst_offsets(const BatchArgs& b, const unsigned long long* off,
+                        unsigned long long* inst_off, cudaStream_t s) {
+    k_inst_offsets<<<grid_for(b.num + 1), 256, 0, s>>>(b, off, inst_off);
+    return 1;
+}
+
+}  // namespace ddm

@@ -27,15 +27,6 @@ constexpr int WARP_SORT_MAX = 512;
 constexpr int BIG_BLOCK = 256;
 constexpr int BIG_ITEMS = 4;
 
-__device__ __forceinline__ int find_inst(const int64_t* base, int num, int64_t id) {
-    int lo = 0, hi = num;  // base[0] = 0 <= id < base[num]
-    while (hi - lo > 1) {
-        int mid = (lo + hi) >> 1;
-        if (base[mid] <= id) lo = mid; else hi = mid;
-    }
-    return lo;
-}
-
 // ---------------------------------------------------------------------------
 // a7 set-up: keys of dims 1..d-1 in rank order, with validation.
 // ---------------------------------------------------------------------------
@@ -122,7 +113,7 @@ __global__ void __launch_bounds__(EMIT_BLOCK) k_class_a(EmitArgs a, DevStatus* s
         unsigned long long base = WRITE ? a.off[i] : 0ull;
         int32_t out_i = (int32_t)i, sub_off_j = 0;
         if (WRITE && a.inst_sub_base) {
-            const int b = find_inst(a.inst_sub_base, a.num_inst, i);
+            const int b = inst_of(a.inst_sub_base, a.num_inst, i);
             out_i = (int32_t)(i - a.inst_sub_base[b]);
             sub_off_j = (int32_t)a.inst_upd_base[b];
         }
@@ -165,7 +156,7 @@ __global__ void __launch_bounds__(EMIT_BLOCK) k_class_b(EmitArgs a, DevStatus* s
         int32_t out_j = (int32_t)j;
         int64_t sub_base = 0;
         if (WRITE && a.inst_upd_base) {
-            const int b = find_inst(a.inst_upd_base, a.num_inst, j);
+            const int b = inst_of(a.inst_upd_base, a.num_inst, j);
             out_j = (int32_t)(j - a.inst_upd_base[b]);
             sub_base = a.inst_sub_base[b];
         }
@@ -353,7 +344,7 @@ __global__ void __launch_bounds__(BIG_BLOCK) k_segsort_big(EmitArgs a, DevStatus
         // Result is in column (passes odd ? 0 : 1); move it to column 1 and
         // restore the subscription ids in column 0.
         int32_t out_i = (int32_t)i;
-        if (a.inst_sub_base) out_i = (int32_t)(i - a.inst_sub_base[find_inst(a.inst_sub_base, a.num_inst, i)]);
+        if (a.inst_sub_base) out_i = (int32_t)(i - a.inst_sub_base[inst_of(a.inst_sub_base, a.num_inst, i)]);
         for (uint32_t k = tid; k < c; k += BIG_BLOCK) {
             if (passes & 1) seg[2 * k + 1] = seg[2 * k];
             seg[2 * k] = out_i;

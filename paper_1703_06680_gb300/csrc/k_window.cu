@@ -203,7 +203,13 @@ __global__ void __launch_bounds__(WIN_BLOCK) k_emit_window(EmitArgs a, DevStatus
     for (uint32_t k = warp; k < ns; k += WIN_BLOCK / 32) {
         const uint32_t pl = s_lo[k], ph = s_hi[k];
         if (ph - pl > LONG_SPAN) continue;
-        const int32_t i = (int32_t)s_id[k];
+        int32_t i = (int32_t)s_id[k];
+        uint32_t j_base = 0;  // batched: ids are written local to the instance
+        if (a.inst_sub_base) {
+            const int b = inst_of(a.inst_sub_base, a.num_inst, i);
+            i -= (int32_t)a.inst_sub_base[b];
+            j_base = (uint32_t)a.inst_upd_base[b];
+        }
         int2* seg = reinterpret_cast<int2*>(a.pairs) + s_off[k];
         const uint32_t c = s_cnt[k];
         uint32_t running = 0;
@@ -212,7 +218,7 @@ __global__ void __launch_bounds__(WIN_BLOCK) k_emit_window(EmitArgs a, DevStatus
             const bool pass = (uint32_t)kv < ph && spay[kk] > pl;
             const unsigned bal = __ballot_sync(0xffffffffu, pass);
             const uint32_t r = running + __popc(bal & lt);
-            if (pass && r < c) seg[r] = make_int2(i, (int32_t)(kv >> 32));
+            if (pass && r < c) seg[r] = make_int2(i, (int32_t)((uint32_t)(kv >> 32) - j_base));
             running += __popc(bal);
         }
         if (lane == 0 && running != c) raise_error(st, DDM_ERR_INTERNAL, 12);

@@ -1,0 +1,81 @@
+"""Batched matching (one pipeline pass over many instances) against the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.gpu_util import to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_1703_06680_gb300 as ddm
+    ddm.build_library()
+    c = ddm.Context(0)
+    yield c
+    c.close()
+
+
+def check_batch(ctx, regs, sample=None):
+    insts = [to_dev(r) for r in regs]
+    pairs, offs = ctx.match_batch(insts)
+    pairs = pairs.cpu().numpy()
+    assert offs[0] == 0 and offs[-1] == len(pairs)
+    assert np.all(np.diff(offs.astype(np.int64)) >= 0)
+    idx = range(len(regs)) if sample is None else sample
+    for b in idx:
+        want = oracle.sbm(regs[b])
+        got = pairs[int(offs[b]):int(offs[b + 1])]
+        assert np.array_equal(got, want), b
+    _, offs2 = ctx.match_batch(insts, count_only=True)
+    assert np.array_equal(offs, offs2)
+    return pairs, offs
+
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_batch_mixed_sizes(ctx, d):
+    rng = np.random.default_rng(100 + d)
+    regs = []
+    for b in range(150):
+        n, m = int(rng.integers(0, 400)), int(rng.integers(0, 400))
+        N = max(n + m, 1)
+        regs.append(synth.make_regions(d, n, m, synth.side_for(float(rng.choice([0.01, 1, 100])),
+                                                               N, d), 1000 * d + b))
+    check_batch(ctx, regs)
+
+
+def test_batch_dense_ties(ctx):
+    from tests.helpers import tiny_grid_instance
+    rng = np.random.default_rng(7)
+    regs = [tiny_grid_instance(rng, 1 + b % 3, int(rng.integers(0, 50)), int(rng.integers(0, 50)))
+            for b in range(99)]
+    # all instances of one call share d: split by d
+    for d in (1, 2, 3):
+        check_batch(ctx, [r for r in regs if r.d == d])
+
+
+def test_batch_equals_plain_calls(ctx):
+    regs = synth.batch_instances(num=64, d=2)
+    pairs, offs = check_batch(ctx, regs, sample=range(0, 64, 8))
+    for b in range(64):
+        assert ctx.count(*to_dev(regs[b])) == int(offs[b + 1] - offs[b])
+
+
+def test_batch_capacity(ctx):
+    import paper_1703_06680_gb300 as ddm
+    regs = [synth.small_1d(), synth.small_1d(1)]
+    insts = [to_dev(r) for r in regs]
+    _, offs = ctx.match_batch(insts, count_only=True)
+    with pytest.raises(ddm.CapacityError) as e:
+        ctx.match_batch(insts, cap=int(offs[-1]) - 1)
+    assert e.value.K == int(offs[-1])
+
+
+def test_batch_full_size_sampled(ctx):
+    # the 4096-instance workload (d=2, alpha=1, N_i log-uniform in [1e2, 1e5])
+    regs = synth.batch_instances(num=4096, d=2)
+    rng = np.random.default_rng(4096)
+    sample = sorted(rng.choice(4096, size=24, replace=False).tolist())
+    check_batch(ctx, regs, sample=sample)

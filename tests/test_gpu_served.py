@@ -1,0 +1,136 @@
+"""Served mode: resident sessions, device drift, count/admit/emit, continuous batching.
+
+The drift kernel is checked bit for bit against the workload generator's own
+implementation of the same counter-based definition; matching results after
+drift are checked against the oracle run on the generator's drifted
+coordinates (never on coordinates read back from the GPU); and every result
+computed inside the concurrent mix must equal the one computed alone.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.gpu_util import to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ddm():
+    import paper_1703_06680_gb300 as ddm
+    ddm.build_library()
+    return ddm
+
+
+def small_sims(count=8, seed=77):
+    rng = np.random.default_rng(seed)
+    sims = []
+    for k in range(count):
+        N = int(rng.integers(2_000, 60_000))
+        d = 1 + k % 3
+        alpha = (0.01, 1.0, 100.0)[k % 3] if d == 1 else (1.0, 100.0)[k % 2]
+        side = synth.side_for(alpha, N, d)
+        sims.append({"reg": synth.make_regions(d, N // 2, N - N // 2, side, 9000 + k),
+                     "seed": 1234 + k, "sigma": 0.1 * side})
+    return sims
+
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_drift_kernel_matches_generator(ddm, d):
+    reg = synth.make_regions(d, 3001, 2999, 2000.0, 31 + d)
+    sess = ddm.Session(*to_dev(reg))
+    host = reg
+    for step in range(3):
+        sess.drift(555, step, 200.0)
+        host = synth.drift(host, 555, step, 200.0)
+        got = [t.cpu().numpy() for t in sess.coords()]
+        for g, w in zip(got, (host.sub_lo, host.sub_hi, host.upd_lo, host.upd_hi)):
+            assert np.array_equal(g.view(np.uint32), w.view(np.uint32))
+    sess.close()
+
+
+def test_session_count_emit_matches_oracle(ddm):
+    import torch
+    for sim in small_sims(4, seed=5):
+        sess = ddm.Session(*to_dev(sim["reg"]))
+        host = sim["reg"]
+        for step in range(2):
+            sess.drift(sim["seed"], step, sim["sigma"])
+            host = synth.drift(host, sim["seed"], step, sim["sigma"])
+            want = oracle.sbm(host)
+            K = sess.count()
+            assert K == len(want)
+            out = torch.empty((K + 3, 2), dtype=torch.int32, device="cuda:0")
+            assert sess.emit(out) == K
+            assert np.array_equal(out[:K].cpu().numpy(), want)
+        sess.close()
+
+
+def test_emit_needs_count_and_capacity(ddm):
+    import torch
+    reg = synth.small_1d()
+    sess = ddm.Session(*to_dev(reg))
+    out = torch.empty((10, 2), dtype=torch.int32, device="cuda:0")
+    with pytest.raises(ddm.DDMError):
+        sess.emit(out)
+    K = sess.count()
+    with pytest.raises(ddm.CapacityError) as e:
+        sess.emit(out[:K - 1] if K > 1 else out[:0])
+    assert e.value.K == K
+    sess.close()
+
+
+def run_alone(ddm, sims, steps):
+    import torch
+    res = {}
+    for k, sim in enumerate(sims):
+        sess = ddm.Session(*to_dev(sim["reg"]))
+        for step in range(steps):
+            sess.drift(sim["seed"], step, sim["sigma"])
+            K = sess.count()
+            out = torch.empty((max(K, 1), 2), dtype=torch.int32, device="cuda:0")
+            sess.emit(out[:K])
+            res[(k, step)] = out[:K].cpu().numpy()
+        sess.close()
+    return res
+
+
+@pytest.mark.parametrize("budget", [4 << 30, None])
+def test_mix_equals_alone(ddm, budget):
+    from paper_1703_06680_gb300.serve import Server, Simulation
+    sims = small_sims(8)
+    steps = 3
+    alone = run_alone(ddm, sims, steps)
+    if budget is None:  # tight budget: admission must make requests wait
+        budget = 8 * max(len(v) for v in alone.values())
+    objs = [Simulation(k, to_dev(s["reg"]), s["seed"], s["sigma"]) for k, s in enumerate(sims)]
+    server = Server(objs, slots=4, out_budget_bytes=budget)
+    reqs = [server.submit(k, keep_pairs=True) for step in range(steps) for k in range(len(sims))]
+    for r in reqs:
+        assert r.done.wait(120)
+    server.close()
+    for r in reqs:
+        assert r.error is None, r.error
+        assert np.array_equal(r.pairs, alone[(r.sim, r.step)]), (r.sim, r.step)
+    for o in objs:
+        o.close()
+
+
+def test_mix_matches_oracle(ddm):
+    from paper_1703_06680_gb300.serve import Server, Simulation
+    sims = small_sims(6, seed=3)
+    objs = [Simulation(k, to_dev(s["reg"]), s["seed"], s["sigma"]) for k, s in enumerate(sims)]
+    server = Server(objs, slots=3)
+    reqs = [server.submit(k, keep_pairs=True) for _ in range(2) for k in range(len(sims))]
+    for r in reqs:
+        assert r.done.wait(120)
+    server.close()
+    hosts = {}
+    for r in sorted(reqs, key=lambda q: (q.sim, q.step)):
+        s = sims[r.sim]
+        prev = hosts.get(r.sim, s["reg"])
+        hosts[r.sim] = synth.drift(prev, s["seed"], r.step, s["sigma"])
+        assert np.array_equal(r.pairs, oracle.sbm(hosts[r.sim])), (r.sim, r.step)
+    for o in objs:
+        o.close()
