@@ -392,4 +392,4 @@ class _DeviceView:
 
     def __init__(self, ptr, count):
         self.__cuda_array_interface__ = {"shape": (count,), "typestr": "<f4",
-                                         "data": (int(ptr), True), "version": 3}
+                                         "data": (int(ptr), False), "version": 3}
