@@ -47,6 +47,8 @@ def parse_args():
     ap.add_argument("--alpha", type=float, default=100.0)
     ap.add_argument("--N", type=int, default=1_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
 
@@ -158,6 +160,134 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def bench_batched(ctx, dev, steps: int = 3):
+    """4096 independent instances (d=2, alpha=1, N_i log-uniform in [1e2, 1e5]) in one
+    ddm_match_batch call, against 4096 plain ddm_match calls on the same stream."""
+    import torch
+    regs = synth.batch_instances(num=4096, d=2)
+    insts = [[torch.from_numpy(a).to(dev) for a in (r.sub_lo, r.sub_hi, r.upd_lo, r.upd_hi)]
+             for r in regs]
+    pack = ctx.pack_batch(insts)
+    K, offs = ctx.match_batch_packed(pack)
+    out = torch.empty((max(K, 1), 2), dtype=torch.int32, device=dev)
+    ctx.match_batch_packed(pack, out[:K])
+    stream = torch.cuda.current_stream(dev)
+    gpu_ms, wall = [], []
+    for _ in range(steps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        ctx.match_batch_packed(pack, out[:K], offs)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        wall.append(time.perf_counter() - t0)
+        gpu_ms.append(e0.elapsed_time(e1))
+    packs = [ctx.pack(*i) for i in insts]
+    views = [out[int(offs[b]):int(offs[b + 1])] for b in range(len(insts))]
+    for b in range(len(insts)):
+        ctx.match_packed(packs[b], views[b])
+    torch.cuda.synchronize()
+    plain = []
+    for _ in range(2):
+        t0 = time.perf_counter()
+        for b in range(len(insts)):
+            ctx.match_packed(packs[b], views[b])
+        torch.cuda.synchronize()
+        plain.append(time.perf_counter() - t0)
+    bw, pw = min(wall), min(plain)
+    return {"workload": "4096 instances, d=2, alpha=1, N_i log-uniform in [1e2, 1e5]",
+            "regions": int(sum(r.n + r.m for r in regs)), "K": K,
+            "batched_gpu_ms": min(gpu_ms), "batched_wall_ms": 1e3 * bw,
+            "batched_pairs_per_s": K / bw, "plain_wall_ms": 1e3 * pw, "plain_pairs_per_s": K / pw,
+            "speedup_vs_plain": pw / bw}
+
+
+def bench_served(dev, requests: int = 96, slots: int = 4, load: float = 0.8):
+    """64 simulations (N log-uniform in [1e3, 1e6], d and alpha uniform), drift between
+    timesteps, Poisson arrivals at `load` x the plain path's measured capacity."""
+    import torch
+
+    from paper_1703_06680_gb300.serve import Server, Simulation, latency_summary, run_plain
+    cfg = synth.served_simulations(64)
+    regs = [synth.simulation_regions(c) for c in cfg]
+    sig = [0.1 * synth.side_for(c["alpha"], c["N"], c["d"]) for c in cfg]
+
+    def make_sims():
+        return [Simulation(k, [torch.from_numpy(a).to(dev) for a in
+                               (r.sub_lo, r.sub_hi, r.upd_lo, r.upd_hi)], cfg[k]["seed"] ^ 0xD41F7,
+                           sig[k]) for k, r in enumerate(regs)]
+
+    rng = np.random.default_rng(64)
+    order = rng.integers(0, 64, size=requests)
+    from paper_1703_06680_gb300.serve import Request
+
+    # 1) plain capacity: all requests queued at once, one at a time
+    sims = make_sims()
+    reqs = [Request(sim=int(k), arrival=0.0) for k in order]
+    cap_wall = run_plain(sims, reqs)
+    capacity = requests / cap_wall
+    plain_sat_pairs = sum(r.K for r in reqs) / cap_wall
+    for s_ in sims:
+        s_.close()
+
+    # 1b) served capacity: the same requests all queued at once
+    sims = make_sims()
+    server = Server(sims, slots=slots)
+    t0 = time.perf_counter()
+    sat = [server.submit(int(k), arrival=t0) for k in order]
+    for r in sat:
+        r.done.wait(600)
+    sat_wall = max(r.finish for r in sat) - t0
+    server.close()
+    served_sat_pairs = sum(r.K for r in sat) / sat_wall
+    for s_ in sims:
+        s_.close()
+    rate = load * capacity
+    gaps = rng.exponential(1.0 / rate, size=requests)
+    offsets = np.cumsum(gaps)
+
+    # 2) served: continuous batching at the offered load
+    sims = make_sims()
+    server = Server(sims, slots=slots)
+    t0 = time.perf_counter()
+    sreqs = []
+    for k, off in zip(order, offsets):
+        now = time.perf_counter() - t0
+        if off > now:
+            time.sleep(off - now)
+        sreqs.append(server.submit(int(k), arrival=t0 + off))
+    for r in sreqs:
+        r.done.wait(600)
+    served_wall = max(r.finish for r in sreqs) - t0
+    server.close()
+    served = latency_summary(sreqs, served_wall)
+    for s_ in sims:
+        s_.close()
+
+    # 3) plain at the same offered load (queueing included)
+    sims = make_sims()
+    t0 = time.perf_counter()
+    preqs = [Request(sim=int(k), arrival=t0 + off) for k, off in zip(order, offsets)]
+    run_plain(sims, preqs)
+    plain_wall = max(r.finish for r in preqs) - t0
+    plain = latency_summary(preqs, plain_wall)
+    for s_ in sims:
+        s_.close()
+    torch.cuda.empty_cache()
+    return {"workload": "64 simulations, N log-uniform in [1e3, 1e6], d in {1,2,3}, "
+                        "alpha in {0.01,1,100}, drift N(0, 0.1 side) per step, Poisson arrivals",
+            "requests": requests, "slots": slots, "offered_load_vs_plain_capacity": load,
+            "plain_capacity_rps": capacity, "offered_rps": rate, "served": served,
+            "plain": plain,
+            "saturated": {"plain_pairs_per_s": plain_sat_pairs, "served_pairs_per_s": served_sat_pairs,
+                          "plain_rps": capacity, "served_rps": requests / sat_wall,
+                          "throughput_speedup": served_sat_pairs / plain_sat_pairs},
+            "p99_speedup": plain["p99_ms"] / served["p99_ms"] if served["p99_ms"] else None,
+            "throughput_speedup": served["pairs_per_s"] / plain["pairs_per_s"]
+            if plain["pairs_per_s"] else None}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -256,6 +386,7 @@ def run_ours(args):
         "sweep_scan": 4 * E + 20 * N + 4 * N,
         "counts": 12 * n,
         "offsets": 4 * n + 8 * (n + 1),
+        "emit_setup": 36 * m,
         "emit": 8 * K,
         "segsort": 8 * K,
     }
@@ -289,6 +420,10 @@ def run_ours(args):
         "clocks": clocks,
         "wall_s_timed": wall,
     }
+    if rank == 0 and world == 1 and not args.no_batched:
+        line["batched"] = bench_batched(ctx, dev)
+    if rank == 0 and world == 1 and not args.no_served:
+        line["served"] = bench_served(dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(reg, args.cpu_seconds)
     if rank == 0:

@@ -146,7 +146,8 @@ int ddm_count_noalloc(const ddm_regions *regions, void *cuda_stream, uint64_t *K
  * boundaries, and stage_ms[] holds the device time of each stage of the last
  * call: 0 key build (a1), 1 radix sort (a2), 2 sweep scan (a3), 3 counts --
  * rank arithmetic for d = 1, filter count for d > 1 (a4/a7), 4 offsets scan
- * (a5), 5 pair emission (a6/a7), 6 per-segment sort (a6), 7 unused.
+ * (a5), 5 emission set-up -- window lists and rank table (a6), 6 pair emission
+ * (a6/a7), 7 per-segment sort (a6).
  * `launches` counts every kernel the context has launched since creation.
  */
 #define DDM_STAGES 8

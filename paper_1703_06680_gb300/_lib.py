@@ -44,8 +44,8 @@ class Stats(ctypes.Structure):
                 ("stage_ms", ctypes.c_float * 8)]
 
 
-STAGE_NAMES = ["keybuild", "radix_sort", "sweep_scan", "counts", "offsets", "emit", "segsort",
-               "unused"]
+STAGE_NAMES = ["keybuild", "radix_sort", "sweep_scan", "counts", "offsets", "emit_setup", "emit",
+               "segsort"]
 
 
 class _Regions(ctypes.Structure):
@@ -233,6 +233,19 @@ class Context:
         self._check(self._lib.ddm_count(self._h, p.ref, ctypes.byref(K)))
         return int(K.value)
 
+    def match_packed(self, packed, out) -> int:
+        """ddm_match with descriptors packed once by pack(); out is a (cap, 2) int32 tensor."""
+        K = ctypes.c_uint64(0)
+        cap = out.shape[0]
+        rc = self._lib.ddm_match(self._h, packed.ref, ctypes.c_void_p(out.data_ptr() if cap else 0),
+                                 cap, ctypes.byref(K))
+        self._check(rc, K.value)
+        return int(K.value)
+
+    @staticmethod
+    def pack(sub_lo, sub_hi, upd_lo, upd_hi):
+        return _pack_device(sub_lo, sub_hi, upd_lo, upd_hi)
+
     def match_into(self, out, sub_lo, sub_hi, upd_lo, upd_hi) -> int:
         """ddm_match into a preallocated (cap, 2) int32 CUDA tensor; returns K."""
         torch = _torch()
@@ -269,6 +282,28 @@ class Context:
                                       ctypes.byref(K))
         self._check(rc, K.value)
         return out[:K.value]
+
+    @staticmethod
+    def pack_batch(instances):
+        """Packs the descriptors of a list of instances once, for repeated match_batch calls."""
+        packs = [_pack_device(*inst) for inst in instances]
+        arr = (_Regions * max(len(packs), 1))(*[p.s for p in packs])
+        return {"packs": packs, "arr": arr, "num": len(packs),
+                "device": instances[0][0].device if instances else None}
+
+    def match_batch_packed(self, pack, out=None, offs=None):
+        """ddm_match_batch on a pack_batch() result; out: (cap, 2) int32 CUDA tensor or None
+        (count only).  Returns (K, inst_offsets)."""
+        num = pack["num"]
+        if offs is None:
+            offs = np.zeros(num + 1, np.uint64)
+        K = ctypes.c_uint64(0)
+        cap = 0 if out is None else out.shape[0]
+        rc = self._lib.ddm_match_batch(self._h, num, ctypes.cast(pack["arr"], ctypes.c_void_p),
+                                       ctypes.c_void_p(out.data_ptr() if out is not None else 0),
+                                       cap, ctypes.c_void_p(offs.ctypes.data), ctypes.byref(K))
+        self._check(rc, K.value)
+        return int(K.value), offs
 
     def match_batch(self, instances, cap: int | None = None, count_only: bool = False):
         """ddm_match_batch over a list of (sub_lo, sub_hi, upd_lo, upd_hi) CUDA tensors.

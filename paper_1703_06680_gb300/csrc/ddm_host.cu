@@ -324,7 +324,7 @@ int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
     }
     if (pl.E == 0) {
         if (do_prefix) {
-            for (int k = 0; k <= DDM_STAGES; ++k) mark(c, k);
+            for (int k = 0; k <= DDM_STAGES; ++k) mark(c, k);  // zero-length stages
             if (batch) L += launch_inst_offsets(ba, pl.off, pl.inst_off, s);
         }
         c->last_inst_off = batch ? pl.inst_off : nullptr;
@@ -404,20 +404,20 @@ int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
                         mode == Mode::Match && phase == Phase::All ? cap : ~0ull,
                         &c->dstat->K, pl.off_status, c->dstat, s);
     if (batch) L += launch_inst_offsets(ba, pl.off, pl.inst_off, s);
-    mark(c, 5);
   }
   if (do_suffix) {
+    mark(c, 5);
     if (pl.window) {
         L += launch_window_sizes(a, c->dstat, s);
         L += launch_offsets(pl.lw_size, pl.num_win, pl.lw_off, ~0ull, pl.lw_total,
                             pl.win_status, c->dstat, s);
         L += launch_tile_active(a, c->dstat, s);
-        L += launch_emit_window(a, c->dstat, s);
     }
-    if (mode == Mode::Match) L += launch_emit_ranges(a, c->dstat, s);
     mark(c, 6);
-    if (mode == Mode::Match) L += launch_segment_sort(a, c->dstat, s);
+    if (pl.window) L += launch_emit_window(a, c->dstat, s);
+    if (mode == Mode::Match) L += launch_emit_ranges(a, c->dstat, s);
     mark(c, 7);
+    if (mode == Mode::Match) L += launch_segment_sort(a, c->dstat, s);
     mark(c, 8);
   }
     CK(cudaGetLastError());
