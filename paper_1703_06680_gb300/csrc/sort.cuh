@@ -12,7 +12,7 @@ namespace ddm {
 constexpr int RADIX_BITS = 8;
 constexpr int RADIX = 1 << RADIX_BITS;
 constexpr int SORT_BLOCK = 256;        // threads per tile
-constexpr int SORT_ITEMS_32 = 16;      // keys per thread, 32-bit keys
+constexpr int SORT_ITEMS_32 = 18;      // keys per thread, 32-bit keys
 constexpr int SORT_ITEMS_64 = 12;      // keys per thread, 64-bit keys
 
 template <typename KeyT>

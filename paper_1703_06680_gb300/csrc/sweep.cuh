@@ -9,7 +9,7 @@
 namespace ddm {
 
 constexpr int SCAN_BLOCK = 256;
-constexpr int SCAN_ITEMS = 32;
+constexpr int SCAN_ITEMS = 16;
 constexpr int SCAN_TILE = SCAN_BLOCK * SCAN_ITEMS;
 constexpr int OFF_BLOCK = 256;
 constexpr int OFF_ITEMS = 8;
