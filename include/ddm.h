@@ -141,6 +141,15 @@ int ddm_match_host(ddm_ctx *ctx, const ddm_regions *regions, int32_t *pairs, uin
 int ddm_count_noalloc(const ddm_regions *regions, void *cuda_stream, uint64_t *K_out);
 
 /*
+ * Tunables of a context (read by the autotuner; defaults are used otherwise).
+ *   DDM_PARAM_WIN_SHIFT   log2 of the window length of the d = 1 emission, in
+ *                         sorted-stream positions: 6 .. 9 (default 8).
+ * Returns DDM_ERR_INVALID for an unknown parameter or a value out of range.
+ */
+#define DDM_PARAM_WIN_SHIFT 1
+int ddm_set_param(ddm_ctx *ctx, int param, int64_t value);
+
+/*
  * Counters and per-stage timing.  With profiling enabled (ddm_set_profiling),
  * every call records CUDA events on the context's stream at the stage
  * boundaries, and stage_ms[] holds the device time of each stage of the last

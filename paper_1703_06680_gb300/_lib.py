@@ -25,6 +25,7 @@ DDM_ERR_DEVICE_TIMEOUT = -4
 DDM_ERR_CUDA = -5
 DDM_ERR_INTERNAL = -6
 MAX_DIMS = 8
+PARAM_WIN_SHIFT = 1
 
 
 class DDMError(RuntimeError):
@@ -72,6 +73,7 @@ SIGNATURES = {
     "ddm_match_host": (ctypes.c_int, [_P, _RP, _P, ctypes.c_uint64, _U64P]),
     "ddm_debug_sweep": (ctypes.c_int, [_P, _RP, _P, _P, _P, _P, _P]),
     "ddm_set_profiling": (ctypes.c_int, [_P, ctypes.c_int]),
+    "ddm_set_param": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64]),
     "ddm_count_noalloc": (ctypes.c_int, [_RP, _P, _U64P]),
     "ddm_match_batch": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_uint64, _P, _U64P]),
     "ddm_session_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _RP, ctypes.c_size_t]),
@@ -215,6 +217,9 @@ class Context:
         if rc == DDM_ERR_CAPACITY:
             raise CapacityError(rc, msg, int(K or 0))
         raise DDMError(rc, msg)
+
+    def set_param(self, param: int, value: int):
+        self._check(self._lib.ddm_set_param(self._h, param, value))
 
     def set_profiling(self, on: bool):
         self._check(self._lib.ddm_set_profiling(self._h, int(bool(on))))

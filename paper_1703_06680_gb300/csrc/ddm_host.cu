@@ -35,6 +35,7 @@ struct ddm_ctx {
     ddm_stats stats{};
     bool prof = false;
     unsigned long long* last_inst_off = nullptr;  // device, batched calls
+    int win_shift = 8;                            // DDM_PARAM_WIN_SHIFT
     cudaEvent_t ev[DDM_STAGES + 1] = {};
 };
 
@@ -191,7 +192,8 @@ struct Plan {
     unsigned long long* inst_off;
     size_t total;
 
-    void layout(char* base, int d_, int64_t n_, int64_t m_, Mode mode, int num_inst_) {
+    void layout(char* base, int d_, int64_t n_, int64_t m_, Mode mode, int num_inst_,
+                int win_shift_ = 8) {
         d = d_; n = n_; m = m_; E = 2 * (n + m); num_inst = num_inst_;
         const bool batch = num_inst > 0;
         passes = batch ? (int)ceil_div(32 + ceil_log2(num_inst), RADIX_BITS) : 4;
@@ -205,7 +207,7 @@ struct Plan {
         cursor_b = cv.take<uint32_t>(mode == Mode::Match ? n : 0);
         big_count = cv.take<uint32_t>(2);
         window = mode == Mode::Match && d == 1;
-        win_shift = 8;
+        win_shift = win_shift_;
         num_win = window ? (uint32_t)ceil_div(E, 1ull << win_shift) : 0;
         lw_fill = cv.take<uint32_t>(num_win);
         num_flagged = cv.take<uint32_t>(1);
@@ -268,12 +270,12 @@ enum class Phase { All, Prefix, Suffix };
 int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
             const DebugOut* dbg, Phase phase = Phase::All) {
     Plan pl;
-    pl.layout(nullptr, job.d, job.n, job.m, mode, job.num_inst);
+    pl.layout(nullptr, job.d, job.n, job.m, mode, job.num_inst, c->win_shift);
     if (phase == Phase::Suffix && pl.total > c->ws_size)
         return fail(c, DDM_ERR_INTERNAL, "emission phase without its prefix");
     int rc = ensure(c, &c->ws, &c->ws_size, pl.total);
     if (rc) return rc;
-    pl.layout(c->ws, job.d, job.n, job.m, mode, job.num_inst);
+    pl.layout(c->ws, job.d, job.n, job.m, mode, job.num_inst, c->win_shift);
     cudaStream_t s = c->stream;
     const bool batch = job.num_inst > 0;
     const bool do_prefix = phase != Phase::Suffix, do_suffix = phase != Phase::Prefix;
@@ -518,6 +520,16 @@ int ddm_set_profiling(ddm_ctx* c, int enable) {
     }
     c->prof = enable != 0;
     return DDM_OK;
+}
+
+int ddm_set_param(ddm_ctx* c, int param, int64_t value) {
+    if (!c) return DDM_ERR_INVALID;
+    if (param == DDM_PARAM_WIN_SHIFT) {
+        if (value < 6 || value > 9) return fail(c, DDM_ERR_INVALID, "window shift must be 6..9");
+        c->win_shift = (int)value;
+        return DDM_OK;
+    }
+    return fail(c, DDM_ERR_INVALID, "unknown parameter");
 }
 
 int ddm_get_stats(const ddm_ctx* c, ddm_stats* out) {

@@ -196,14 +196,22 @@ int launch_filter_count(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
     return launches;
 }
 
+// When the window path ran (flags in use), the range path only serves the few
+// flagged subscriptions and usually finds none: a small grid keeps that cheap.
+static unsigned fallback_grid(const EmitArgs& a, int64_t items) {
+    return a.flag ? 152u : warp_grid(items);
+}
+
 int launch_emit_ranges(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
     int launches = 0;
     if (a.d > 1) {
         if (a.n > 0) k_class_a<true, true><<<warp_grid(a.n), EMIT_BLOCK, 0, s>>>(a, st), ++launches;
         if (a.m > 0) k_class_b<true, true><<<warp_grid(a.m), EMIT_BLOCK, 0, s>>>(a, st), ++launches;
     } else {
-        if (a.n > 0) k_class_a<true, false><<<warp_grid(a.n), EMIT_BLOCK, 0, s>>>(a, st), ++launches;
-        if (a.m > 0) k_class_b<true, false><<<warp_grid(a.m), EMIT_BLOCK, 0, s>>>(a, st), ++launches;
+        if (a.n > 0)
+            k_class_a<true, false><<<fallback_grid(a, a.n), EMIT_BLOCK, 0, s>>>(a, st), ++launches;
+        if (a.m > 0)
+            k_class_b<true, false><<<fallback_grid(a, a.m), EMIT_BLOCK, 0, s>>>(a, st), ++launches;
     }
     return launches;
 }
@@ -354,7 +362,7 @@ __global__ void __launch_bounds__(BIG_BLOCK) k_segsort_big(EmitArgs a, DevStatus
 
 int launch_segment_sort(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
     if (a.n == 0) return 0;
-    k_segsort_warp<<<warp_grid(a.n), EMIT_BLOCK, 0, s>>>(a, st);
+    k_segsort_warp<<<fallback_grid(a, a.n), EMIT_BLOCK, 0, s>>>(a, st);
     k_segsort_big<<<152, BIG_BLOCK, 0, s>>>(a, st);
     return 2;
 }

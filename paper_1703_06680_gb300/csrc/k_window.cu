@@ -29,7 +29,7 @@ constexpr int WIN_BLOCK = 256;
 constexpr uint32_t LCAP = 1024;       // active updates per window boundary
 constexpr uint32_t WCAP = 1024;       // candidates per window
 constexpr uint32_t LONG_SPAN = 512;   // positions; longer subscriptions use the range path
-constexpr int MAX_WIN_SHIFT = 8;      // windows of at most 256 positions
+constexpr int MAX_WIN_SHIFT = 9;      // windows of at most 512 positions
 constexpr int NBUCKET = 256;          // buckets of the per-window id sort
 constexpr int WITEMS = WCAP / WIN_BLOCK;
 
@@ -78,8 +78,8 @@ __global__ void k_tile_active(EmitArgs a, DevStatus* st) {
 
 __global__ void __launch_bounds__(WIN_BLOCK) k_emit_window(EmitArgs a, DevStatus* st) {
     constexpr uint32_t MAXSUB = 1u << MAX_WIN_SHIFT;
-    __shared__ unsigned long long skey[WCAP];  // staging: (update id << 32) | pos(U.lo)
-    __shared__ uint4 cand[WCAP];               // sorted W: {id, pos(U.lo), pos(U.hi), 0}
+    __shared__ unsigned long long skey[WCAP];  // (update id << 32) | pos(U.lo)
+    __shared__ uint32_t spay[WCAP];            // pos(U.hi)
     __shared__ uint32_t s_id[MAXSUB], s_lo[MAXSUB], s_hi[MAXSUB], s_cnt[MAXSUB];
     __shared__ unsigned long long s_off[MAXSUB];
     __shared__ uint32_t bcnt[NBUCKET], bstart[NBUCKET], warp_tmp[16];
@@ -183,13 +183,18 @@ __global__ void __launch_bounds__(WIN_BLOCK) k_emit_window(EmitArgs a, DevStatus
 #pragma unroll
     for (int it = 0; it < WITEMS; ++it) {
         const uint32_t k = tid + it * WIN_BLOCK;
-        if (k < W)
-            cand[fin[it]] = make_uint4((uint32_t)(key[it] >> 32), (uint32_t)key[it], pay[it], 0u);
+        if (k < W) {
+            skey[fin[it]] = key[it];
+            spay[fin[it]] = pay[it];
+        }
     }
     // Pad W to whole warps with entries that no subscription keeps
     // (pos(lo) = 0xffffffff is never below a pos(S.hi)).
     const uint32_t Wpad = (W + 31) & ~31u;
-    for (uint32_t k = W + tid; k < Wpad; k += WIN_BLOCK) cand[k] = make_uint4(0u, ~0u, 0u, 0u);
+    for (uint32_t k = W + tid; k < Wpad; k += WIN_BLOCK) {
+        skey[k] = ~0ull;
+        spay[k] = 0u;
+    }
     __syncthreads();
     if (s_nreg == 0) return;
 
@@ -208,18 +213,15 @@ __global__ void __launch_bounds__(WIN_BLOCK) k_emit_window(EmitArgs a, DevStatus
         int2* seg = reinterpret_cast<int2*>(a.pairs) + s_off[k];
         const uint32_t c = s_cnt[k];
         uint32_t running = 0;
-        bool ok = true;
-#pragma unroll 2
         for (uint32_t kk = lane; kk < Wpad; kk += 32) {
-            const uint4 e = cand[kk];
-            const bool pass = (e.y < ph) & (e.z > pl);
+            const unsigned long long kv = skey[kk];
+            const bool pass = (uint32_t)kv < ph && spay[kk] > pl;
             const unsigned bal = __ballot_sync(0xffffffffu, pass);
-            const uint32_t total = running + __popc(bal);
-            ok &= total <= c;  // never write past the segment
-            if (pass && ok) seg[running + __popc(bal & lt)] = make_int2(i, (int32_t)(e.x - j_base));
-            running = total;
+            const uint32_t r = running + __popc(bal & lt);
+            if (pass && r < c) seg[r] = make_int2(i, (int32_t)((uint32_t)(kv >> 32) - j_base));
+            running += __popc(bal);
         }
-        if (lane == 0 && (running != c || !ok)) raise_error(st, DDM_ERR_INTERNAL, 12);
+        if (lane == 0 && running != c) raise_error(st, DDM_ERR_INTERNAL, 12);
     }
 }
 
