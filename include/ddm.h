@@ -156,7 +156,8 @@ int ddm_set_param(ddm_ctx *ctx, int param, int64_t value);
  * call: 0 key build (a1), 1 radix sort (a2), 2 sweep scan (a3), 3 counts --
  * rank arithmetic for d = 1, filter count for d > 1 (a4/a7), 4 offsets scan
  * (a5), 5 emission set-up -- window lists and rank table (a6), 6 pair emission
- * (a6/a7), 7 per-segment sort (a6).
+ * (a6/a7: the window kernel for d = 1, the range kernels for d > 1), 7 range
+ * path of flagged subscriptions and per-segment sort (a6).
  * `launches` counts every kernel the context has launched since creation.
  */
 #define DDM_STAGES 8

@@ -229,9 +229,9 @@ struct Plan {
         vals0 = cv.take<uint32_t>(E);
         vals1 = cv.take<uint32_t>(E);
         rec.s_lo = cv.take<uint4>(n);
-        rec.s_hi = cv.take<uint2>(n);
+        rec.s_hi = cv.take<uint4>(n);
         rec.u_lo = cv.take<uint4>(m);
-        rec.u_hi = cv.take<uint2>(m);
+        rec.u_hi = cv.take<uint4>(m);
         rec.sub_order = cv.take<uint32_t>(n);
         rec.upd_order = cv.take<uint32_t>(m);
         rec.windows = nullptr;
@@ -417,8 +417,9 @@ int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
     }
     mark(c, 6);
     if (pl.window) L += launch_emit_window(a, c->dstat, s);
-    if (mode == Mode::Match) L += launch_emit_ranges(a, c->dstat, s);
+    else if (mode == Mode::Match) L += launch_emit_ranges(a, c->dstat, s);
     mark(c, 7);
+    if (pl.window && mode == Mode::Match) L += launch_emit_ranges(a, c->dstat, s);  // flagged only
     if (mode == Mode::Match) L += launch_segment_sort(a, c->dstat, s);
     mark(c, 8);
   }

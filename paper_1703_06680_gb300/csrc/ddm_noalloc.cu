@@ -92,9 +92,9 @@ struct NoallocLayout {
         vals1 = s.take<uint32_t>(E);
         rec = Records{};
         rec.s_lo = s.take<uint4>(n);
-        rec.s_hi = s.take<uint2>(n);
+        rec.s_hi = s.take<uint4>(n);
         rec.u_lo = s.take<uint4>(m);
-        rec.u_hi = s.take<uint2>(m);
+        rec.u_hi = s.take<uint4>(m);
         rec.sub_order = s.take<uint32_t>(n);
         rec.upd_order = s.take<uint32_t>(m);
         cnt = s.take<uint32_t>(n);

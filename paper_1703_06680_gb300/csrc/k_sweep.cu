@@ -111,25 +111,21 @@ k_sweep_scan(const uint32_t* __restrict__ vals, uint32_t E, uint32_t n, uint32_t
         }
         if (rec.windows && (p & ((1u << rec.win_shift) - 1)) == 0)
             rec.windows[p >> rec.win_shift] = make_uint4(cSlo, cUlo, cUhi, p);
-        switch (kind) {
-            case KIND_SLO:
-                rec.s_lo[id] = make_uint4(p, cUlo, cUhi, cSlo);
-                if (cSlo < n) rec.sub_order[cSlo] = id;
-                ++cSlo;
-                break;
-            case KIND_ULO:
-                rec.u_lo[id] = make_uint4(p, cSlo, cShi, cUlo);
-                if (cUlo < m) rec.upd_order[cUlo] = id;
-                ++cUlo;
-                break;
-            case KIND_SHI:
-                rec.s_hi[id] = make_uint2(p, cUlo);
-                ++cShi;
-                break;
-            default:
-                rec.u_hi[id] = make_uint2(p, cSlo);
-                break;
+        // One record store per endpoint, address and value selected by kind.
+        const bool is_upd = kind & 1u, is_upper = kind >> 1;
+        uint4* const tab = is_upper ? (is_upd ? rec.u_hi : rec.s_hi) : (is_upd ? rec.u_lo : rec.s_lo);
+        const uint32_t own = is_upd ? cSlo : cUlo;  // lower endpoints seen of the other set
+        const uint32_t y = own;
+        const uint32_t z = is_upper ? 0u : (is_upd ? cShi : cUhi);
+        const uint32_t w = is_upper ? 0u : (is_upd ? cUlo : cSlo);
+        tab[id] = make_uint4(p, y, z, w);
+        if (!is_upper) {
+            const uint32_t r = is_upd ? cUlo : cSlo;
+            if (r < (is_upd ? m : n)) (is_upd ? rec.upd_order : rec.sub_order)[r] = id;
         }
+        cSlo += kind == KIND_SLO;
+        cUlo += kind == KIND_ULO;
+        cShi += kind == KIND_SHI;
         if (rec.windows && p + 1 == E)  // closing entry at position E
             rec.windows[(E + (1u << rec.win_shift) - 1) >> rec.win_shift] =
                 make_uint4(cSlo, cUlo, E - cSlo - cUlo - cShi, E);
@@ -157,7 +153,7 @@ int launch_sweep_scan(const uint32_t* vals, uint64_t E, int64_t n, int64_t m, co
 // ---------------------------------------------------------------------------
 // a4
 // ---------------------------------------------------------------------------
-__global__ void k_rank_count(const uint4* __restrict__ lo, const uint2* __restrict__ hi,
+__global__ void k_rank_count(const uint4* __restrict__ lo, const uint4* __restrict__ hi,
                              int64_t count, uint32_t* __restrict__ cnt, DevStatus* st) {
     if (read_error(st)) return;
     bool bad = false;

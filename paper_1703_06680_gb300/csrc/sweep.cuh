@@ -20,16 +20,18 @@ constexpr int OFF_TILE = OFF_BLOCK * OFF_ITEMS;
 // count the S lowers, U lowers, S uppers and U uppers strictly before p.
 // Each endpoint event writes ONE packed record (a single scattered store):
 //   s_lo[i] = {pos(S_i.lo), A = cUlo(pos lo), C = cUhi(pos lo), cSlo(pos lo)}
-//   s_hi[i] = {pos(S_i.hi), B = cUlo(pos hi)}
+//   s_hi[i] = {pos(S_i.hi), B = cUlo(pos hi), 0, 0}
 //   u_lo[j] = {pos(U_j.lo), A = cSlo(pos lo), C = cShi(pos lo), cUlo(pos lo)}
-//   u_hi[j] = {pos(U_j.hi), B = cSlo(pos hi)}
+//   u_hi[j] = {pos(U_j.hi), B = cSlo(pos hi), 0, 0}
+// All four are 16-byte records so that the scan writes every endpoint's record
+// with one store through a computed address (no divergent branch per kind).
 // sub_order[r] (upd_order[r]) is the id of the subscription (update) whose
 // lower endpoint is the r-th S (U) lower endpoint of the stream.
 struct Records {
     uint4* s_lo;
-    uint2* s_hi;
+    uint4* s_hi;
     uint4* u_lo;
-    uint2* u_hi;
+    uint4* u_hi;
     uint32_t *sub_order, *upd_order;
     uint4* windows;       // (cSlo, cUlo, cUhi, p) at p = w << win_shift, or NULL
     int win_shift;
