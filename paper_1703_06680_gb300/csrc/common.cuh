@@ -89,8 +89,18 @@ __device__ __forceinline__ void backoff(uint32_t iter) {
 constexpr unsigned long long LB64_AGG = 1ull << 62, LB64_INC = 2ull << 62;
 constexpr unsigned long long LB64_VAL = (1ull << 62) - 1;
 
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
 // Warp-cooperative look-back: exclusive prefix of tile `tile` over the values
 // published by tiles 0..tile-1 in `status`.  Called by all 32 lanes of one warp.
+// Each step examines the 128 nearest unexamined predecessors (four words per
+// lane, loaded together) and sums back to the nearest inclusive prefix.  Each
+// word carries its own flag and value, so relaxed loads suffice and can be
+// pipelined; the publisher's release store makes the word visible whole.
 __device__ __forceinline__ unsigned long long warp_lookback_u64(unsigned long long* status,
                                                                 long long tile, DevStatus* st,
                                                                 int where) {
@@ -98,27 +108,41 @@ __device__ __forceinline__ unsigned long long warp_lookback_u64(unsigned long lo
     unsigned long long sum = 0;
     long long p = tile - 1;
     while (p >= 0) {
-        long long q = p - lane;
-        unsigned long long v = LB64_INC;  // before tile 0: inclusive prefix 0
-        if (q >= 0) {
+        unsigned long long v[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const long long q = p - (j * 32 + lane);
+            v[j] = q >= 0 ? ld_relaxed_u64(status + q) : LB64_INC;  // before tile 0: prefix 0
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const long long q = p - (j * 32 + lane);
             uint32_t it = 0;
-            while ((v = ld_acquire_u64(status + q)) == 0ull) {
+            while (v[j] == 0ull) {  // not yet published: wait (bounded)
                 if (++it > SPIN_LIMIT) {
                     raise_error(st, DDM_ERR_DEVICE_TIMEOUT, where);
-                    v = LB64_INC;
+                    v[j] = LB64_INC;
                     break;
                 }
                 backoff(it);
+                v[j] = ld_relaxed_u64(status + q);
             }
         }
-        unsigned inc = __ballot_sync(0xffffffffu, (v >> 62) == 2ull);
-        int stop = inc ? __ffs(inc) - 1 : 32;
-        unsigned long long mine = (lane <= stop) ? (v & LB64_VAL) : 0ull;
+        int first = 128;  // distance index (j * 32 + lane) of the nearest inclusive prefix
+#pragma unroll
+        for (int j = 3; j >= 0; --j) {
+            const unsigned inc = __ballot_sync(0xffffffffu, (v[j] >> 62) == 2ull);
+            if (inc) first = j * 32 + __ffs(inc) - 1;
+        }
+        unsigned long long mine = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (j * 32 + lane <= first) mine += v[j] & LB64_VAL;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
         sum += mine;
-        if (inc) break;
-        p -= 32;
+        if (first < 128) break;
+        p -= 128;
     }
     return sum;
 }

@@ -42,35 +42,30 @@ __global__ void k_window_sizes(EmitArgs a) {
     }
 }
 
-// Rank-ordered update table: urank[r] = {id, pos(lo), pos(hi)} of the update
-// with the r-th lower endpoint, so that windows read candidates contiguously.
-__global__ void k_rank_table(EmitArgs a) {
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < a.m;
-         r += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t id = a.rec.upd_order[r];
-        a.urank[r] = make_uint4(id, a.rec.u_lo[id].x, a.rec.u_hi[id].x, 0u);
-    }
-}
-
 __device__ __forceinline__ bool list_fits(const EmitArgs& a, uint32_t w, uint32_t s) {
     return s <= LCAP && a.lw_off[w] + s <= a.lw_cap;
 }
 
-// L_w: every update U contributes {id, pos(U.hi)} to the boundaries w*T with
-// pos(U.lo) < w*T <= pos(U.hi).
+// One pass over the updates in lower-endpoint order (rank r, id = upd_order[r]):
+//  - the rank table urank[r] = {id, pos(lo), pos(hi)}, so that windows read
+//    their candidates contiguously;
+//  - the boundary lists: U contributes {id, pos(U.hi)} to every boundary w*T
+//    with pos(U.lo) < w*T <= pos(U.hi) (the paper's UpdSet at that boundary).
 __global__ void k_tile_active(EmitArgs a, DevStatus* st) {
     if (read_error(st)) return;
     const int S = a.win_shift;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < a.m;
-         j += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < a.m;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t j = a.rec.upd_order[r];
         const uint32_t pl = a.rec.u_lo[j].x, ph = a.rec.u_hi[j].x;
+        a.urank[r] = make_uint4(j, pl, ph, 0u);
         const uint32_t w1 = min(ph >> S, a.num_win - 1);
         for (uint32_t w = (pl >> S) + 1; w <= w1; ++w) {
             const uint4 t = a.windows[w];
             const uint32_t s = t.y - t.z;
             if (!list_fits(a, w, s)) continue;
             const uint32_t slot = atomicAdd(&a.lw_fill[w], 1u);
-            if (slot < s) a.lw[a.lw_off[w] + slot] = make_uint2((uint32_t)j, ph);
+            if (slot < s) a.lw[a.lw_off[w] + slot] = make_uint2(j, ph);
             else raise_error(st, DDM_ERR_INTERNAL, 10);
         }
     }
@@ -239,9 +234,8 @@ int launch_window_sizes(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
 
 int launch_tile_active(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
     if (a.m == 0 || a.num_win == 0) return 0;
-    k_rank_table<<<grid_for(a.m, 256, 152 * 16), 256, 0, s>>>(a);
     k_tile_active<<<grid_for(a.m, 256, 152 * 16), 256, 0, s>>>(a, st);
-    return 2;
+    return 1;
 }
 
 int launch_emit_window(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
