@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(WIN_BLOCK) k_emit_window(EmitArgs a, DevStatus
     __shared__ uint32_t s_id[MAXSUB], s_lo[MAXSUB], s_hi[MAXSUB], s_cnt[MAXSUB];
     __shared__ unsigned long long s_off[MAXSUB];
     __shared__ uint32_t bcnt[NBUCKET], bstart[NBUCKET], warp_tmp[16];
-    __shared__ uint32_t s_pmax, s_nreg, s_uend;
+    __shared__ uint32_t s_pmax, s_nreg;
     if (read_error(st)) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t w = blockIdx.x;
@@ -106,17 +106,12 @@ __global__ void __launch_bounds__(WIN_BLOCK) k_emit_window(EmitArgs a, DevStatus
     const uint32_t wend = min(max((s_pmax >> S) + 1, w + 1), a.num_win);
     const uint32_t u0 = t0.y;
     // Updates starting in [wT, pmax): the rank table is sorted by pos(lo), so
-    // the exact end is found by binary search inside [u0, cUlo(wend * T)).
-    if (tid == 0) {
-        uint32_t lo = u0, hi = a.windows[wend].y;
-        while (lo < hi) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (a.urank[mid].y < s_pmax) lo = mid + 1; else hi = mid;
-        }
-        s_uend = lo;
-    }
-    __syncthreads();
-    const uint32_t nlow = s_uend - u0;
+    // the count of entries of [u0, cUlo(wend * T)) below pmax is the exact
+    // length of the range (one parallel pass, no search).
+    const uint32_t u1 = a.windows[wend].y;
+    uint32_t nlow = 0;
+    for (uint32_t r = u0; r < u1; r += WIN_BLOCK)
+        nlow += __syncthreads_count(r + tid < u1 && a.urank[r + tid].y < s_pmax);
     const uint32_t W = lw_n + nlow;
     const bool overflow = !list_fits(a, w, lw_n) || W > WCAP;
     // Flags: 1 = served by the range path.
