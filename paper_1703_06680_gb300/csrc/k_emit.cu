@@ -101,7 +101,10 @@ __global__ void __launch_bounds__(EMIT_BLOCK) k_class_a(EmitArgs a, DevStatus* s
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int64_t warps = (int64_t)gridDim.x * (EMIT_BLOCK / 32);
-    for (int64_t i = ((int64_t)blockIdx.x * EMIT_BLOCK + threadIdx.x) >> 5; i < a.n; i += warps) {
+    // Subscriptions in lower-endpoint order: neighbouring warps expand
+    // overlapping ranges of upd_order, so candidate keys are reused from L1.
+    for (int64_t r = ((int64_t)blockIdx.x * EMIT_BLOCK + threadIdx.x) >> 5; r < a.n; r += warps) {
+        const int64_t i = a.rec.sub_order[r];
         if (a.flag && !a.flag[i]) continue;
         const uint32_t A = a.rec.s_lo[i].y, B = a.rec.s_hi[i].y;
         if (A > B || B > (uint64_t)a.m) {  // guard against an upstream fault
@@ -145,7 +148,9 @@ __global__ void __launch_bounds__(EMIT_BLOCK) k_class_b(EmitArgs a, DevStatus* s
     if (a.flag && *(volatile uint32_t*)a.num_flagged == 0u) return;
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (EMIT_BLOCK / 32);
-    for (int64_t j = ((int64_t)blockIdx.x * EMIT_BLOCK + threadIdx.x) >> 5; j < a.m; j += warps) {
+    // Updates in lower-endpoint order (neighbouring warps share sub_order ranges).
+    for (int64_t q = ((int64_t)blockIdx.x * EMIT_BLOCK + threadIdx.x) >> 5; q < a.m; q += warps) {
+        const int64_t j = a.rec.upd_order[q];
         const uint32_t A = a.rec.u_lo[j].y, B = a.rec.u_hi[j].y;
         if (A > B || B > (uint64_t)a.n) {  // guard against an upstream fault
             if (lane == 0) raise_error(st, DDM_ERR_INTERNAL, 9);
