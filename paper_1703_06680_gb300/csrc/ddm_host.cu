@@ -4,6 +4,7 @@
 // per-segment sort.  Everything is enqueued on the context's stream; device
 // kernels gate on the device status word (an input error or a capacity
 // overflow stops the later stages), and the host reads {status, K} once.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -162,9 +163,10 @@ struct Plan {
     unsigned long long* off_status;
     uint32_t* cursor_b;
     uint32_t* big_count;
-    // window path (d = 1, match)
-    bool window;
+    // window path (d = 1, match) and tiled join (d > 1)
+    bool window, join;
     int win_shift;
+    uint32_t lcap;
     uint32_t num_win;
     uint32_t* lw_fill;
     uint32_t* num_flagged;
@@ -174,7 +176,7 @@ struct Plan {
     uint4* windows;
     uint32_t* lw_size;
     unsigned long long* lw_off;
-    uint2* lw;
+    uint4* lw;
     uint4* urank;
     unsigned long long lw_cap;
     uint8_t* flag;
@@ -207,20 +209,26 @@ struct Plan {
         cursor_b = cv.take<uint32_t>(mode == Mode::Match ? n : 0);
         big_count = cv.take<uint32_t>(2);
         window = mode == Mode::Match && d == 1;
-        win_shift = win_shift_;
-        num_win = window ? (uint32_t)ceil_div(E, 1ull << win_shift) : 0;
+        join = d > 1 && mode != Mode::Debug;
+        const bool lists = window || join;
+        win_shift = join ? 11 : win_shift_;
+        lcap = join ? 0xffffffffu : 1024u;
+        num_win = lists ? (uint32_t)ceil_div(E, 1ull << win_shift) : 0;
         lw_fill = cv.take<uint32_t>(num_win);
         num_flagged = cv.take<uint32_t>(1);
         lw_total = cv.take<unsigned long long>(1);
-        win_status = cv.take<unsigned long long>(window ? ceil_div(num_win, OFF_TILE) + 2 : 0);
+        win_status = cv.take<unsigned long long>(lists ? ceil_div(num_win, OFF_TILE) + 2 : 0);
         zero_bytes = (cv.off + 255) & ~(size_t)255;
-        windows = cv.take<uint4>(window ? num_win + 1 : 0);
+        windows = cv.take<uint4>(lists ? num_win + 1 : 0);
         lw_size = cv.take<uint32_t>(num_win);
-        lw_off = cv.take<unsigned long long>(window ? num_win + 1 : 0);
-        lw_cap = window ? (unsigned long long)E + 4096 : 0;
-        lw = cv.take<uint2>(lw_cap);
-        urank = cv.take<uint4>(window ? m : 0);
-        flag = cv.take<uint8_t>(window ? n : 0);
+        lw_off = cv.take<unsigned long long>(lists ? num_win + 1 : 0);
+        if (window) lw_cap = (unsigned long long)E + 4096;
+        else if (join) lw_cap = std::min<unsigned long long>(
+            std::max<unsigned long long>(16ull * E, 16ull << 20), 64ull << 20);
+        else lw_cap = 0;
+        lw = cv.take<uint4>(lw_cap);
+        urank = cv.take<uint4>(lists ? m : 0);
+        flag = cv.take<uint8_t>(lists ? n : 0);
         sort.tile_hist = cv.take<uint32_t>(stiles * RADIX);
         sort.offs = cv.take<unsigned long long>(stiles * RADIX + 1);
         const size_t ksz = batch ? 8 : 4;
@@ -334,7 +342,7 @@ int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
     }
     uint32_t* vals_sorted = (pl.passes & 1) ? pl.vals1 : pl.vals0;
     Records rec = pl.rec;
-    if (pl.window) {
+    if (pl.window || pl.join) {
         rec.windows = pl.windows;
         rec.win_shift = pl.win_shift;
     }
@@ -359,7 +367,9 @@ int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
     a.num_inst = job.num_inst;
     a.flag = nullptr;
     a.num_flagged = pl.num_flagged;
-    if (pl.window) {
+    a.sort_all = pl.join;
+    a.lcap = pl.lcap;
+    if (pl.window || pl.join) {
         a.flag = pl.flag;
         a.windows = pl.windows;
         a.win_shift = pl.win_shift;
@@ -397,7 +407,12 @@ int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
         L += launch_rank_count(rec, pl.n, pl.m, pl.cnt, dbg ? dbg->upd_cnt : nullptr, c->dstat, s);
     } else {
         L += launch_permute_keys(a, c->dstat, s);
-        L += launch_filter_count(a, c->dstat, s);
+        L += launch_window_sizes(a, c->dstat, s);
+        L += launch_offsets(pl.lw_size, pl.num_win, pl.lw_off, ~0ull, pl.lw_total,
+                            pl.win_status, c->dstat, s);
+        L += launch_tile_active(a, c->dstat, s);
+        L += launch_join(a, false, c->dstat, s);
+        L += launch_filter_count(a, c->dstat, s);  // flagged subscriptions only
     }
     mark(c, 4);
     if (dbg && dbg->sub_cnt && pl.n > 0)
@@ -417,9 +432,11 @@ int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
     }
     mark(c, 6);
     if (pl.window) L += launch_emit_window(a, c->dstat, s);
+    else if (pl.join && mode == Mode::Match) L += launch_join(a, true, c->dstat, s);
     else if (mode == Mode::Match) L += launch_emit_ranges(a, c->dstat, s);
     mark(c, 7);
-    if (pl.window && mode == Mode::Match) L += launch_emit_ranges(a, c->dstat, s);  // flagged only
+    if ((pl.window || pl.join) && mode == Mode::Match)
+        L += launch_emit_ranges(a, c->dstat, s);  // flagged subscriptions only
     if (mode == Mode::Match) L += launch_segment_sort(a, c->dstat, s);
     mark(c, 8);
   }

@@ -48,11 +48,16 @@ struct EmitArgs {
     uint32_t* lw_size;              // capped list sizes (0 when a list overflows)
     unsigned long long* lw_off;     // list offsets (exclusive scan of lw_size), numWin + 1
     uint32_t* lw_fill;              // per-window fill cursor (zeroed)
-    uint2* lw;                      // list storage {id, pos(U.hi)}, lw_cap entries
+    uint4* lw;                      // list storage {id, pos(U.hi), rank, 0}, lw_cap entries
+    uint32_t lcap;                  // longest boundary list a window may use
     uint4* urank;                   // {id, pos(lo), pos(hi), 0} by lower-endpoint rank, m
     unsigned long long lw_cap;
     const uint32_t* vals;           // sorted endpoint stream (payloads)
+    bool sort_all;                  // segment sort every subscription, not only flagged ones
 };
+
+// d > 1: tiled join of windows of subscriptions with chunks of candidates.
+int launch_join(const EmitArgs& a, bool write, DevStatus* st, cudaStream_t s);
 
 // Window path for d = 1.
 int launch_window_sizes(const EmitArgs& a, DevStatus* st, cudaStream_t s);

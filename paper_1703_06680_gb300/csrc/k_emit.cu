@@ -196,22 +196,24 @@ int launch_permute_keys(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
 
 int launch_filter_count(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
     int launches = 0;
-    if (a.n > 0) k_class_a<false, true><<<warp_grid(a.n), EMIT_BLOCK, 0, s>>>(a, st), ++launches;
-    if (a.m > 0) k_class_b<false, true><<<warp_grid(a.m), EMIT_BLOCK, 0, s>>>(a, st), ++launches;
+    const unsigned ga = a.flag ? 152u : warp_grid(a.n), gb = a.flag ? 152u : warp_grid(a.m);
+    if (a.n > 0) k_class_a<false, true><<<ga, EMIT_BLOCK, 0, s>>>(a, st), ++launches;
+    if (a.m > 0) k_class_b<false, true><<<gb, EMIT_BLOCK, 0, s>>>(a, st), ++launches;
     return launches;
 }
 
 // When the window path ran (flags in use), the range path only serves the few
 // flagged subscriptions and usually finds none: a small grid keeps that cheap.
 static unsigned fallback_grid(const EmitArgs& a, int64_t items) {
-    return a.flag ? 152u : warp_grid(items);
+    return a.flag && !a.sort_all ? 152u : warp_grid(items);
 }
 
 int launch_emit_ranges(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
     int launches = 0;
     if (a.d > 1) {
-        if (a.n > 0) k_class_a<true, true><<<warp_grid(a.n), EMIT_BLOCK, 0, s>>>(a, st), ++launches;
-        if (a.m > 0) k_class_b<true, true><<<warp_grid(a.m), EMIT_BLOCK, 0, s>>>(a, st), ++launches;
+        const unsigned ga = a.flag ? 152u : warp_grid(a.n), gb = a.flag ? 152u : warp_grid(a.m);
+        if (a.n > 0) k_class_a<true, true><<<ga, EMIT_BLOCK, 0, s>>>(a, st), ++launches;
+        if (a.m > 0) k_class_b<true, true><<<gb, EMIT_BLOCK, 0, s>>>(a, st), ++launches;
     } else {
         if (a.n > 0)
             k_class_a<true, false><<<fallback_grid(a, a.n), EMIT_BLOCK, 0, s>>>(a, st), ++launches;
@@ -229,12 +231,12 @@ int launch_emit_ranges(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
 __global__ void __launch_bounds__(EMIT_BLOCK) k_segsort_warp(EmitArgs a, DevStatus* st) {
     __shared__ uint32_t buf_all[EMIT_BLOCK / 32][WARP_SORT_MAX];
     if (read_error(st)) return;
-    if (a.flag && *(volatile uint32_t*)a.num_flagged == 0u) return;
+    if (a.flag && !a.sort_all && *(volatile uint32_t*)a.num_flagged == 0u) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t* buf = buf_all[warp];
     const int64_t warps = (int64_t)gridDim.x * (EMIT_BLOCK / 32);
     for (int64_t i = ((int64_t)blockIdx.x * EMIT_BLOCK + threadIdx.x) >> 5; i < a.n; i += warps) {
-        if (a.flag && !a.flag[i]) continue;
+        if (a.flag && !a.sort_all && !a.flag[i]) continue;
         const uint32_t c = a.cnt[i];
         if (c < 2) continue;
         if (c > WARP_SORT_MAX) {

@@ -1,0 +1,186 @@
+// a7 for d > 1: the dimension-0 sweep joined with the filter of dims 1..d-1,
+// tiled so that candidate keys are read once per window, not once per
+// subscription.
+//
+// Paper: Section 3 reduces d dimensions to d = 1 -- two rectangles intersect
+// iff every projection does -- and Algorithm 4 provides the dimension-0
+// candidates.  As in the d = 1 window path (k_window.cu), a window of the
+// sorted stream is one thread block; its dimension-0 candidates are the
+// updates active at the window boundary (the paper's UpdSet[p], the list L_w)
+// and the updates starting between the boundary and the farthest upper
+// endpoint of the window's subscriptions.  Here the candidates are streamed
+// through shared memory in chunks (positions plus keys of dims 1..d-1) and
+// every subscription of the window tests each chunk: Algorithm 1 on stream
+// positions for dimension 0 and on integer keys for the others.  The range
+// part of the candidates is in lower-endpoint order, so a subscription stops
+// at the first chunk that starts past its own upper endpoint.
+//
+// Pass 1 (count) stores each subscription's survivor count; after the offsets
+// scan, pass 2 (write) appends the survivors to the subscription's segment.
+// Segments are then sorted by update id (k_emit.cu).  Windows whose boundary
+// list does not fit flag their subscriptions for the range path.
+#include "emit.cuh"
+
+namespace ddm {
+
+constexpr int JOIN_BLOCK = 512;
+constexpr int JOIN_WARPS = JOIN_BLOCK / 32;
+constexpr uint32_t JOIN_CHUNK = 512;
+constexpr int JOIN_SHIFT = 11;  // windows of 2048 stream positions
+constexpr uint32_t JOIN_MAXSUB = 1u << JOIN_SHIFT;
+
+// Dynamic shared memory of one join block for d dimensions.
+__host__ __device__ inline size_t join_smem_bytes(int d) {
+    return (size_t)JOIN_MAXSUB * 4 * sizeof(uint32_t)         // sub lo, hi, id, count
+           + (size_t)JOIN_CHUNK * (sizeof(uint2) + sizeof(uint32_t))  // candidate pos, id
+           + (size_t)(d - 1) * JOIN_CHUNK * sizeof(uint2)       // candidate keys, dims 1..d-1
+           + 64;
+}
+
+template <bool WRITE>
+__global__ void __launch_bounds__(JOIN_BLOCK) k_join(EmitArgs a, DevStatus* st) {
+    extern __shared__ __align__(16) unsigned char jsm[];
+    uint32_t* s_lo = reinterpret_cast<uint32_t*>(jsm);
+    uint32_t* s_hi = s_lo + JOIN_MAXSUB;
+    uint32_t* s_id = s_hi + JOIN_MAXSUB;
+    uint32_t* s_cnt = s_id + JOIN_MAXSUB;
+    uint2* c_pos = reinterpret_cast<uint2*>(s_cnt + JOIN_MAXSUB);
+    uint32_t* c_id = reinterpret_cast<uint32_t*>(c_pos + JOIN_CHUNK);
+    uint2* c_key = reinterpret_cast<uint2*>(c_id + JOIN_CHUNK);  // [(d-1)][JOIN_CHUNK]
+    __shared__ uint32_t s_pmax, s_first;
+
+    if (read_error(st)) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const uint32_t w = blockIdx.x;
+    const int S = a.win_shift;
+    const int dd = a.d - 1;
+    const uint4 t0 = a.windows[w], t1 = a.windows[w + 1];
+    const uint32_t r0 = t0.x, ns = t1.x - t0.x;
+    if (ns == 0) return;
+    if (ns > JOIN_MAXSUB) {
+        if (tid == 0) raise_error(st, DDM_ERR_INTERNAL, 16);
+        return;
+    }
+    const uint32_t lw_n = t0.y - t0.z;
+    const bool overflow = !(lw_n <= a.lcap && a.lw_off[w] + lw_n <= a.lw_cap);
+    if (tid == 0) s_pmax = 0;
+    __syncthreads();
+    for (uint32_t k = tid; k < ns; k += JOIN_BLOCK) {
+        const uint32_t i = a.rec.sub_order[r0 + k];
+        const uint32_t pl = a.rec.s_lo[i].x, ph = a.rec.s_hi[i].x;
+        s_id[k] = i; s_lo[k] = pl; s_hi[k] = ph; s_cnt[k] = 0;
+        if (!WRITE) {  // the count pass decides the flags; the write pass reads them
+            a.flag[i] = overflow ? 1 : 0;
+            if (overflow) atomicAdd(a.num_flagged, 1u);
+        }
+        atomicMax(&s_pmax, ph);
+    }
+    __syncthreads();
+    if (overflow) return;
+    const uint32_t wend = min(max((s_pmax >> S) + 1, w + 1), a.num_win);
+    const uint32_t u0 = t0.y, u1 = a.windows[wend].y;
+    uint32_t nlow = 0;  // range part: updates starting in [wT, pmax), in rank order
+    for (uint32_t r = u0; r < u1; r += JOIN_BLOCK)
+        nlow += __syncthreads_count(r + tid < u1 && a.urank[r + tid].y < s_pmax);
+    const uint32_t W = lw_n + nlow;
+
+    for (uint32_t c0 = 0; c0 < W; c0 += JOIN_CHUNK) {
+        const uint32_t clen = min(JOIN_CHUNK, W - c0);
+        const uint32_t cpad = (clen + 31) & ~31u;
+        for (uint32_t t = tid; t < cpad; t += JOIN_BLOCK) {
+            const uint32_t k = c0 + t;
+            if (t < clen) {
+                uint32_t id, pl, ph, rank;
+                if (k < lw_n) {
+                    const uint4 e = a.lw[a.lw_off[w] + k];
+                    id = e.x; ph = e.y; rank = e.z; pl = 0u;  // starts before the window
+                } else {
+                    rank = u0 + (k - lw_n);
+                    const uint4 e = a.urank[rank];
+                    id = e.x; pl = e.y; ph = e.z;
+                }
+                c_pos[t] = make_uint2(pl, ph);
+                c_id[t] = id;
+                for (int q = 0; q < dd; ++q) c_key[q * JOIN_CHUNK + t] = a.updK[(int64_t)q * a.m + rank];
+            } else {
+                c_pos[t] = make_uint2(0xffffffffu, 0u);  // never kept
+                c_id[t] = 0;
+                for (int q = 0; q < dd; ++q) c_key[q * JOIN_CHUNK + t] = make_uint2(1u, 0u);
+            }
+        }
+        if (tid == 0) s_first = c0 >= lw_n ? c_pos[0].x : 0u;  // first pos(lo) of a range chunk
+        __syncthreads();
+        const uint32_t first = s_first;
+        for (uint32_t k = warp; k < ns; k += JOIN_WARPS) {
+            const uint32_t pl = s_lo[k], ph = s_hi[k];
+            if (c0 >= lw_n && first >= ph) continue;  // every later candidate starts after S ends
+            uint2 own[DDM_MAX_DIMS - 1];
+#pragma unroll
+            for (int q = 0; q < DDM_MAX_DIMS - 1; ++q)
+                if (q < dd) own[q] = a.subK[(int64_t)q * a.n + r0 + k];
+            const uint32_t i = s_id[k];
+            uint32_t cur = s_cnt[k];
+            int2* seg = nullptr;
+            uint32_t c = 0;
+            int32_t i_out = (int32_t)i;
+            uint32_t j_base = 0;
+            if (WRITE) {
+                seg = reinterpret_cast<int2*>(a.pairs) + a.off[i];
+                c = a.cnt[i];
+                if (a.inst_sub_base) {
+                    const int b = inst_of(a.inst_sub_base, a.num_inst, i);
+                    i_out -= (int32_t)a.inst_sub_base[b];
+                    j_base = (uint32_t)a.inst_upd_base[b];
+                }
+            }
+            for (uint32_t kk = lane; kk < cpad; kk += 32) {
+                const uint2 p = c_pos[kk];
+                bool pass = (p.x < ph) & (p.y > pl);
+#pragma unroll
+                for (int q = 0; q < DDM_MAX_DIMS - 1; ++q) {
+                    if (q < dd) {
+                        const uint2 u = c_key[q * JOIN_CHUNK + kk];
+                        pass &= (own[q].x <= u.y) & (u.x <= own[q].y);
+                    }
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, pass);
+                if (WRITE) {
+                    const uint32_t r = cur + __popc(bal & lt);
+                    if (pass && r < c) seg[r] = make_int2(i_out, (int32_t)(c_id[kk] - j_base));
+                }
+                cur += __popc(bal);
+            }
+            if (lane == 0) s_cnt[k] = cur;
+        }
+        __syncthreads();
+    }
+    for (uint32_t k = tid; k < ns; k += JOIN_BLOCK) {
+        const uint32_t i = s_id[k];
+        if (!WRITE) a.cnt[i] = s_cnt[k];
+        else if (s_cnt[k] != a.cnt[i]) raise_error(st, DDM_ERR_INTERNAL, 17);
+    }
+}
+
+int launch_join(const EmitArgs& a, bool write, DevStatus* st, cudaStream_t s) {
+    if (a.num_win == 0 || a.n == 0) return 0;
+    if (a.win_shift != JOIN_SHIFT) return -1;
+    const size_t smem = join_smem_bytes(a.d);
+    static unsigned long long attr_set[2] = {0, 0};  // per device, per pass
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int w = write ? 1 : 0;
+    if (dev < 0 || dev >= 64 || !(attr_set[w] & (1ull << dev))) {
+        const size_t max_smem = join_smem_bytes(DDM_MAX_DIMS);
+        if (write)
+            cudaFuncSetAttribute(k_join<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
+        else
+            cudaFuncSetAttribute(k_join<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
+        if (dev >= 0 && dev < 64) attr_set[w] |= 1ull << dev;
+    }
+    if (write) k_join<true><<<a.num_win, JOIN_BLOCK, smem, s>>>(a, st);
+    else k_join<false><<<a.num_win, JOIN_BLOCK, smem, s>>>(a, st);
+    return 1;
+}
+
+}  // namespace ddm

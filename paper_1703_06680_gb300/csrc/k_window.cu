@@ -26,7 +26,7 @@
 namespace ddm {
 
 constexpr int WIN_BLOCK = 256;
-constexpr uint32_t LCAP = 1024;       // active updates per window boundary
+// The longest boundary list a window may use is a.lcap (1024 on this path).
 constexpr uint32_t WCAP = 1024;       // candidates per window
 constexpr uint32_t LONG_SPAN = 512;   // positions; longer subscriptions use the range path
 constexpr int MAX_WIN_SHIFT = 9;      // windows of at most 512 positions
@@ -38,18 +38,18 @@ __global__ void k_window_sizes(EmitArgs a) {
          w += gridDim.x * blockDim.x) {
         const uint4 t = a.windows[w];
         const uint32_t s = t.y - t.z;  // updates with pos(lo) < wT <= pos(hi)
-        a.lw_size[w] = s <= LCAP ? s : 0u;
+        a.lw_size[w] = s <= a.lcap ? s : 0u;
     }
 }
 
 __device__ __forceinline__ bool list_fits(const EmitArgs& a, uint32_t w, uint32_t s) {
-    return s <= LCAP && a.lw_off[w] + s <= a.lw_cap;
+    return s <= a.lcap && a.lw_off[w] + s <= a.lw_cap;
 }
 
 // One pass over the updates in lower-endpoint order (rank r, id = upd_order[r]):
 //  - the rank table urank[r] = {id, pos(lo), pos(hi)}, so that windows read
 //    their candidates contiguously;
-//  - the boundary lists: U contributes {id, pos(U.hi)} to every boundary w*T
+//  - the boundary lists: U contributes {id, pos(U.hi), rank} to every boundary w*T
 //    with pos(U.lo) < w*T <= pos(U.hi) (the paper's UpdSet at that boundary).
 __global__ void k_tile_active(EmitArgs a, DevStatus* st) {
     if (read_error(st)) return;
@@ -65,7 +65,7 @@ __global__ void k_tile_active(EmitArgs a, DevStatus* st) {
             const uint32_t s = t.y - t.z;
             if (!list_fits(a, w, s)) continue;
             const uint32_t slot = atomicAdd(&a.lw_fill[w], 1u);
-            if (slot < s) a.lw[a.lw_off[w] + slot] = make_uint2(j, ph);
+            if (slot < s) a.lw[a.lw_off[w] + slot] = make_uint4(j, ph, (uint32_t)r, 0u);
             else raise_error(st, DDM_ERR_INTERNAL, 10);
         }
     }
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(WIN_BLOCK) k_emit_window(EmitArgs a, DevStatus
         if (k < W) {
             uint32_t id, pl;
             if (k < lw_n) {
-                const uint2 e = a.lw[a.lw_off[w] + k];
+                const uint4 e = a.lw[a.lw_off[w] + k];
                 id = e.x; pl = 0u; pay[it] = e.y;  // starts before the window: pos(lo) < any pos(S.hi)
             } else {
                 const uint4 e = a.urank[u0 + k - lw_n];
