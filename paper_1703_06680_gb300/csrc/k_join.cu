@@ -31,7 +31,9 @@ constexpr uint32_t JOIN_MAXSUB = 1u << JOIN_SHIFT;
 
 // Dynamic shared memory of one join block for d dimensions.
 __host__ __device__ inline size_t join_smem_bytes(int d) {
-    return (size_t)JOIN_MAXSUB * 4 * sizeof(uint32_t)         // sub lo, hi, id, count
+    return (size_t)JOIN_MAXSUB * sizeof(unsigned long long)   // sub output offsets
+           + (size_t)JOIN_MAXSUB * 5 * sizeof(uint32_t)         // sub lo, hi, id, count, expected
+           + (size_t)(d - 1) * JOIN_MAXSUB * sizeof(uint2)      // sub keys, dims 1..d-1
            + (size_t)JOIN_CHUNK * (sizeof(uint2) + sizeof(uint32_t))  // candidate pos, id
            + (size_t)(d - 1) * JOIN_CHUNK * sizeof(uint2)       // candidate keys, dims 1..d-1
            + 64;
@@ -40,11 +42,14 @@ __host__ __device__ inline size_t join_smem_bytes(int d) {
 template <bool WRITE>
 __global__ void __launch_bounds__(JOIN_BLOCK) k_join(EmitArgs a, DevStatus* st) {
     extern __shared__ __align__(16) unsigned char jsm[];
-    uint32_t* s_lo = reinterpret_cast<uint32_t*>(jsm);
+    unsigned long long* s_off = reinterpret_cast<unsigned long long*>(jsm);
+    uint32_t* s_lo = reinterpret_cast<uint32_t*>(s_off + JOIN_MAXSUB);
     uint32_t* s_hi = s_lo + JOIN_MAXSUB;
     uint32_t* s_id = s_hi + JOIN_MAXSUB;
     uint32_t* s_cnt = s_id + JOIN_MAXSUB;
-    uint2* c_pos = reinterpret_cast<uint2*>(s_cnt + JOIN_MAXSUB);
+    uint32_t* s_exp = s_cnt + JOIN_MAXSUB;  // write pass: the count from pass 1
+    uint2* s_key = reinterpret_cast<uint2*>(s_exp + JOIN_MAXSUB);  // [(d-1)][JOIN_MAXSUB]
+    uint2* c_pos = s_key + (size_t)(a.d - 1) * JOIN_MAXSUB;
     uint32_t* c_id = reinterpret_cast<uint32_t*>(c_pos + JOIN_CHUNK);
     uint2* c_key = reinterpret_cast<uint2*>(c_id + JOIN_CHUNK);  // [(d-1)][JOIN_CHUNK]
     __shared__ uint32_t s_pmax, s_first;
@@ -70,6 +75,12 @@ __global__ void __launch_bounds__(JOIN_BLOCK) k_join(EmitArgs a, DevStatus* st) 
         const uint32_t i = a.rec.sub_order[r0 + k];
         const uint32_t pl = a.rec.s_lo[i].x, ph = a.rec.s_hi[i].x;
         s_id[k] = i; s_lo[k] = pl; s_hi[k] = ph; s_cnt[k] = 0;
+        if (WRITE) {
+            s_off[k] = a.off[i];
+            s_exp[k] = a.cnt[i];
+        }
+        for (int q = 0; q < a.d - 1; ++q)  // keys of dims 1..d-1 (sub_order rank layout)
+            s_key[q * JOIN_MAXSUB + k] = a.subK[(int64_t)q * a.n + r0 + k];
         if (!WRITE) {  // the count pass decides the flags; the write pass reads them
             a.flag[i] = overflow ? 1 : 0;
             if (overflow) atomicAdd(a.num_flagged, 1u);
@@ -118,7 +129,7 @@ __global__ void __launch_bounds__(JOIN_BLOCK) k_join(EmitArgs a, DevStatus* st) 
             uint2 own[DDM_MAX_DIMS - 1];
 #pragma unroll
             for (int q = 0; q < DDM_MAX_DIMS - 1; ++q)
-                if (q < dd) own[q] = a.subK[(int64_t)q * a.n + r0 + k];
+                if (q < dd) own[q] = s_key[q * JOIN_MAXSUB + k];
             const uint32_t i = s_id[k];
             uint32_t cur = s_cnt[k];
             int2* seg = nullptr;
@@ -126,8 +137,8 @@ __global__ void __launch_bounds__(JOIN_BLOCK) k_join(EmitArgs a, DevStatus* st) 
             int32_t i_out = (int32_t)i;
             uint32_t j_base = 0;
             if (WRITE) {
-                seg = reinterpret_cast<int2*>(a.pairs) + a.off[i];
-                c = a.cnt[i];
+                seg = reinterpret_cast<int2*>(a.pairs) + s_off[k];
+                c = s_exp[k];
                 if (a.inst_sub_base) {
                     const int b = inst_of(a.inst_sub_base, a.num_inst, i);
                     i_out -= (int32_t)a.inst_sub_base[b];
