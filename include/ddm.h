@@ -145,8 +145,13 @@ int ddm_count_noalloc(const ddm_regions *regions, void *cuda_stream, uint64_t *K
  *   DDM_PARAM_WIN_SHIFT   log2 of the window length of the d = 1 emission, in
  *                         sorted-stream positions: 6 .. 9 (default 8).
  * Returns DDM_ERR_INVALID for an unknown parameter or a value out of range.
+ *   DDM_PARAM_ND_PATH     strategy for d > 1: 0 = automatic (default: the tiled
+ *                         join for d >= 3, range expansion for d = 2, as
+ *                         measured on GB300), 1 = tiled join, 2 = range
+ *                         expansion.  Results are identical; only speed differs.
  */
 #define DDM_PARAM_WIN_SHIFT 1
+#define DDM_PARAM_ND_PATH 2
 int ddm_set_param(ddm_ctx *ctx, int param, int64_t value);
 
 /*

@@ -26,6 +26,7 @@ DDM_ERR_CUDA = -5
 DDM_ERR_INTERNAL = -6
 MAX_DIMS = 8
 PARAM_WIN_SHIFT = 1
+PARAM_ND_PATH = 2
 
 
 class DDMError(RuntimeError):

@@ -13,10 +13,12 @@ import math
 import os
 import statistics
 
-from ._lib import PARAM_WIN_SHIFT
+from ._lib import PARAM_ND_PATH, PARAM_WIN_SHIFT
 
-CANDIDATES = {PARAM_WIN_SHIFT: (7, 8, 9)}
-NAMES = {PARAM_WIN_SHIFT: "win_shift"}
+# Candidate values per tunable, and which dimensionalities a tunable affects.
+CANDIDATES = {PARAM_WIN_SHIFT: (7, 8, 9), PARAM_ND_PATH: (1, 2)}
+NAMES = {PARAM_WIN_SHIFT: "win_shift", PARAM_ND_PATH: "nd_path"}
+APPLIES = {PARAM_WIN_SHIFT: lambda d: d == 1, PARAM_ND_PATH: lambda d: d > 1}
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
 
@@ -54,6 +56,8 @@ def tune(ctx, tensors, reps: int = 5, cache_path: str = DEFAULT_CACHE) -> dict:
     stream = ctx.stream
     chosen = {"key": key}
     for param, values in CANDIDATES.items():
+        if not APPLIES[param](d):
+            continue
         best, best_ms, times = None, float("inf"), {}
         for v in values:
             ctx.set_param(param, v)

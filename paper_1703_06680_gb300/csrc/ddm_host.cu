@@ -37,6 +37,7 @@ struct ddm_ctx {
     bool prof = false;
     unsigned long long* last_inst_off = nullptr;  // device, batched calls
     int win_shift = 8;                            // DDM_PARAM_WIN_SHIFT
+    int nd_path = 0;                              // DDM_PARAM_ND_PATH
     cudaEvent_t ev[DDM_STAGES + 1] = {};
 };
 
@@ -195,7 +196,7 @@ struct Plan {
     size_t total;
 
     void layout(char* base, int d_, int64_t n_, int64_t m_, Mode mode, int num_inst_,
-                int win_shift_ = 8) {
+                int win_shift_ = 8, int nd_path = 0) {
         d = d_; n = n_; m = m_; E = 2 * (n + m); num_inst = num_inst_;
         const bool batch = num_inst > 0;
         passes = batch ? (int)ceil_div(32 + ceil_log2(num_inst), RADIX_BITS) : 4;
@@ -209,7 +210,7 @@ struct Plan {
         cursor_b = cv.take<uint32_t>(mode == Mode::Match ? n : 0);
         big_count = cv.take<uint32_t>(2);
         window = mode == Mode::Match && d == 1;
-        join = d > 1 && mode != Mode::Debug;
+        join = d > 1 && mode != Mode::Debug && (nd_path == 1 || (nd_path == 0 && d >= 3));
         const bool lists = window || join;
         win_shift = join ? 11 : win_shift_;
         lcap = join ? 0xffffffffu : 1024u;
@@ -278,12 +279,12 @@ enum class Phase { All, Prefix, Suffix };
 int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
             const DebugOut* dbg, Phase phase = Phase::All) {
     Plan pl;
-    pl.layout(nullptr, job.d, job.n, job.m, mode, job.num_inst, c->win_shift);
+    pl.layout(nullptr, job.d, job.n, job.m, mode, job.num_inst, c->win_shift, c->nd_path);
     if (phase == Phase::Suffix && pl.total > c->ws_size)
         return fail(c, DDM_ERR_INTERNAL, "emission phase without its prefix");
     int rc = ensure(c, &c->ws, &c->ws_size, pl.total);
     if (rc) return rc;
-    pl.layout(c->ws, job.d, job.n, job.m, mode, job.num_inst, c->win_shift);
+    pl.layout(c->ws, job.d, job.n, job.m, mode, job.num_inst, c->win_shift, c->nd_path);
     cudaStream_t s = c->stream;
     const bool batch = job.num_inst > 0;
     const bool do_prefix = phase != Phase::Suffix, do_suffix = phase != Phase::Prefix;
@@ -407,12 +408,14 @@ int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
         L += launch_rank_count(rec, pl.n, pl.m, pl.cnt, dbg ? dbg->upd_cnt : nullptr, c->dstat, s);
     } else {
         L += launch_permute_keys(a, c->dstat, s);
-        L += launch_window_sizes(a, c->dstat, s);
-        L += launch_offsets(pl.lw_size, pl.num_win, pl.lw_off, ~0ull, pl.lw_total,
-                            pl.win_status, c->dstat, s);
-        L += launch_tile_active(a, c->dstat, s);
-        L += launch_join(a, false, c->dstat, s);
-        L += launch_filter_count(a, c->dstat, s);  // flagged subscriptions only
+        if (pl.join) {
+            L += launch_window_sizes(a, c->dstat, s);
+            L += launch_offsets(pl.lw_size, pl.num_win, pl.lw_off, ~0ull, pl.lw_total,
+                                pl.win_status, c->dstat, s);
+            L += launch_tile_active(a, c->dstat, s);
+            L += launch_join(a, false, c->dstat, s);
+        }
+        L += launch_filter_count(a, c->dstat, s);  // with the join: flagged subscriptions only
     }
     mark(c, 4);
     if (dbg && dbg->sub_cnt && pl.n > 0)
@@ -545,6 +548,11 @@ int ddm_set_param(ddm_ctx* c, int param, int64_t value) {
     if (param == DDM_PARAM_WIN_SHIFT) {
         if (value < 6 || value > 9) return fail(c, DDM_ERR_INVALID, "window shift must be 6..9");
         c->win_shift = (int)value;
+        return DDM_OK;
+    }
+    if (param == DDM_PARAM_ND_PATH) {
+        if (value < 0 || value > 2) return fail(c, DDM_ERR_INVALID, "nd path must be 0..2");
+        c->nd_path = (int)value;
         return DDM_OK;
     }
     return fail(c, DDM_ERR_INVALID, "unknown parameter");

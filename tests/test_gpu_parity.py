@@ -187,3 +187,34 @@ def test_deterministic(ctx):
     a = gpu_pairs(ctx, reg)
     b = gpu_pairs(ctx, reg)
     assert np.array_equal(a, b)
+
+
+# --- both d > 1 strategies (tiled join, range expansion) against the oracle -----------
+
+@pytest.fixture(scope="module", params=[1, 2], ids=["join", "ranges"])
+def ctx_path(request):
+    import paper_1703_06680_gb300 as ddm
+    ddm.build_library()
+    c = ddm.Context(0)
+    c.set_param(ddm._lib.PARAM_ND_PATH, request.param)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("d,alpha", [(2, 1.0), (2, 100.0), (3, 1.0), (3, 100.0)])
+def test_nd_paths_reduced(ctx_path, d, alpha):
+    assert_parity(ctx_path, synth.large_nd(d, alpha, N=60_001))
+
+
+def test_nd_paths_tiny_and_mixed(ctx_path):
+    rng = np.random.default_rng(21)
+    for s in range(120):
+        d = 2 + s % 2
+        reg = tiny_grid_instance(rng, d, int(rng.integers(0, 70)), int(rng.integers(0, 70)))
+        assert_parity(ctx_path, reg)
+    n, m = 15_000, 12_000
+    def ext(c):
+        lo = (rng.random((3, c)) * 1e5).astype(np.float32)
+        side = np.exp(rng.normal(5.0, 2.0, size=(3, c))).astype(np.float32)
+        return lo, (lo + side).astype(np.float32)
+    assert_parity(ctx_path, synth.Regions(*ext(n), *ext(m)))
