@@ -148,9 +148,9 @@ __global__ void __launch_bounds__(EMIT_BLOCK) k_class_b(EmitArgs a, DevStatus* s
     if (a.flag && *(volatile uint32_t*)a.num_flagged == 0u) return;
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (EMIT_BLOCK / 32);
-    // Updates in lower-endpoint order (neighbouring warps share sub_order ranges).
-    for (int64_t q = ((int64_t)blockIdx.x * EMIT_BLOCK + threadIdx.x) >> 5; q < a.m; q += warps) {
-        const int64_t j = a.rec.upd_order[q];
+    // Updates in id order: neighbouring updates in stream order would target the
+    // same subscriptions' counters at once (atomic contention).
+    for (int64_t j = ((int64_t)blockIdx.x * EMIT_BLOCK + threadIdx.x) >> 5; j < a.m; j += warps) {
         const uint32_t A = a.rec.u_lo[j].y, B = a.rec.u_hi[j].y;
         if (A > B || B > (uint64_t)a.n) {  // guard against an upstream fault
             if (lane == 0) raise_error(st, DDM_ERR_INTERNAL, 9);
