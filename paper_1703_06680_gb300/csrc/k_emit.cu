@@ -101,12 +101,11 @@ __global__ void __launch_bounds__(EMIT_BLOCK) k_class_a(EmitArgs a, DevStatus* s
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int64_t warps = (int64_t)gridDim.x * (EMIT_BLOCK / 32);
-    // Counting visits subscriptions in lower-endpoint order (neighbouring warps
-    // expand overlapping ranges of upd_order, so candidate keys come from L1);
-    // writing visits them in id order (neighbouring warps fill neighbouring
-    // output segments, so the output stream stays nearly sequential).
-    for (int64_t r = ((int64_t)blockIdx.x * EMIT_BLOCK + threadIdx.x) >> 5; r < a.n; r += warps) {
-        const int64_t i = WRITE ? r : (int64_t)a.rec.sub_order[r];
+    // Subscriptions in id order: neighbouring warps fill neighbouring output
+    // segments.  (Visiting them in lower-endpoint order would let neighbouring
+    // warps share candidate keys in L1; measured, that only pays for the long
+    // ranges of d >= 3, which the tiled join serves by default.)
+    for (int64_t i = ((int64_t)blockIdx.x * EMIT_BLOCK + threadIdx.x) >> 5; i < a.n; i += warps) {
         if (a.flag && !a.flag[i]) continue;
         const uint32_t A = a.rec.s_lo[i].y, B = a.rec.s_hi[i].y;
         if (A > B || B > (uint64_t)a.m) {  // guard against an upstream fault
