@@ -212,18 +212,34 @@ __global__ void __launch_bounds__(WIN_BLOCK) k_emit_window(EmitArgs a, DevStatus
             i -= (int32_t)a.inst_sub_base[b];
             j_base = (uint32_t)a.inst_upd_base[b];
         }
-        int2* seg = reinterpret_cast<int2*>(a.pairs) + s_off[k];
-        const uint32_t c = s_cnt[k];
-        uint32_t running = 0;
-        for (uint32_t kk = lane; kk < Wpad; kk += 32) {
-            const unsigned long long kv = skey[kk];
-            const bool pass = (uint32_t)kv < ph && spay[kk] > pl;
-            const unsigned bal = __ballot_sync(0xffffffffu, pass);
-            const uint32_t r = running + __popc(bal & lt);
-            if (pass && r < c) seg[r] = make_int2(i, (int32_t)((uint32_t)(kv >> 32) - j_base));
-            running += __popc(bal);
+        int2* out = reinterpret_cast<int2*>(a.pairs) + s_off[k];  // next free slot of the segment
+        int2* const end = out + s_cnt[k];
+        // Two 32-wide chunks per iteration for independent shared-memory loads.
+        // Wpad is a multiple of 32, so every loop condition and the capacity
+        // check are uniform across the warp.
+        uint32_t kk = lane;
+        for (; kk + 32 < Wpad; kk += 64) {
+            const unsigned long long kv0 = skey[kk], kv1 = skey[kk + 32];
+            const uint32_t p0 = spay[kk], p1 = spay[kk + 32];
+            const bool pass0 = ((uint32_t)kv0 < ph) & (p0 > pl);
+            const bool pass1 = ((uint32_t)kv1 < ph) & (p1 > pl);
+            const unsigned b0 = __ballot_sync(0xffffffffu, pass0);
+            const unsigned b1 = __ballot_sync(0xffffffffu, pass1);
+            const int n0 = __popc(b0), n1 = __popc(b1);
+            if (out + n0 + n1 > end) break;  // uniform: never write past the segment
+            if (pass0) out[__popc(b0 & lt)] = make_int2(i, (int32_t)((uint32_t)(kv0 >> 32) - j_base));
+            if (pass1) out[n0 + __popc(b1 & lt)] = make_int2(i, (int32_t)((uint32_t)(kv1 >> 32) - j_base));
+            out += n0 + n1;
         }
-        if (lane == 0 && running != c) raise_error(st, DDM_ERR_INTERNAL, 12);
+        for (; kk < Wpad; kk += 32) {
+            const unsigned long long kv = skey[kk];
+            const bool pass = ((uint32_t)kv < ph) & (spay[kk] > pl);
+            const unsigned b = __ballot_sync(0xffffffffu, pass);
+            if (out + __popc(b) > end) break;
+            if (pass) out[__popc(b & lt)] = make_int2(i, (int32_t)((uint32_t)(kv >> 32) - j_base));
+            out += __popc(b);
+        }
+        if (lane == 0 && (out != end || kk < Wpad)) raise_error(st, DDM_ERR_INTERNAL, 12);
     }
 }
 
