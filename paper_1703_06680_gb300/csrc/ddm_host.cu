@@ -402,6 +402,16 @@ int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
                                          pl.vals1, pl.E, pl.passes, pl.sort, true, c->dstat, s);
     }
     mark(c, 2);
+    // The sweep scan writes one 16-byte rank record per endpoint at a random
+    // id.  Into sectors absent from L2 such partial writes cost a DRAM read
+    // each; clearing the record tables first (full-sector writes) leaves them
+    // resident in L2.  Measured: scan 57 -> 44 us including the clear, for
+    // E = 2e6.  (Overlapping the clear with the sort on a second stream was
+    // no faster: it slows key build and sort by as much as it saves.)
+    {
+        const size_t rec_bytes = (size_t)((char*)(rec.upd_order + pl.m) - (char*)rec.s_lo);
+        if (rec_bytes && pl.E > 0) CK(cudaMemsetAsync(rec.s_lo, 0, rec_bytes, s));
+    }
     L += launch_sweep_scan(vals_sorted, pl.E, pl.n, pl.m, rec, pl.scan_status, c->dstat, s);
     mark(c, 3);
     if (job.d == 1) {
