@@ -149,9 +149,14 @@ int ddm_count_noalloc(const ddm_regions *regions, void *cuda_stream, uint64_t *K
  *                         join for d >= 3, range expansion for d = 2, as
  *                         measured on GB300), 1 = tiled join, 2 = range
  *                         expansion.  Results are identical; only speed differs.
+ *   DDM_PARAM_PDL         1 (default) = launch the kernels of a call with
+ *                         programmatic dependent launch, so that each grid is
+ *                         scheduled while its predecessor finishes; 0 = plain
+ *                         stream order.  Results are identical.
  */
 #define DDM_PARAM_WIN_SHIFT 1
 #define DDM_PARAM_ND_PATH 2
+#define DDM_PARAM_PDL 3
 int ddm_set_param(ddm_ctx *ctx, int param, int64_t value);
 
 /*
@@ -164,6 +169,12 @@ int ddm_set_param(ddm_ctx *ctx, int param, int64_t value);
  * (a6/a7: the window kernel for d = 1, the range kernels for d > 1), 7 range
  * path of flagged subscriptions and per-segment sort (a6).
  * `launches` counts every kernel the context has launched since creation.
+ * ddm_set_profiling modes: 0 = off; 1 = events at every stage boundary;
+ * 2 + k (0 <= k < DDM_STAGES) = events only around stage k, so that a single
+ * stage can be timed with the least disturbance of the others (each event
+ * between two kernels also ends the overlap of programmatic dependent launch
+ * there); the other stage_ms entries are then 0.  DDM_ERR_INVALID for any
+ * other mode.
  */
 #define DDM_STAGES 8
 typedef struct {

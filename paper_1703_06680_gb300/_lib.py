@@ -27,6 +27,7 @@ DDM_ERR_INTERNAL = -6
 MAX_DIMS = 8
 PARAM_WIN_SHIFT = 1
 PARAM_ND_PATH = 2
+PARAM_PDL = 3
 
 
 class DDMError(RuntimeError):
@@ -222,8 +223,11 @@ class Context:
     def set_param(self, param: int, value: int):
         self._check(self._lib.ddm_set_param(self._h, param, value))
 
-    def set_profiling(self, on: bool):
-        self._check(self._lib.ddm_set_profiling(self._h, int(bool(on))))
+    def set_profiling(self, on: bool, stage: int | None = None):
+        """Per-stage CUDA events: on=True records every stage boundary; with `stage`
+        (an index into STAGE_NAMES) only that stage is bracketed."""
+        mode = 0 if not on else (1 if stage is None else 2 + int(stage))
+        self._check(self._lib.ddm_set_profiling(self._h, mode))
 
     def stats(self) -> dict:
         s = Stats()

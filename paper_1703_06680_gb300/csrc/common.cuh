@@ -2,11 +2,57 @@
 #pragma once
 
 #include <cstdint>
+#include <utility>
 #include <cuda_runtime.h>
 
 #include "ddm.h"
 
 namespace ddm {
+
+// ---------------------------------------------------------------------------
+// Programmatic dependent launch.  The kernels of one call run back to back on
+// one stream.  Launched with the programmatic-serialization attribute, a
+// kernel's blocks may be scheduled while its predecessor is still finishing,
+// which hides the launch and ramp-up of every grid behind the tail of the
+// previous one.  Memory ordering is unchanged: every kernel begins with
+// griddepcontrol.wait, which returns once the predecessor grid has completed
+// and its writes are visible (and, transitively, those of all earlier
+// kernels), before the kernel touches global memory.  It then lets its own
+// dependent be scheduled; that grid is launched only once every block of this
+// one has started, so waiting dependents occupy free slots only.  Without the
+// attribute both instructions are no-ops.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_begin() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Host switch for the attribute, set per call by the entry points (PdlScope).
+extern thread_local bool g_pdl;
+
+struct PdlScope {
+    bool prev;
+    explicit PdlScope(bool on) : prev(g_pdl) { g_pdl = on; }
+    ~PdlScope() { g_pdl = prev; }
+};
+
+// Launches kernel k on stream s, with the programmatic-serialization
+// attribute when the calling entry point enabled it.
+template <typename... P, typename... A>
+inline cudaError_t launch_k(void (*k)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                            A&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = g_pdl ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+}
 
 // ---------------------------------------------------------------------------
 // Endpoint payload: (kind << 30) | id, kind 0 = S lower, 1 = U lower,

@@ -18,6 +18,10 @@
 
 using namespace ddm;
 
+namespace ddm {
+thread_local bool g_pdl = false;
+}
+
 struct ddm_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -34,10 +38,11 @@ struct ddm_ctx {
     size_t out_size = 0;
     // counters and per-stage timing
     ddm_stats stats{};
-    bool prof = false;
+    int prof = 0;  // 0 off, 1 every stage boundary, 2 + k only around stage k
     unsigned long long* last_inst_off = nullptr;  // device, batched calls
     int win_shift = 8;                            // DDM_PARAM_WIN_SHIFT
     int nd_path = 0;                              // DDM_PARAM_ND_PATH
+    bool pdl = true;                              // DDM_PARAM_PDL
     cudaEvent_t ev[DDM_STAGES + 1] = {};
 };
 
@@ -131,7 +136,8 @@ enum class Mode { Count, Match, Debug };
 
 // Stage boundary k (0..DDM_STAGES): records an event when profiling.
 void mark(ddm_ctx* c, int k) {
-    if (c->prof) cudaEventRecord(c->ev[k], c->stream);
+    if (c->prof == 1 || (c->prof >= 2 && (k == c->prof - 2 || k == c->prof - 1)))
+        cudaEventRecord(c->ev[k], c->stream);
 }
 
 struct DebugOut {
@@ -286,6 +292,7 @@ int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
     if (rc) return rc;
     pl.layout(c->ws, job.d, job.n, job.m, mode, job.num_inst, c->win_shift, c->nd_path);
     cudaStream_t s = c->stream;
+    PdlScope pdl_scope(c->pdl);
     const bool batch = job.num_inst > 0;
     const bool do_prefix = phase != Phase::Suffix, do_suffix = phase != Phase::Prefix;
     if (do_prefix) {
@@ -408,9 +415,11 @@ int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
     // resident in L2.  Measured: scan 57 -> 44 us including the clear, for
     // E = 2e6.  (Overlapping the clear with the sort on a second stream was
     // no faster: it slows key build and sort by as much as it saves.)
+    // (The tables start 256-byte aligned and the next buffer starts 256-byte
+    // aligned too, so rounding up to 16-byte words stays inside them.)
     {
         const size_t rec_bytes = (size_t)((char*)(rec.upd_order + pl.m) - (char*)rec.s_lo);
-        if (rec_bytes && pl.E > 0) CK(cudaMemsetAsync(rec.s_lo, 0, rec_bytes, s));
+        if (pl.E > 0) L += launch_clear16(rec.s_lo, (rec_bytes + 15) / 16, s);
     }
     L += launch_sweep_scan(vals_sorted, pl.E, pl.n, pl.m, rec, pl.scan_status, c->dstat, s);
     mark(c, 3);
@@ -472,6 +481,10 @@ int finish(ddm_ctx* c, uint64_t* K_out) {
     if (c->prof) {
         for (int k = 0; k < DDM_STAGES; ++k) {
             float ms = 0.f;
+            if (c->prof >= 2 && k != c->prof - 2) {
+                c->stats.stage_ms[k] = 0.0;
+                continue;
+            }
             if (cudaEventElapsedTime(&ms, c->ev[k], c->ev[k + 1]) != cudaSuccess) {
                 cudaGetLastError();
                 ms = 0.f;
@@ -545,11 +558,13 @@ const char* ddm_last_error(const ddm_ctx* c) { return c ? c->err.c_str() : "null
 
 int ddm_set_profiling(ddm_ctx* c, int enable) {
     if (!c) return DDM_ERR_INVALID;
+    if (enable < 0 || enable >= 2 + DDM_STAGES)
+        return fail(c, DDM_ERR_INVALID, "profiling mode must be 0, 1 or 2 + stage");
     DeviceGuard g(c->device);
     if (enable && !c->ev[0]) {
         for (auto& e : c->ev) CK(cudaEventCreate(&e));
     }
-    c->prof = enable != 0;
+    c->prof = enable;
     return DDM_OK;
 }
 
@@ -563,6 +578,11 @@ int ddm_set_param(ddm_ctx* c, int param, int64_t value) {
     if (param == DDM_PARAM_ND_PATH) {
         if (value < 0 || value > 2) return fail(c, DDM_ERR_INVALID, "nd path must be 0..2");
         c->nd_path = (int)value;
+        return DDM_OK;
+    }
+    if (param == DDM_PARAM_PDL) {
+        if (value < 0 || value > 1) return fail(c, DDM_ERR_INVALID, "pdl must be 0 or 1");
+        c->pdl = value != 0;
         return DDM_OK;
     }
     return fail(c, DDM_ERR_INVALID, "unknown parameter");
@@ -785,6 +805,7 @@ int ddm_session_drift(ddm_session* s, void* stream, uint64_t seed, uint64_t step
         a.upd_hi[k] = const_cast<float*>(s->ptrs[3][k]);
     }
     a.seed = seed; a.step = step; a.sigma = sigma;
+    PdlScope pdl_scope(c->pdl);
     c->stats.launches += launch_drift(a, c->stream);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(c->stream));

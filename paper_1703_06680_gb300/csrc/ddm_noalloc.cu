@@ -130,6 +130,7 @@ extern "C" int ddm_count_noalloc(const ddm_regions* r, void* cuda_stream, uint64
     if (rc) return rc;
     L.carve(base, r->d, r->n, r->m);
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    PdlScope pdl_scope(true);
     const int64_t n = r->n, m = r->m;
     const uint64_t E = 2 * (uint64_t)(n + m);
     if (cudaMemsetAsync(base, 0, L.zero_bytes, s) != cudaSuccess) {

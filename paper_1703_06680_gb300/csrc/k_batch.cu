@@ -17,6 +17,7 @@ namespace ddm {
 
 // Gather every instance's coordinates into the concatenated arrays.
 __global__ void k_concat(BatchArgs b) {
+    pdl_begin();
     const int64_t R = b.n + b.m;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < R;
          r += (int64_t)gridDim.x * blockDim.x) {
@@ -40,6 +41,7 @@ __global__ void k_concat(BatchArgs b) {
 // Instance-tagged dimension-0 keys in [S lo | U lo | S hi | U hi] layout.
 __global__ void k_keybuild_batch(BatchArgs b, unsigned long long* __restrict__ keys,
                                  uint32_t* __restrict__ vals, DevStatus* st) {
+    pdl_begin();
     const int64_t R = b.n + b.m;
     bool bad = false;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < R;
@@ -62,6 +64,7 @@ __global__ void k_keybuild_batch(BatchArgs b, unsigned long long* __restrict__ k
 // inst_off[b] = first output pair of instance b = off[n_base[b]].
 __global__ void k_inst_offsets(BatchArgs b, const unsigned long long* __restrict__ off,
                                unsigned long long* __restrict__ inst_off) {
+    pdl_begin();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= b.num; i += gridDim.x * blockDim.x)
         inst_off[i] = b.n == 0 ? 0ull : off[b.n_base[i]];  // off[] exists only when n > 0
 }
@@ -73,20 +76,20 @@ static unsigned grid_for(uint64_t items) {
 
 int launch_concat(const BatchArgs& b, cudaStream_t s) {
     if (b.n + b.m == 0) return 0;
-    k_concat<<<grid_for(b.n + b.m), 256, 0, s>>>(b);
+    launch_k(k_concat, grid_for(b.n + b.m), 256, 0, s, b);
     return 1;
 }
 
 int launch_keybuild_batch(const BatchArgs& b, unsigned long long* keys, uint32_t* vals,
                           DevStatus* st, cudaStream_t s) {
     if (b.n + b.m == 0) return 0;
-    k_keybuild_batch<<<grid_for(b.n + b.m), 256, 0, s>>>(b, keys, vals, st);
+    launch_k(k_keybuild_batch, grid_for(b.n + b.m), 256, 0, s, b, keys, vals, st);
     return 1;
 }
 
 int launch_inst_offsets(const BatchArgs& b, const unsigned long long* off,
                         unsigned long long* inst_off, cudaStream_t s) {
-    k_inst_offsets<<<grid_for(b.num + 1), 256, 0, s>>>(b, off, inst_off);
+    launch_k(k_inst_offsets, grid_for(b.num + 1), 256, 0, s, b, off, inst_off);
     return 1;
 }
 

@@ -24,6 +24,7 @@ __device__ __forceinline__ unsigned long long splitmix64_at(unsigned long long s
 }
 
 __global__ void k_drift(DriftArgs a) {
+    pdl_begin();
     const int64_t count = (int64_t)a.d * (a.n + a.m);
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -50,7 +51,7 @@ int launch_drift(const DriftArgs& a, cudaStream_t s) {
     const int64_t count = (int64_t)a.d * (a.n + a.m);
     if (count == 0) return 0;
     uint64_t g = ceil_div((uint64_t)count, 256ull * 4);
-    k_drift<<<(unsigned)(g < 1 ? 1 : (g > 152 * 16 ? 152 * 16 : g)), 256, 0, s>>>(a);
+    launch_k(k_drift, (unsigned)(g < 1 ? 1 : (g > 152 * 16 ? 152 * 16 : g)), 256, 0, s, a);
     return 1;
 }
 

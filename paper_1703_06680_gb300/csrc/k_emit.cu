@@ -31,6 +31,7 @@ constexpr int BIG_ITEMS = 4;
 // a7 set-up: keys of dims 1..d-1 in rank order, with validation.
 // ---------------------------------------------------------------------------
 __global__ void k_permute_keys(EmitArgs a, DevStatus* st) {
+    pdl_begin();
     bool bad = false;
     const int64_t total = a.n + a.m;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < total;
@@ -96,6 +97,7 @@ __device__ __forceinline__ void put_pair(const EmitArgs& a, unsigned long long p
 // ---------------------------------------------------------------------------
 template <bool WRITE, bool FILTER>
 __global__ void __launch_bounds__(EMIT_BLOCK) k_class_a(EmitArgs a, DevStatus* st) {
+    pdl_begin();
     if (read_error(st)) return;
     if (a.flag && *(volatile uint32_t*)a.num_flagged == 0u) return;
     const int lane = threadIdx.x & 31;
@@ -145,6 +147,7 @@ __global__ void __launch_bounds__(EMIT_BLOCK) k_class_a(EmitArgs a, DevStatus* s
 // ---------------------------------------------------------------------------
 template <bool WRITE, bool FILTER>
 __global__ void __launch_bounds__(EMIT_BLOCK) k_class_b(EmitArgs a, DevStatus* st) {
+    pdl_begin();
     if (read_error(st)) return;
     if (a.flag && *(volatile uint32_t*)a.num_flagged == 0u) return;
     const int lane = threadIdx.x & 31;
@@ -191,15 +194,15 @@ int launch_permute_keys(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
     const int64_t total = a.n + a.m;
     if (a.d <= 1 || total == 0) return 0;
     int64_t g = ceil_div((uint64_t)total, 256 * 4);
-    k_permute_keys<<<(unsigned)(g < 1 ? 1 : (g > 152 * 16 ? 152 * 16 : g)), 256, 0, s>>>(a, st);
+    launch_k(k_permute_keys, (unsigned)(g < 1 ? 1 : (g > 152 * 16 ? 152 * 16 : g)), 256, 0, s, a, st);
     return 1;
 }
 
 int launch_filter_count(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
     int launches = 0;
     const unsigned ga = a.flag ? 152u : warp_grid(a.n), gb = a.flag ? 152u : warp_grid(a.m);
-    if (a.n > 0) k_class_a<false, true><<<ga, EMIT_BLOCK, 0, s>>>(a, st), ++launches;
-    if (a.m > 0) k_class_b<false, true><<<gb, EMIT_BLOCK, 0, s>>>(a, st), ++launches;
+    if (a.n > 0) launch_k(k_class_a<false, true>, ga, EMIT_BLOCK, 0, s, a, st), ++launches;
+    if (a.m > 0) launch_k(k_class_b<false, true>, gb, EMIT_BLOCK, 0, s, a, st), ++launches;
     return launches;
 }
 
@@ -213,13 +216,13 @@ int launch_emit_ranges(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
     int launches = 0;
     if (a.d > 1) {
         const unsigned ga = a.flag ? 152u : warp_grid(a.n), gb = a.flag ? 152u : warp_grid(a.m);
-        if (a.n > 0) k_class_a<true, true><<<ga, EMIT_BLOCK, 0, s>>>(a, st), ++launches;
-        if (a.m > 0) k_class_b<true, true><<<gb, EMIT_BLOCK, 0, s>>>(a, st), ++launches;
+        if (a.n > 0) launch_k(k_class_a<true, true>, ga, EMIT_BLOCK, 0, s, a, st), ++launches;
+        if (a.m > 0) launch_k(k_class_b<true, true>, gb, EMIT_BLOCK, 0, s, a, st), ++launches;
     } else {
         if (a.n > 0)
-            k_class_a<true, false><<<fallback_grid(a, a.n), EMIT_BLOCK, 0, s>>>(a, st), ++launches;
+            launch_k(k_class_a<true, false>, fallback_grid(a, a.n), EMIT_BLOCK, 0, s, a, st), ++launches;
         if (a.m > 0)
-            k_class_b<true, false><<<fallback_grid(a, a.m), EMIT_BLOCK, 0, s>>>(a, st), ++launches;
+            launch_k(k_class_b<true, false>, fallback_grid(a, a.m), EMIT_BLOCK, 0, s, a, st), ++launches;
     }
     return launches;
 }
@@ -230,6 +233,7 @@ int launch_emit_ranges(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
 // queued for k_segsort_big.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(EMIT_BLOCK) k_segsort_warp(EmitArgs a, DevStatus* st) {
+    pdl_begin();
     __shared__ uint32_t buf_all[EMIT_BLOCK / 32][WARP_SORT_MAX];
     if (read_error(st)) return;
     if (a.flag && !a.sort_all && *(volatile uint32_t*)a.num_flagged == 0u) return;
@@ -271,6 +275,7 @@ __global__ void __launch_bounds__(EMIT_BLOCK) k_segsort_warp(EmitArgs a, DevStat
 // buffer; the subscription ids are rewritten at the end.  Stable ranking as in
 // the onesweep pass (match_any within a warp, warp-ordered chunks).
 __global__ void __launch_bounds__(BIG_BLOCK) k_segsort_big(EmitArgs a, DevStatus* st) {
+    pdl_begin();
     constexpr int WARPS = BIG_BLOCK / 32;
     constexpr int CHUNK = BIG_BLOCK * BIG_ITEMS;
     __shared__ uint32_t hist[256];
@@ -370,8 +375,8 @@ __global__ void __launch_bounds__(BIG_BLOCK) k_segsort_big(EmitArgs a, DevStatus
 
 int launch_segment_sort(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
     if (a.n == 0) return 0;
-    k_segsort_warp<<<fallback_grid(a, a.n), EMIT_BLOCK, 0, s>>>(a, st);
-    k_segsort_big<<<152, BIG_BLOCK, 0, s>>>(a, st);
+    launch_k(k_segsort_warp, fallback_grid(a, a.n), EMIT_BLOCK, 0, s, a, st);
+    launch_k(k_segsort_big, 152, BIG_BLOCK, 0, s, a, st);
     return 2;
 }
 

@@ -41,6 +41,7 @@ __host__ __device__ inline size_t join_smem_bytes(int d) {
 
 template <bool WRITE>
 __global__ void __launch_bounds__(JOIN_BLOCK) k_join(EmitArgs a, DevStatus* st) {
+    pdl_begin();
     extern __shared__ __align__(16) unsigned char jsm[];
     unsigned long long* s_off = reinterpret_cast<unsigned long long*>(jsm);
     uint32_t* s_lo = reinterpret_cast<uint32_t*>(s_off + JOIN_MAXSUB);
@@ -189,8 +190,8 @@ int launch_join(const EmitArgs& a, bool write, DevStatus* st, cudaStream_t s) {
             cudaFuncSetAttribute(k_join<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
         if (dev >= 0 && dev < 64) attr_set[w] |= 1ull << dev;
     }
-    if (write) k_join<true><<<a.num_win, JOIN_BLOCK, smem, s>>>(a, st);
-    else k_join<false><<<a.num_win, JOIN_BLOCK, smem, s>>>(a, st);
+    if (write) launch_k(k_join<true>, a.num_win, JOIN_BLOCK, smem, s, a, st);
+    else launch_k(k_join<false>, a.num_win, JOIN_BLOCK, smem, s, a, st);
     return 1;
 }
 

@@ -24,6 +24,7 @@ __global__ void __launch_bounds__(KB_BLOCK)
 k_keybuild_d0(const float* __restrict__ sub_lo, const float* __restrict__ sub_hi,
               const float* __restrict__ upd_lo, const float* __restrict__ upd_hi, int64_t n,
               int64_t m, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, DevStatus* st) {
+    pdl_begin();
     const int64_t R = n + m;
     bool bad = false;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < R;
@@ -48,7 +49,7 @@ int launch_keybuild_d0(const float* sub_lo, const float* sub_hi, const float* up
     if (R == 0) return 0;
     int grid = (int)ceil_div((uint64_t)R, (uint64_t)KB_BLOCK * 4);
     grid = grid < 1 ? 1 : (grid > 152 * 16 ? 152 * 16 : grid);
-    k_keybuild_d0<<<grid, KB_BLOCK, 0, s>>>(sub_lo, sub_hi, upd_lo, upd_hi, n, m, keys, vals, st);
+    launch_k(k_keybuild_d0, grid, KB_BLOCK, 0, s, sub_lo, sub_hi, upd_lo, upd_hi, n, m, keys, vals, st);
     return 1;
 }
 
@@ -94,6 +95,7 @@ template <typename KeyT, int ITEMS>
 __global__ void __launch_bounds__(SORT_BLOCK)
 k_upsweep(const KeyT* __restrict__ keys, uint32_t E, int shift, uint32_t* __restrict__ tile_hist,
           uint32_t tiles, DevStatus* st) {
+    pdl_begin();
     constexpr int TILE = SORT_BLOCK * ITEMS;
     __shared__ alignas(128) KeyT sk[TILE];
     __shared__ uint32_t h[RADIX];
@@ -151,6 +153,7 @@ k_downsweep(const KeyT* __restrict__ keys_in, const uint32_t* __restrict__ vals_
             KeyT* __restrict__ keys_out, uint32_t* __restrict__ vals_out, uint32_t E, int shift,
             const unsigned long long* __restrict__ base, uint32_t tiles, int write_keys,
             DevStatus* st) {
+    pdl_begin();
     using Smem = DownSmem<KeyT, ITEMS>;
     constexpr int TILE = Smem::TILE;
     constexpr int WARPS = SORT_BLOCK / 32;
@@ -273,13 +276,13 @@ int launch_radix_sort(KeyT* keys0, uint32_t* vals0, KeyT* keys1, uint32_t* vals1
     int launches = 0;
     for (int p = 0; p < passes; ++p) {
         const int write_keys = !(skip_last_keys && p == passes - 1);
-        k_upsweep<KeyT, ITEMS><<<(unsigned)tiles, SORT_BLOCK, 0, s>>>(
-            kb[p & 1], (uint32_t)E, 8 * p, sc.tile_hist, (uint32_t)tiles, st);
+        launch_k(k_upsweep<KeyT, ITEMS>, (unsigned)tiles, SORT_BLOCK, 0, s, kb[p & 1], (uint32_t)E,
+                 8 * p, sc.tile_hist, (uint32_t)tiles, st);
         launches += 1 + launch_offsets(sc.tile_hist, (int64_t)cells, sc.offs, ~0ull, sc.total,
                                        sc.status + (size_t)p * sort_status_stride(E), st, s);
-        k_downsweep<KeyT, ITEMS><<<(unsigned)tiles, SORT_BLOCK, smem, s>>>(
-            kb[p & 1], vb[p & 1], kb[(p + 1) & 1], vb[(p + 1) & 1], (uint32_t)E, 8 * p, sc.offs,
-            (uint32_t)tiles, write_keys, st);
+        launch_k(k_downsweep<KeyT, ITEMS>, (unsigned)tiles, SORT_BLOCK, smem, s, kb[p & 1],
+                 vb[p & 1], kb[(p + 1) & 1], vb[(p + 1) & 1], (uint32_t)E, 8 * p, sc.offs,
+                 (uint32_t)tiles, write_keys, st);
         ++launches;
     }
     return launches;

@@ -33,6 +33,7 @@ __global__ void __launch_bounds__(SCAN_BLOCK)
 k_sweep_scan(const uint32_t* __restrict__ vals, uint32_t E, uint32_t n, uint32_t m,
              Records rec, unsigned long long* __restrict__ status,
              uint32_t* __restrict__ tile_counter, DevStatus* st) {
+    pdl_begin();
     __shared__ unsigned long long warp_sum[SCAN_BLOCK / 32];
     __shared__ unsigned long long tile_prefix[3];
     __shared__ uint32_t tile_id_s;
@@ -145,8 +146,26 @@ int launch_sweep_scan(const uint32_t* vals, uint64_t E, int64_t n, int64_t m, co
     // layout: 3 counters x (tiles + 1) words; the last word of counter 0's row
     // region doubles as the tile counter.
     uint32_t* counter = reinterpret_cast<uint32_t*>(status + 3 * (tiles + 1));
-    k_sweep_scan<<<(unsigned)tiles, SCAN_BLOCK, 0, s>>>(vals, (uint32_t)E, (uint32_t)n,
+    launch_k(k_sweep_scan, (unsigned)tiles, SCAN_BLOCK, 0, s, vals, (uint32_t)E, (uint32_t)n,
                                                         (uint32_t)m, rec, status, counter, st);
+    return 1;
+}
+
+// Zero fill of `words` 16-byte words, used to make the record tables resident
+// in L2 before the scan's scattered writes (a kernel rather than a memset, so
+// that it takes part in programmatic dependent launch).
+__global__ void k_clear16(uint4* __restrict__ p, uint64_t words) {
+    pdl_begin();
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        p[i] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+int launch_clear16(void* p, uint64_t words, cudaStream_t s) {
+    if (words == 0) return 0;
+    const uint64_t g = ceil_div(words, 256ull * 4);
+    launch_k(k_clear16, (unsigned)(g < 1 ? 1 : (g > 152 * 8 ? 152 * 8 : g)), 256, 0, s,
+             static_cast<uint4*>(p), words);
     return 1;
 }
 
@@ -155,6 +174,7 @@ int launch_sweep_scan(const uint32_t* vals, uint64_t E, int64_t n, int64_t m, co
 // ---------------------------------------------------------------------------
 __global__ void k_rank_count(const uint4* __restrict__ lo, const uint4* __restrict__ hi,
                              int64_t count, uint32_t* __restrict__ cnt, DevStatus* st) {
+    pdl_begin();
     if (read_error(st)) return;
     bool bad = false;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
@@ -173,9 +193,9 @@ int launch_rank_count(const Records& rec, int64_t n, int64_t m, uint32_t* cnt,
         return (unsigned)(g < 1 ? 1 : (g > 152 * 16 ? 152 * 16 : g));
     };
     int launches = 0;
-    if (n > 0) k_rank_count<<<grid(n), 256, 0, s>>>(rec.s_lo, rec.s_hi, n, cnt, st), ++launches;
+    if (n > 0) launch_k(k_rank_count, grid(n), 256, 0, s, rec.s_lo, rec.s_hi, n, cnt, st), ++launches;
     if (upd_cnt && m > 0)
-        k_rank_count<<<grid(m), 256, 0, s>>>(rec.u_lo, rec.u_hi, m, upd_cnt, st), ++launches;
+        launch_k(k_rank_count, grid(m), 256, 0, s, rec.u_lo, rec.u_hi, m, upd_cnt, st), ++launches;
     return launches;
 }
 
@@ -191,6 +211,7 @@ k_offsets(const uint32_t* __restrict__ cnt, uint32_t n, unsigned long long* __re
           unsigned long long cap, unsigned long long* total_out,
           unsigned long long* __restrict__ status, uint32_t* __restrict__ tile_counter,
           DevStatus* st) {
+    pdl_begin();
     __shared__ uint32_t s_in[OFF_TILE + OFF_TILE / 32];
     __shared__ unsigned long long s_out[OFF_TILE + OFF_TILE / 32];
     __shared__ unsigned long long warp_sum[OFF_BLOCK / 32];
@@ -267,7 +288,7 @@ int launch_offsets(const uint32_t* cnt, int64_t n, unsigned long long* off, uint
     if (n == 0) return 0;
     const uint64_t tiles = ceil_div((uint64_t)n, OFF_TILE);
     uint32_t* counter = reinterpret_cast<uint32_t*>(status + tiles);
-    k_offsets<<<(unsigned)tiles, OFF_BLOCK, 0, s>>>(cnt, (uint32_t)n, off, cap, total, status,
+    launch_k(k_offsets, (unsigned)tiles, OFF_BLOCK, 0, s, cnt, (uint32_t)n, off, cap, total, status,
                                                     counter, st);
     return 1;
 }

@@ -34,6 +34,7 @@ constexpr int NBUCKET = 256;          // buckets of the per-window id sort
 constexpr int WITEMS = WCAP / WIN_BLOCK;
 
 __global__ void k_window_sizes(EmitArgs a) {
+    pdl_begin();
     for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < a.num_win;
          w += gridDim.x * blockDim.x) {
         const uint4 t = a.windows[w];
@@ -52,6 +53,7 @@ __device__ __forceinline__ bool list_fits(const EmitArgs& a, uint32_t w, uint32_
 //  - the boundary lists: U contributes {id, pos(U.hi), rank} to every boundary w*T
 //    with pos(U.lo) < w*T <= pos(U.hi) (the paper's UpdSet at that boundary).
 __global__ void k_tile_active(EmitArgs a, DevStatus* st) {
+    pdl_begin();
     if (read_error(st)) return;
     const int S = a.win_shift;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < a.m;
@@ -72,6 +74,7 @@ __global__ void k_tile_active(EmitArgs a, DevStatus* st) {
 }
 
 __global__ void __launch_bounds__(WIN_BLOCK) k_emit_window(EmitArgs a, DevStatus* st) {
+    pdl_begin();
     constexpr uint32_t MAXSUB = 1u << MAX_WIN_SHIFT;
     __shared__ unsigned long long skey[WCAP];  // (update id << 32) | pos(U.lo)
     __shared__ uint32_t spay[WCAP];            // pos(U.hi)
@@ -251,20 +254,20 @@ static unsigned grid_for(uint64_t items, unsigned per_block, unsigned cap) {
 int launch_window_sizes(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
     (void)st;
     if (a.num_win == 0) return 0;
-    k_window_sizes<<<grid_for(a.num_win, 256, 152 * 8), 256, 0, s>>>(a);
+    launch_k(k_window_sizes, grid_for(a.num_win, 256, 152 * 8), 256, 0, s, a);
     return 1;
 }
 
 int launch_tile_active(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
     if (a.m == 0 || a.num_win == 0) return 0;
-    k_tile_active<<<grid_for(a.m, 256, 152 * 16), 256, 0, s>>>(a, st);
+    launch_k(k_tile_active, grid_for(a.m, 256, 152 * 16), 256, 0, s, a, st);
     return 1;
 }
 
 int launch_emit_window(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
     if (a.num_win == 0 || a.n == 0) return 0;
     if (a.win_shift > MAX_WIN_SHIFT) return -1;
-    k_emit_window<<<a.num_win, WIN_BLOCK, 0, s>>>(a, st);
+    launch_k(k_emit_window, a.num_win, WIN_BLOCK, 0, s, a, st);
     return 1;
 }
 

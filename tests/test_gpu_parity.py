@@ -218,3 +218,38 @@ def test_nd_paths_tiny_and_mixed(ctx_path):
         side = np.exp(rng.normal(5.0, 2.0, size=(3, c))).astype(np.float32)
         return lo, (lo + side).astype(np.float32)
     assert_parity(ctx_path, synth.Regions(*ext(n), *ext(m)))
+
+
+@pytest.mark.parametrize("d,alpha", [(1, 100.0), (1, 0.01), (2, 1.0), (3, 100.0)])
+def test_pdl_off_and_profiling_modes(d, alpha):
+    # Programmatic dependent launch and the stage events change only timing:
+    # every combination gives the oracle's result.
+    import paper_1703_06680_gb300 as ddm
+    reg = synth.large_1d(alpha, N=200_001) if d == 1 else synth.large_nd(d, alpha, N=60_001)
+    want = oracle.sbm(reg)
+    c = ddm.Context(0)
+    try:
+        for pdl in (0, 1):
+            c.set_param(ddm.PARAM_PDL, pdl)
+            for prof in ("off", "all", "emit", "sort"):
+                if prof == "off":
+                    c.set_profiling(False)
+                elif prof == "all":
+                    c.set_profiling(True)
+                else:
+                    stage = "emit" if prof == "emit" else "radix_sort"
+                    c.set_profiling(True, stage=ddm.STAGE_NAMES.index(stage))
+                got = gpu_pairs(c, reg)
+                assert np.array_equal(got, want), (pdl, prof)
+                st = c.stats()["stage_ms"]
+                if prof in ("emit", "sort"):
+                    stage = "emit" if prof == "emit" else "radix_sort"
+                    assert st[stage] > 0
+                    assert all(v == 0 for k, v in st.items() if k != stage)
+        with pytest.raises(ddm.DDMError):
+            c.set_param(ddm.PARAM_PDL, 2)
+        with pytest.raises(ddm.DDMError):
+            c.set_profiling(True, stage=len(ddm.STAGE_NAMES))
+    finally:
+        c.set_profiling(False)
+        c.close()
