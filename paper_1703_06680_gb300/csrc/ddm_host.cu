@@ -211,6 +211,11 @@ struct Plan {
         cv.base = base;
         sort.status = cv.take<unsigned long long>((size_t)passes * sort_status_stride(E));
         sort.total = cv.take<unsigned long long>(1);
+        {
+            const size_t gw = sort_group_words(stiles, passes);
+            sort.grp = cv.take<uint32_t>(gw);
+            if (gw == 0) sort.grp = nullptr;
+        }
         scan_status = cv.take<unsigned long long>(3 * (ceil_div(E, SCAN_TILE) + 1) + 1);
         off_status = cv.take<unsigned long long>(ceil_div(n, OFF_TILE) + 2);
         cursor_b = cv.take<uint32_t>(mode == Mode::Match ? n : 0);

@@ -81,6 +81,11 @@ struct NoallocLayout {
         st = s.take<DevStatus>(1);
         sort.status = s.take<unsigned long long>(4 * sort_status_stride(E));
         sort.total = s.take<unsigned long long>(1);
+        {
+            const size_t gw = sort_group_words(sort_tiles<uint32_t>(E), 4);
+            sort.grp = s.take<uint32_t>(gw);
+            if (gw == 0) sort.grp = nullptr;
+        }
         scan_status = s.take<unsigned long long>(3 * (ceil_div(E, SCAN_TILE) + 1) + 1);
         off_status = s.take<unsigned long long>(ceil_div((uint64_t)n, OFF_TILE) + 2);
         zero_bytes = (s.off + 255) & ~(size_t)255;

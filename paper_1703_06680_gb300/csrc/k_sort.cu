@@ -1,8 +1,10 @@
 // a1: endpoint key build with fused digit histograms.
 // a2: LSD radix sort, 8-bit digits, per pass: tile digit histograms (upsweep),
-//     one flat exclusive scan of the digit-major (digit, tile) table with
-//     decoupled look-back (k_offsets), and a downsweep that ranks keys stably
-//     with warp ballots and scatters runs of equal digits coalesced.
+//     the (digit, tile) output bases -- for up to 1024 tiles computed inside
+//     the downsweep from group sums, else by one flat exclusive scan of the
+//     digit-major table with decoupled look-back (k_offsets) -- and a
+//     downsweep that ranks keys stably with warp ballots and scatters runs of
+//     equal digits coalesced.
 //
 // Paper: Algorithm 4 ("Insert x.lower and x.upper in T"; "Sort T in
 // non-decreasing order"), parallel sort phase of Section 4 (Asymptotic
@@ -87,14 +89,16 @@ __device__ __forceinline__ uint32_t digit_of(KeyT k, int shift) {
     return (uint32_t)(k >> shift) & (RADIX - 1);
 }
 
-// Upsweep: digit histogram of one tile, stored digit-major
-// (tile_hist[d * tiles + tile]) so that one flat exclusive scan yields every
-// (digit, tile) output base: all smaller digits first, then earlier tiles.
+// Upsweep: digit histogram of one tile.  Flat-scan mode (grp == NULL): stored
+// digit-major (tile_hist[d * tiles + tile]) so that one flat exclusive scan
+// yields every (digit, tile) output base: all smaller digits first, then
+// earlier tiles.  Fused mode: stored tile-major (tile_hist[tile * 256 + d])
+// and added into the sums of the tile's group (grp[group * 256 + d]).
 // A full tile arrives in shared memory by one TMA bulk copy.
 template <typename KeyT, int ITEMS>
 __global__ void __launch_bounds__(SORT_BLOCK)
 k_upsweep(const KeyT* __restrict__ keys, uint32_t E, int shift, uint32_t* __restrict__ tile_hist,
-          uint32_t tiles, DevStatus* st) {
+          uint32_t tiles, uint32_t* __restrict__ grp, DevStatus* st) {
     pdl_begin();
     constexpr int TILE = SORT_BLOCK * ITEMS;
     __shared__ alignas(128) KeyT sk[TILE];
@@ -122,7 +126,12 @@ k_upsweep(const KeyT* __restrict__ keys, uint32_t E, int shift, uint32_t* __rest
         }
     }
     __syncthreads();
-    tile_hist[(uint64_t)tid * tiles + tile] = h[tid];
+    if (grp) {
+        tile_hist[(uint64_t)tile * RADIX + tid] = h[tid];
+        if (h[tid]) atomicAdd(&grp[(tile >> SORT_GROUP_SHIFT) * RADIX + tid], h[tid]);
+    } else {
+        tile_hist[(uint64_t)tid * tiles + tile] = h[tid];
+    }
 }
 
 // Shared memory of one downsweep tile (dynamic, > 48 KB).
@@ -151,8 +160,8 @@ template <typename KeyT, int ITEMS>
 __global__ void __launch_bounds__(SORT_BLOCK, 3)
 k_downsweep(const KeyT* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
             KeyT* __restrict__ keys_out, uint32_t* __restrict__ vals_out, uint32_t E, int shift,
-            const unsigned long long* __restrict__ base, uint32_t tiles, int write_keys,
-            DevStatus* st) {
+            const unsigned long long* __restrict__ base, const uint32_t* __restrict__ tile_hist,
+            const uint32_t* __restrict__ grp, uint32_t tiles, int write_keys, DevStatus* st) {
     pdl_begin();
     using Smem = DownSmem<KeyT, ITEMS>;
     constexpr int TILE = Smem::TILE;
@@ -168,7 +177,23 @@ k_downsweep(const KeyT* __restrict__ keys_in, const uint32_t* __restrict__ vals_
         (&sm.whist[0][0])[t] = 0;
         (&sm.u.peers[0][0])[t] = 0;
     }
-    sm.gbase[tid] = (uint32_t)base[(uint64_t)tid * tiles + tile];
+    if (grp) {  // fused offsets (thread = digit)
+        const uint32_t g = tile >> SORT_GROUP_SHIFT;
+        const uint32_t ngroups = (tiles + (1u << SORT_GROUP_SHIFT) - 1) >> SORT_GROUP_SHIFT;
+        uint32_t total = 0, before = 0;
+#pragma unroll 8
+        for (uint32_t q = 0; q < ngroups; ++q) {
+            const uint32_t v = grp[q * RADIX + tid];
+            total += v;
+            before += q < g ? v : 0u;
+        }
+#pragma unroll 8
+        for (uint32_t t = g << SORT_GROUP_SHIFT; t < tile; ++t)
+            before += tile_hist[(uint64_t)t * RADIX + tid];
+        sm.gbase[tid] = block_excl_scan_256(total, sm.warp_tmp) + before;
+    } else {
+        sm.gbase[tid] = (uint32_t)base[(uint64_t)tid * tiles + tile];
+    }
     __syncthreads();
     if (full) {
         if (tid == 0) {
@@ -273,16 +298,20 @@ int launch_radix_sort(KeyT* keys0, uint32_t* vals0, KeyT* keys1, uint32_t* vals1
                              smem);
         if (dev >= 0 && dev < 64) attr_set |= 1ull << dev;
     }
+    const bool fused = sc.grp && tiles <= SORT_FUSED_MAX_TILES;
     int launches = 0;
     for (int p = 0; p < passes; ++p) {
         const int write_keys = !(skip_last_keys && p == passes - 1);
+        uint32_t* grp = fused ? sc.grp + (size_t)p * sort_groups(tiles) * RADIX : nullptr;
         launch_k(k_upsweep<KeyT, ITEMS>, (unsigned)tiles, SORT_BLOCK, 0, s, kb[p & 1], (uint32_t)E,
-                 8 * p, sc.tile_hist, (uint32_t)tiles, st);
-        launches += 1 + launch_offsets(sc.tile_hist, (int64_t)cells, sc.offs, ~0ull, sc.total,
+                 8 * p, sc.tile_hist, (uint32_t)tiles, grp, st);
+        ++launches;
+        if (!fused)
+            launches += launch_offsets(sc.tile_hist, (int64_t)cells, sc.offs, ~0ull, sc.total,
                                        sc.status + (size_t)p * sort_status_stride(E), st, s);
         launch_k(k_downsweep<KeyT, ITEMS>, (unsigned)tiles, SORT_BLOCK, smem, s, kb[p & 1],
                  vb[p & 1], kb[(p + 1) & 1], vb[(p + 1) & 1], (uint32_t)E, 8 * p, sc.offs,
-                 (uint32_t)tiles, write_keys, st);
+                 sc.tile_hist, grp, (uint32_t)tiles, write_keys, st);
         ++launches;
     }
     return launches;

@@ -23,15 +23,37 @@ inline uint64_t sort_tiles(uint64_t E) {
     return ceil_div(E, (uint64_t)SORT_BLOCK * sort_items<KeyT>());
 }
 
+// Fused offsets: with at most SORT_FUSED_MAX_TILES tiles, the downsweep
+// computes each (digit, tile) output base itself, and the flat scan between
+// upsweep and downsweep is not launched.  The upsweep then stores its
+// histogram tile-major and adds it into per-group sums (groups of 32 tiles);
+// the downsweep's base for digit d is
+//   sum over all groups and digits d' < d of the group sums   (digit start)
+// + sum over earlier groups of the group sums of d
+// + sum over earlier tiles of its own group of their counts of d,
+// at most 32 + 31 independent loads per thread (thread = digit).
+constexpr int SORT_GROUP_SHIFT = 5;
+constexpr uint64_t SORT_FUSED_MAX_TILES = 1024;
+
 // Scratch of the sort besides the two ping-pong key/value buffers:
 // tile_hist[256 * tiles] (u32), offs[256 * tiles + 1] (u64), per-pass scan
-// status words (zeroed, sort_status_stride() u64 per pass) and one u64 total.
+// status words (zeroed, sort_status_stride() u64 per pass), one u64 total,
+// and the per-pass group sums of the fused-offsets mode (zeroed,
+// sort_group_words() u32 in all; NULL selects the flat scan).
 struct SortScratch {
     uint32_t* tile_hist;
     unsigned long long* offs;
     unsigned long long* status;
     unsigned long long* total;
+    uint32_t* grp;
 };
+
+inline uint64_t sort_groups(uint64_t tiles) { return ceil_div(tiles, 1ull << SORT_GROUP_SHIFT); }
+
+// Group-sum words for `passes` passes (0 when the tiles exceed the fused limit).
+inline size_t sort_group_words(uint64_t tiles, int passes) {
+    return tiles <= SORT_FUSED_MAX_TILES ? (size_t)passes * sort_groups(tiles) * RADIX : 0;
+}
 
 // Status words of one pass's flat scan (sized for the 64-bit-key tiling, the
 // larger of the two).
