@@ -52,23 +52,50 @@ __device__ __forceinline__ bool list_fits(const EmitArgs& a, uint32_t w, uint32_
 //    their candidates contiguously;
 //  - the boundary lists: U contributes {id, pos(U.hi), rank} to every boundary w*T
 //    with pos(U.lo) < w*T <= pos(U.hi) (the paper's UpdSet at that boundary).
+// The lanes of a warp hold consecutive ranks, whose lower endpoints are close
+// in the stream, so they mostly cross the same boundaries: the warp walks the
+// union of its lanes' boundary ranges and reserves the slots of all lanes
+// crossing boundary w with one atomic (order inside a list is irrelevant: the
+// window kernel sorts its candidates by id).
 __global__ void k_tile_active(EmitArgs a, DevStatus* st) {
     pdl_begin();
     if (read_error(st)) return;
     const int S = a.win_shift;
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < a.m;
-         r += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t j = a.rec.upd_order[r];
-        const uint32_t pl = a.rec.u_lo[j].x, ph = a.rec.u_hi[j].x;
-        a.urank[r] = make_uint4(j, pl, ph, 0u);
-        const uint32_t w1 = min(ph >> S, a.num_win - 1);
-        for (uint32_t w = (pl >> S) + 1; w <= w1; ++w) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); r0 < a.m;
+         r0 += stride) {
+        const int64_t r = r0 + lane;
+        const bool valid = r < a.m;
+        uint32_t j = 0, ph = 0, wlo = 1, whi = 0;  // empty boundary range
+        if (valid) {
+            j = a.rec.upd_order[r];
+            const uint32_t pl = a.rec.u_lo[j].x;
+            ph = a.rec.u_hi[j].x;
+            a.urank[r] = make_uint4(j, pl, ph, 0u);
+            wlo = (pl >> S) + 1;
+            whi = min(ph >> S, a.num_win - 1);
+        }
+        const bool any = valid && wlo <= whi;
+        const uint32_t wmin = __reduce_min_sync(0xffffffffu, any ? wlo : 0xffffffffu);
+        const uint32_t wmax = __reduce_max_sync(0xffffffffu, any ? whi : 0u);
+        for (uint32_t w = wmin; w <= wmax; ++w) {  // no iteration when no lane crosses one
+            const bool mine = any && wlo <= w && w <= whi;
+            const unsigned mask = __ballot_sync(0xffffffffu, mine);
+            if (!mask) continue;
             const uint4 t = a.windows[w];
             const uint32_t s = t.y - t.z;
             if (!list_fits(a, w, s)) continue;
-            const uint32_t slot = atomicAdd(&a.lw_fill[w], 1u);
-            if (slot < s) a.lw[a.lw_off[w] + slot] = make_uint4(j, ph, (uint32_t)r, 0u);
-            else raise_error(st, DDM_ERR_INTERNAL, 10);
+            const int leader = __ffs(mask) - 1;
+            uint32_t base = 0;
+            if (lane == leader) base = atomicAdd(&a.lw_fill[w], (uint32_t)__popc(mask));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (mine) {
+                const uint32_t slot = base + __popc(mask & lt);
+                if (slot < s) a.lw[a.lw_off[w] + slot] = make_uint4(j, ph, (uint32_t)r, 0u);
+                else raise_error(st, DDM_ERR_INTERNAL, 10);
+            }
         }
     }
 }
