@@ -181,7 +181,6 @@ struct Plan {
     unsigned long long* win_status;
     size_t zero_bytes;
     uint4* windows;
-    uint32_t* lw_size;
     unsigned long long* lw_off;
     uint4* lw;
     uint4* urank;
@@ -232,7 +231,6 @@ struct Plan {
         win_status = cv.take<unsigned long long>(lists ? ceil_div(num_win, OFF_TILE) + 2 : 0);
         zero_bytes = (cv.off + 255) & ~(size_t)255;
         windows = cv.take<uint4>(lists ? num_win + 1 : 0);
-        lw_size = cv.take<uint32_t>(num_win);
         lw_off = cv.take<unsigned long long>(lists ? num_win + 1 : 0);
         if (window) lw_cap = (unsigned long long)E + 4096;
         else if (join) lw_cap = std::min<unsigned long long>(
@@ -387,7 +385,6 @@ int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
         a.windows = pl.windows;
         a.win_shift = pl.win_shift;
         a.num_win = pl.num_win;
-        a.lw_size = pl.lw_size;
         a.lw_off = pl.lw_off;
         a.lw_fill = pl.lw_fill;
         a.lw = pl.lw;
@@ -428,14 +425,17 @@ int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
     }
     L += launch_sweep_scan(vals_sorted, pl.E, pl.n, pl.m, rec, pl.scan_status, c->dstat, s);
     mark(c, 3);
+    // d = 1: the counts are formed inside the offsets scan (one kernel for a4
+    // and a5), except for diagnostics, which also want the update counts.
+    const bool fused_counts = job.d == 1 && !dbg;
     if (job.d == 1) {
-        L += launch_rank_count(rec, pl.n, pl.m, pl.cnt, dbg ? dbg->upd_cnt : nullptr, c->dstat, s);
+        if (!fused_counts)
+            L += launch_rank_count(rec, pl.n, pl.m, pl.cnt, dbg ? dbg->upd_cnt : nullptr, c->dstat, s);
     } else {
         L += launch_permute_keys(a, c->dstat, s);
         if (pl.join) {
-            L += launch_window_sizes(a, c->dstat, s);
-            L += launch_offsets(pl.lw_size, pl.num_win, pl.lw_off, ~0ull, pl.lw_total,
-                                pl.win_status, c->dstat, s);
+            L += launch_window_offsets(pl.windows, pl.num_win, pl.lcap, pl.lw_off, pl.lw_total,
+                                       pl.win_status, c->dstat, s);
             L += launch_tile_active(a, c->dstat, s);
             L += launch_join(a, false, c->dstat, s);
         }
@@ -444,17 +444,19 @@ int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
     mark(c, 4);
     if (dbg && dbg->sub_cnt && pl.n > 0)
         CK(cudaMemcpyAsync(dbg->sub_cnt, pl.cnt, pl.n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
-    L += launch_offsets(pl.cnt, pl.n, pl.off,
-                        mode == Mode::Match && phase == Phase::All ? cap : ~0ull,
-                        &c->dstat->K, pl.off_status, c->dstat, s);
+    const uint64_t off_cap = mode == Mode::Match && phase == Phase::All ? cap : ~0ull;
+    if (fused_counts)
+        L += launch_rank_offsets(rec, pl.n, pl.cnt, pl.off, off_cap, &c->dstat->K, pl.off_status,
+                                 c->dstat, s);
+    else
+        L += launch_offsets(pl.cnt, pl.n, pl.off, off_cap, &c->dstat->K, pl.off_status, c->dstat, s);
     if (batch) L += launch_inst_offsets(ba, pl.off, pl.inst_off, s);
   }
   if (do_suffix) {
     mark(c, 5);
     if (pl.window) {
-        L += launch_window_sizes(a, c->dstat, s);
-        L += launch_offsets(pl.lw_size, pl.num_win, pl.lw_off, ~0ull, pl.lw_total,
-                            pl.win_status, c->dstat, s);
+        L += launch_window_offsets(pl.windows, pl.num_win, pl.lcap, pl.lw_off, pl.lw_total,
+                                   pl.win_status, c->dstat, s);
         L += launch_tile_active(a, c->dstat, s);
     }
     mark(c, 6);

@@ -148,7 +148,7 @@ extern "C" int ddm_count_noalloc(const ddm_regions* r, void* cuda_stream, uint64
         launch_radix_sort<uint32_t>(L.keys0, L.vals0, L.keys1, L.vals1, E, 4, L.sort, true, L.st, s);
         launch_sweep_scan(L.vals0, E, n, m, L.rec, L.scan_status, L.st, s);
         if (r->d == 1) {
-            launch_rank_count(L.rec, n, m, L.cnt, nullptr, L.st, s);
+            launch_rank_offsets(L.rec, n, L.cnt, L.off, ~0ull, &L.st->K, L.off_status, L.st, s);
         } else {
             EmitArgs a{};
             a.d = r->d; a.n = n; a.m = m;
@@ -160,8 +160,8 @@ extern "C" int ddm_count_noalloc(const ddm_regions* r, void* cuda_stream, uint64
             a.cnt = L.cnt; a.cnt_a = L.cnt_a; a.subK = L.subK; a.updK = L.updK;
             launch_permute_keys(a, L.st, s);
             launch_filter_count(a, L.st, s);
+            launch_offsets(L.cnt, n, L.off, ~0ull, &L.st->K, L.off_status, L.st, s);
         }
-        launch_offsets(L.cnt, n, L.off, ~0ull, &L.st->K, L.off_status, L.st, s);
     }
     if (cudaGetLastError() != cudaSuccess) return DDM_ERR_CUDA;
     DevStatus h{};

@@ -45,8 +45,8 @@ struct EmitArgs {
     const uint4* windows;           // (cSlo, cUlo, cUhi, p) at p = w << win_shift, numWin + 1
     int win_shift;
     uint32_t num_win;
-    uint32_t* lw_size;              // capped list sizes (0 when a list overflows)
-    unsigned long long* lw_off;     // list offsets (exclusive scan of lw_size), numWin + 1
+    unsigned long long* lw_off;     // list offsets (exclusive scan of the capped list sizes,
+                                    // 0 for a list over lcap), numWin + 1
     uint32_t* lw_fill;              // per-window fill cursor (zeroed)
     uint4* lw;                      // list storage {id, pos(U.hi), rank, 0}, lw_cap entries
     uint32_t lcap;                  // longest boundary list a window may use
@@ -60,7 +60,6 @@ struct EmitArgs {
 int launch_join(const EmitArgs& a, bool write, DevStatus* st, cudaStream_t s);
 
 // Window path for d = 1.
-int launch_window_sizes(const EmitArgs& a, DevStatus* st, cudaStream_t s);
 int launch_tile_active(const EmitArgs& a, DevStatus* st, cudaStream_t s);
 int launch_emit_window(const EmitArgs& a, DevStatus* st, cudaStream_t s);
 

@@ -206,8 +206,39 @@ int launch_rank_count(const Records& rec, int64_t n, int64_t m, uint32_t* cnt,
 // when a thread walks its own run of OFF_ITEMS consecutive elements.
 __device__ __forceinline__ int pad32(int i) { return i + (i >> 5); }
 
+// Where the scanned values come from (so that the producing step needs no
+// kernel of its own).
+struct OffsetSource {
+    int kind;                 // 0: cnt[i]
+                              // 1: rank-arithmetic count B_i - C_i = hi[i].y - lo[i].z
+                              //    of a4, also stored to cnt_out[i]
+                              // 2: boundary-list size of window i,
+                              //    s = windows[i].y - windows[i].z, or 0 when s > lcap
+    const uint32_t* cnt;
+    const uint4* lo;
+    const uint4* hi;
+    uint32_t* cnt_out;
+    const uint4* windows;
+    uint32_t lcap;
+};
+
+__device__ __forceinline__ uint32_t offset_value(const OffsetSource& src, uint64_t i, bool& bad) {
+    if (src.kind == 1) {
+        const uint32_t b = src.hi[i].y, c = src.lo[i].z;
+        bad |= b < c;
+        src.cnt_out[i] = b - c;
+        return b - c;
+    }
+    if (src.kind == 2) {
+        const uint4 t = src.windows[i];
+        const uint32_t sz = t.y - t.z;
+        return sz <= src.lcap ? sz : 0u;
+    }
+    return src.cnt[i];
+}
+
 __global__ void __launch_bounds__(OFF_BLOCK)
-k_offsets(const uint32_t* __restrict__ cnt, uint32_t n, unsigned long long* __restrict__ off,
+k_offsets(OffsetSource src, uint32_t n, unsigned long long* __restrict__ off,
           unsigned long long cap, unsigned long long* total_out,
           unsigned long long* __restrict__ status, uint32_t* __restrict__ tile_counter,
           DevStatus* st) {
@@ -223,10 +254,14 @@ k_offsets(const uint32_t* __restrict__ cnt, uint32_t n, unsigned long long* __re
     const uint32_t tile = tile_id_s;
     const uint64_t tbase = (uint64_t)tile * OFF_TILE;
     // Coalesced load (striped), then each thread takes OFF_ITEMS consecutive values.
+    {
+        bool bad = false;
 #pragma unroll
-    for (int k = 0; k < OFF_ITEMS; ++k) {
-        const int i = k * OFF_BLOCK + tid;
-        s_in[pad32(i)] = tbase + i < n ? cnt[tbase + i] : 0u;
+        for (int k = 0; k < OFF_ITEMS; ++k) {
+            const int i = k * OFF_BLOCK + tid;
+            s_in[pad32(i)] = tbase + i < n ? offset_value(src, tbase + i, bad) : 0u;
+        }
+        if (bad) raise_error(st, DDM_ERR_INTERNAL, 4);
     }
     __syncthreads();
     uint32_t c[OFF_ITEMS];
@@ -288,8 +323,42 @@ int launch_offsets(const uint32_t* cnt, int64_t n, unsigned long long* off, uint
     if (n == 0) return 0;
     const uint64_t tiles = ceil_div((uint64_t)n, OFF_TILE);
     uint32_t* counter = reinterpret_cast<uint32_t*>(status + tiles);
-    launch_k(k_offsets, (unsigned)tiles, OFF_BLOCK, 0, s, cnt, (uint32_t)n, off, cap, total, status,
-                                                    counter, st);
+    OffsetSource src{};
+    src.kind = 0;
+    src.cnt = cnt;
+    launch_k(k_offsets, (unsigned)tiles, OFF_BLOCK, 0, s, src, (uint32_t)n, off, cap, total, status,
+             counter, st);
+    return 1;
+}
+
+int launch_rank_offsets(const Records& rec, int64_t n, uint32_t* cnt, unsigned long long* off,
+                        uint64_t cap, unsigned long long* total, unsigned long long* status,
+                        DevStatus* st, cudaStream_t s) {
+    if (n == 0) return 0;
+    const uint64_t tiles = ceil_div((uint64_t)n, OFF_TILE);
+    uint32_t* counter = reinterpret_cast<uint32_t*>(status + tiles);
+    OffsetSource src{};
+    src.kind = 1;
+    src.lo = rec.s_lo;
+    src.hi = rec.s_hi;
+    src.cnt_out = cnt;
+    launch_k(k_offsets, (unsigned)tiles, OFF_BLOCK, 0, s, src, (uint32_t)n, off, cap, total, status,
+             counter, st);
+    return 1;
+}
+
+int launch_window_offsets(const uint4* windows, uint32_t num_win, uint32_t lcap,
+                          unsigned long long* off, unsigned long long* total,
+                          unsigned long long* status, DevStatus* st, cudaStream_t s) {
+    if (num_win == 0) return 0;
+    const uint64_t tiles = ceil_div((uint64_t)num_win, OFF_TILE);
+    uint32_t* counter = reinterpret_cast<uint32_t*>(status + tiles);
+    OffsetSource src{};
+    src.kind = 2;
+    src.windows = windows;
+    src.lcap = lcap;
+    launch_k(k_offsets, (unsigned)tiles, OFF_BLOCK, 0, s, src, num_win, off, ~0ull, total, status,
+             counter, st);
     return 1;
 }
 

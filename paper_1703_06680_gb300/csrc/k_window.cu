@@ -33,16 +33,6 @@ constexpr int MAX_WIN_SHIFT = 9;      // windows of at most 512 positions
 constexpr int NBUCKET = 256;          // buckets of the per-window id sort
 constexpr int WITEMS = WCAP / WIN_BLOCK;
 
-__global__ void k_window_sizes(EmitArgs a) {
-    pdl_begin();
-    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < a.num_win;
-         w += gridDim.x * blockDim.x) {
-        const uint4 t = a.windows[w];
-        const uint32_t s = t.y - t.z;  // updates with pos(lo) < wT <= pos(hi)
-        a.lw_size[w] = s <= a.lcap ? s : 0u;
-    }
-}
-
 __device__ __forceinline__ bool list_fits(const EmitArgs& a, uint32_t w, uint32_t s) {
     return s <= a.lcap && a.lw_off[w] + s <= a.lw_cap;
 }
@@ -276,13 +266,6 @@ __global__ void __launch_bounds__(WIN_BLOCK) k_emit_window(EmitArgs a, DevStatus
 static unsigned grid_for(uint64_t items, unsigned per_block, unsigned cap) {
     uint64_t g = ceil_div(items, per_block);
     return (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
-}
-
-int launch_window_sizes(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
-    (void)st;
-    if (a.num_win == 0) return 0;
-    launch_k(k_window_sizes, grid_for(a.num_win, 256, 152 * 8), 256, 0, s, a);
-    return 1;
 }
 
 int launch_tile_active(const EmitArgs& a, DevStatus* st, cudaStream_t s) {

@@ -56,4 +56,16 @@ int launch_offsets(const uint32_t* cnt, int64_t n, unsigned long long* off, uint
                    unsigned long long* total, unsigned long long* status, DevStatus* st,
                    cudaStream_t s);
 
+// a4 + a5 in one kernel: cnt[i] = B_i - C_i of the subscriptions' records and
+// off[] / *total as launch_offsets gives for those counts.  Same status words.
+int launch_rank_offsets(const Records& rec, int64_t n, uint32_t* cnt, unsigned long long* off,
+                        uint64_t cap, unsigned long long* total, unsigned long long* status,
+                        DevStatus* st, cudaStream_t s);
+
+// Offsets of the boundary lists: value of window w = windows[w].y - windows[w].z
+// (updates active at the window boundary), or 0 when that exceeds lcap.
+int launch_window_offsets(const uint4* windows, uint32_t num_win, uint32_t lcap,
+                          unsigned long long* off, unsigned long long* total,
+                          unsigned long long* status, DevStatus* st, cudaStream_t s);
+
 }  // namespace ddm
