@@ -146,8 +146,8 @@ int ddm_count_noalloc(const ddm_regions *regions, void *cuda_stream, uint64_t *K
  *                         sorted-stream positions: 6 .. 9 (default 8).
  * Returns DDM_ERR_INVALID for an unknown parameter or a value out of range.
  *   DDM_PARAM_ND_PATH     strategy for d > 1: 0 = automatic (default: the tiled
- *                         join for d >= 3, range expansion for d = 2, as
- *                         measured on GB300), 1 = tiled join, 2 = range
+ *                         join with dimension-1 pruning, measured faster on
+ *                         GB300 for d = 2 and 3), 1 = tiled join, 2 = range
  *                         expansion.  Results are identical; only speed differs.
  *   DDM_PARAM_PDL         1 (default) = launch the kernels of a call with
  *                         programmatic dependent launch, so that each grid is

@@ -78,6 +78,11 @@ __device__ __forceinline__ uint32_t float_key(float x) {
     return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
+// Inverse of float_key (-0 comes back as +0).
+__device__ __forceinline__ float key_float(uint32_t k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
 __device__ __forceinline__ bool is_nan_bits(float x) {
     return (__float_as_uint(x) & 0x7fffffffu) > 0x7f800000u;
 }

@@ -220,7 +220,7 @@ struct Plan {
         cursor_b = cv.take<uint32_t>(mode == Mode::Match ? n : 0);
         big_count = cv.take<uint32_t>(2);
         window = mode == Mode::Match && d == 1;
-        join = d > 1 && mode != Mode::Debug && (nd_path == 1 || (nd_path == 0 && d >= 3));
+        join = d > 1 && mode != Mode::Debug && nd_path != 2;
         const bool lists = window || join;
         win_shift = join ? 11 : win_shift_;
         lcap = join ? 0xffffffffu : 1024u;
