@@ -30,6 +30,8 @@
 // scan, pass 2 (write) appends the survivors to the subscription's segment.
 // Segments are then sorted by update id (k_emit.cu).  Windows whose boundary
 // list does not fit flag their subscriptions for the range path.
+#include <atomic>
+
 #include "emit.cuh"
 
 namespace ddm {
@@ -39,6 +41,7 @@ constexpr int JOIN_WARPS = JOIN_BLOCK / 32;
 constexpr uint32_t JOIN_CHUNK = 512;
 constexpr int JOIN_SHIFT = 11;  // windows of 2048 stream positions
 constexpr uint32_t JOIN_MAXSUB = 1u << JOIN_SHIFT;
+constexpr uint32_t JOIN_LONG_RANGE = 16;  // candidate ranges walked by the whole warp
 
 // Dynamic shared memory of one join block for d dimensions.
 __host__ __device__ inline size_t join_smem_bytes(int d) {
@@ -50,28 +53,28 @@ __host__ __device__ inline size_t join_smem_bytes(int d) {
            + 64;
 }
 
-// Range [b0, b1) of the sorted chunk keys sk[0..JOIN_CHUNK) with lo <= key <= hi,
-// found by one warp: a coarse ballot over the last key of each 16-entry
-// segment (coarse[g] = sk[16 g + 15]) for both bounds at once, then a fine
-// ballot inside the two segments (lanes 0-15 for the lower bound, 16-31 for
-// the upper).
-__device__ __forceinline__ void chunk_range(const uint32_t* sk, const uint32_t* coarse, uint32_t lo,
-                                            uint32_t hi, int lane, uint32_t& b0, uint32_t& b1) {
-    static_assert(JOIN_CHUNK == 32 * 16, "two-level search assumes 32 segments of 16");
-    const uint32_t kc = coarse[lane];
-    const uint32_t g0 = __popc(__ballot_sync(0xffffffffu, kc < lo));   // segments all < lo
-    const uint32_t g1 = __popc(__ballot_sync(0xffffffffu, kc <= hi));  // segments all <= hi
-    const int l = lane & 15;
-    const uint32_t g = lane < 16 ? g0 : g1;
-    const uint32_t kf = g < 32 ? sk[g * 16 + l] : 0xffffffffu;
-    const unsigned f0 = __ballot_sync(0xffffffffu, lane < 16 && g0 < 32 && kf < lo);
-    const unsigned f1 = __ballot_sync(0xffffffffu, lane >= 16 && g1 < 32 && kf <= hi);
-    b0 = g0 < 32 ? g0 * 16 + __popc(f0) : JOIN_CHUNK;
-    b1 = g1 < 32 ? g1 * 16 + __popc(f1) : JOIN_CHUNK;
+// Number of sorted chunk keys sk[0..JOIN_CHUNK) below v / at most v (branch-free
+// binary search, one thread).
+__device__ __forceinline__ uint32_t chunk_count_below(const uint32_t* sk, uint32_t v) {
+    uint32_t pos = 0;
+#pragma unroll
+    for (uint32_t step = JOIN_CHUNK / 2; step > 0; step >>= 1)
+        pos += sk[pos + step - 1] < v ? step : 0u;
+    return pos + (sk[pos] < v ? 1u : 0u);  // pos <= JOIN_CHUNK - 1 here
+}
+__device__ __forceinline__ uint32_t chunk_count_at_most(const uint32_t* sk, uint32_t v) {
+    uint32_t pos = 0;
+#pragma unroll
+    for (uint32_t step = JOIN_CHUNK / 2; step > 0; step >>= 1)
+        pos += sk[pos + step - 1] <= v ? step : 0u;
+    return pos + (sk[pos] <= v ? 1u : 0u);
 }
 
-template <bool WRITE>
+// DD > 0: compiled for DD = d - 1 extra dimensions; DD = 0: any d (arrays of
+// DDM_MAX_DIMS - 1, runtime bound).
+template <bool WRITE, int DD>
 __global__ void __launch_bounds__(JOIN_BLOCK) k_join(EmitArgs a, DevStatus* st) {
+    constexpr int NK = DD > 0 ? DD : DDM_MAX_DIMS - 1;
     pdl_begin();
     extern __shared__ __align__(16) unsigned char jsm[];
     unsigned long long* s_off = reinterpret_cast<unsigned long long*>(jsm);
@@ -86,16 +89,14 @@ __global__ void __launch_bounds__(JOIN_BLOCK) k_join(EmitArgs a, DevStatus* st) 
     uint2* c_key = reinterpret_cast<uint2*>(c_id + JOIN_CHUNK);  // [(d-1)][JOIN_CHUNK]
     __shared__ unsigned long long c_srt[JOIN_CHUNK];  // (dim-1 lo key << 32) | chunk index
     __shared__ uint32_t c_sk[JOIN_CHUNK];             // sorted dim-1 lo keys
-    __shared__ uint32_t c_coarse[32];                 // c_sk[16 g + 15]
     __shared__ uint32_t s_wmax[JOIN_WARPS];
     __shared__ uint32_t s_pmax, s_first;
 
     if (read_error(st)) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const unsigned lt = (1u << lane) - 1u;
     const uint32_t w = blockIdx.x;
     const int S = a.win_shift;
-    const int dd = a.d - 1;
+    const int dd = DD > 0 ? DD : a.d - 1;
     const uint4 t0 = a.windows[w], t1 = a.windows[w + 1];
     const uint32_t r0 = t0.x, ns = t1.x - t0.x;
     if (ns == 0) return;
@@ -190,17 +191,16 @@ __global__ void __launch_bounds__(JOIN_BLOCK) k_join(EmitArgs a, DevStatus* st) 
             const uint32_t id = c_id[x];
             uint2 kq[DDM_MAX_DIMS - 1];
 #pragma unroll
-            for (int q = 0; q < DDM_MAX_DIMS - 1; ++q)
+            for (int q = 0; q < NK; ++q)
                 if (q < dd) kq[q] = c_key[q * JOIN_CHUNK + x];
             __syncthreads();
             c_pos[tid] = p;
             c_id[tid] = id;
 #pragma unroll
-            for (int q = 0; q < DDM_MAX_DIMS - 1; ++q)
+            for (int q = 0; q < NK; ++q)
                 if (q < dd) c_key[q * JOIN_CHUNK + tid] = kq[q];
             const uint32_t key = (uint32_t)(e >> 32);
             c_sk[tid] = key;
-            if ((tid & 15) == 15) c_coarse[tid >> 4] = key;
         }
         __syncthreads();
         uint32_t maxbits = 0;
@@ -208,55 +208,117 @@ __global__ void __launch_bounds__(JOIN_BLOCK) k_join(EmitArgs a, DevStatus* st) 
         for (int q = 0; q < JOIN_WARPS; ++q) maxbits = max(maxbits, s_wmax[q]);
         const float maxlen = __uint_as_float(maxbits);
         const uint32_t first = s_first;
-        for (uint32_t k = warp; k < ns; k += JOIN_WARPS) {
-            const uint32_t pl = s_lo[k], ph = s_hi[k];
-            if (c0 >= lw_n && first >= ph) continue;  // every later candidate starts after S ends
-            uint2 own[DDM_MAX_DIMS - 1];
+        // One lane per subscription: two binary searches give its candidate
+        // range; a short range is walked by the lane alone, a long one by the
+        // whole warp (32 candidates per step, writes compacted by ballot).
+        const uint32_t ns_pad = (ns + 31) & ~31u;
+        for (uint32_t k = (uint32_t)tid; k < ns_pad; k += JOIN_BLOCK) {  // uniform per warp
+            bool act = k < ns;
+            uint32_t pl = 0, ph = 0;
+            if (act) {
+                pl = s_lo[k];
+                ph = s_hi[k];
+                act = !(c0 >= lw_n && first >= ph);  // every later candidate starts after S ends
+            }
+            uint2 own[NK];
+            uint32_t b0 = 0, b1 = 0, cur = 0;
+            if (act) {
 #pragma unroll
-            for (int q = 0; q < DDM_MAX_DIMS - 1; ++q)
-                if (q < dd) own[q] = s_key[q * JOIN_MAXSUB + k];
-            // candidates whose dimension-1 lower bound lies in [own.lo - maxlen, own.hi]
-            const float bound = __fsub_rd(key_float(own[0].x), maxlen);
-            const uint32_t lo_b = bound == bound ? float_key(bound) : 0u;  // NaN: inf - inf
-            uint32_t b0, b1;
-            chunk_range(c_sk, c_coarse, lo_b, own[0].y, lane, b0, b1);
-            if (b0 >= b1) continue;
-            const uint32_t i = s_id[k];
-            uint32_t cur = s_cnt[k];
-            int2* seg = nullptr;
-            uint32_t c = 0;
-            int32_t i_out = (int32_t)i;
+                for (int q = 0; q < NK; ++q)
+                    if (q < dd) own[q] = s_key[q * JOIN_MAXSUB + k];
+                // candidates whose dimension-1 lower bound lies in [own.lo - maxlen, own.hi]
+                const float bound = __fsub_rd(key_float(own[0].x), maxlen);
+                const uint32_t lo_b = bound == bound ? float_key(bound) : 0u;  // NaN: inf - inf
+                b0 = chunk_count_below(c_sk, lo_b);
+                b1 = chunk_count_at_most(c_sk, own[0].y);
+                cur = s_cnt[k];
+            } else {
+#pragma unroll
+                for (int q = 0; q < NK; ++q) own[q] = make_uint2(0u, 0u);
+            }
+            unsigned long long obase = 0;  // write pass: segment start
+            uint32_t c = 0;                // write pass: expected count
+            int32_t i_out = 0;
             uint32_t j_base = 0;
-            if (WRITE) {
-                seg = reinterpret_cast<int2*>(a.pairs) + s_off[k];
+            if (WRITE && act && b0 < b1) {
+                const uint32_t i = s_id[k];
+                obase = s_off[k];
                 c = s_exp[k];
+                i_out = (int32_t)i;
                 if (a.inst_sub_base) {
                     const int b = inst_of(a.inst_sub_base, a.num_inst, i);
                     i_out -= (int32_t)a.inst_sub_base[b];
                     j_base = (uint32_t)a.inst_upd_base[b];
                 }
             }
-            for (uint32_t base = b0; base < b1; base += 32) {
-                const uint32_t kk = base + lane;
-                const bool inr = kk < b1;
-                const uint32_t x = inr ? kk : 0u;
-                const uint2 p = c_pos[x];
-                bool pass = inr & (p.x < ph) & (p.y > pl);
+            const bool longr = b1 - b0 >= JOIN_LONG_RANGE;
+            if (b0 < b1 && !longr) {
+                int2* seg = reinterpret_cast<int2*>(a.pairs) + obase;
+                for (uint32_t x = b0; x < b1; ++x) {
+                    const uint2 p = c_pos[x];
+                    bool pass = (p.x < ph) & (p.y > pl);
 #pragma unroll
-                for (int q = 0; q < DDM_MAX_DIMS - 1; ++q) {
-                    if (q < dd) {
-                        const uint2 u = c_key[q * JOIN_CHUNK + x];
-                        pass &= (own[q].x <= u.y) & (u.x <= own[q].y);
+                    for (int q = 0; q < NK; ++q) {
+                        if (q < dd) {
+                            const uint2 u = c_key[q * JOIN_CHUNK + x];
+                            pass &= (own[q].x <= u.y) & (u.x <= own[q].y);
+                        }
+                    }
+                    if (pass) {
+                        if (WRITE && cur < c) seg[cur] = make_int2(i_out, (int32_t)(c_id[x] - j_base));
+                        ++cur;
                     }
                 }
-                const unsigned bal = __ballot_sync(0xffffffffu, pass);
-                if (WRITE) {
-                    const uint32_t r = cur + __popc(bal & lt);
-                    if (pass && r < c) seg[r] = make_int2(i_out, (int32_t)(c_id[x] - j_base));
-                }
-                cur += __popc(bal);
             }
-            if (lane == 0) s_cnt[k] = cur;
+            unsigned todo = __ballot_sync(0xffffffffu, longr);
+            while (todo) {
+                const int src = __ffs(todo) - 1;
+                todo &= todo - 1;
+                const uint32_t spl = __shfl_sync(0xffffffffu, pl, src);
+                const uint32_t sph = __shfl_sync(0xffffffffu, ph, src);
+                const uint32_t sb0 = __shfl_sync(0xffffffffu, b0, src);
+                const uint32_t sb1 = __shfl_sync(0xffffffffu, b1, src);
+                uint32_t scur = __shfl_sync(0xffffffffu, cur, src);
+                uint2 sown[NK];
+#pragma unroll
+                for (int q = 0; q < NK; ++q) {
+                    if (q < dd) {
+                        sown[q].x = __shfl_sync(0xffffffffu, own[q].x, src);
+                        sown[q].y = __shfl_sync(0xffffffffu, own[q].y, src);
+                    }
+                }
+                int2* sseg = nullptr;
+                uint32_t sc = 0, sj = 0;
+                int32_t si = 0;
+                if (WRITE) {
+                    sseg = reinterpret_cast<int2*>(a.pairs) + __shfl_sync(0xffffffffu, obase, src);
+                    sc = __shfl_sync(0xffffffffu, c, src);
+                    si = __shfl_sync(0xffffffffu, i_out, src);
+                    sj = __shfl_sync(0xffffffffu, j_base, src);
+                }
+                for (uint32_t base = sb0; base < sb1; base += 32) {
+                    const uint32_t x = base + lane;
+                    const bool inr = x < sb1;
+                    const uint32_t xx = inr ? x : sb0;
+                    const uint2 p = c_pos[xx];
+                    bool pass = inr & (p.x < sph) & (p.y > spl);
+#pragma unroll
+                    for (int q = 0; q < NK; ++q) {
+                        if (q < dd) {
+                            const uint2 u = c_key[q * JOIN_CHUNK + xx];
+                            pass &= (sown[q].x <= u.y) & (u.x <= sown[q].y);
+                        }
+                    }
+                    const unsigned bal = __ballot_sync(0xffffffffu, pass);
+                    if (WRITE) {
+                        const uint32_t r = scur + __popc(bal & ((1u << lane) - 1u));
+                        if (pass && r < sc) sseg[r] = make_int2(si, (int32_t)(c_id[xx] - sj));
+                    }
+                    scur += __popc(bal);
+                }
+                if (lane == src) cur = scur;
+            }
+            if (act) s_cnt[k] = cur;
         }
         __syncthreads();
     }
@@ -267,24 +329,36 @@ __global__ void __launch_bounds__(JOIN_BLOCK) k_join(EmitArgs a, DevStatus* st) 
     }
 }
 
+// One instantiation: sets its dynamic shared-memory limit once per device.
+template <bool WRITE, int DD>
+static void launch_join_t(const EmitArgs& a, size_t smem, DevStatus* st, cudaStream_t s) {
+    static std::atomic<unsigned long long> attr_set{0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !(attr_set.load() & (1ull << dev))) {
+        cudaFuncSetAttribute(k_join<WRITE, DD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)join_smem_bytes(DDM_MAX_DIMS));
+        if (dev >= 0 && dev < 64) attr_set.fetch_or(1ull << dev);
+    }
+    launch_k(k_join<WRITE, DD>, a.num_win, JOIN_BLOCK, smem, s, a, st);
+}
+
+template <bool WRITE>
+static void launch_join_w(const EmitArgs& a, size_t smem, DevStatus* st, cudaStream_t s) {
+    switch (a.d - 1) {
+        case 1: launch_join_t<WRITE, 1>(a, smem, st, s); break;
+        case 2: launch_join_t<WRITE, 2>(a, smem, st, s); break;
+        case 3: launch_join_t<WRITE, 3>(a, smem, st, s); break;
+        default: launch_join_t<WRITE, 0>(a, smem, st, s); break;
+    }
+}
+
 int launch_join(const EmitArgs& a, bool write, DevStatus* st, cudaStream_t s) {
     if (a.num_win == 0 || a.n == 0) return 0;
     if (a.win_shift != JOIN_SHIFT) return -1;
     const size_t smem = join_smem_bytes(a.d);
-    static unsigned long long attr_set[2] = {0, 0};  // per device, per pass
-    int dev = 0;
-    cudaGetDevice(&dev);
-    const int w = write ? 1 : 0;
-    if (dev < 0 || dev >= 64 || !(attr_set[w] & (1ull << dev))) {
-        const size_t max_smem = join_smem_bytes(DDM_MAX_DIMS);
-        if (write)
-            cudaFuncSetAttribute(k_join<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
-        else
-            cudaFuncSetAttribute(k_join<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
-        if (dev >= 0 && dev < 64) attr_set[w] |= 1ull << dev;
-    }
-    if (write) launch_k(k_join<true>, a.num_win, JOIN_BLOCK, smem, s, a, st);
-    else launch_k(k_join<false>, a.num_win, JOIN_BLOCK, smem, s, a, st);
+    if (write) launch_join_w<true>(a, smem, st, s);
+    else launch_join_w<false>(a, smem, st, s);
     return 1;
 }
 
