@@ -288,6 +288,26 @@ def bench_served(dev, requests: int = 96, slots: int = 4, load: float = 0.8):
             if plain["pairs_per_s"] else None}
 
 
+def job_totals(t_ms: float, K: int, steps: int, e2e_s: float, e2e_steps: int, world: int, dev):
+    """Whole-job figures over all ranks (weak scaling: every rank its own
+    problem): the slowest rank's device time and end-to-end time, and the
+    pairs of all ranks.  With world > 1 this reduces over the default process
+    group (NCCL on the GPU machine; gloo with dev = cpu in the multi-rank tests)."""
+    import torch
+    import torch.distributed as dist
+    times = torch.tensor([t_ms, e2e_s], dtype=torch.float64, device=dev)
+    k_all = torch.tensor([float(K)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(times, op=dist.ReduceOp.MAX)
+        dist.all_reduce(k_all, op=dist.ReduceOp.SUM)
+    t_max_s = float(times[0].item()) / 1e3
+    e2e_max_s = float(times[1].item())
+    pairs = float(k_all.item())
+    return {"t_max_s": t_max_s, "pairs_all_ranks": pairs,
+            "value": pairs * steps / t_max_s, "ms_per_step": 1e3 * t_max_s / steps,
+            "e2e_value": pairs * e2e_steps / e2e_max_s}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -362,14 +382,6 @@ def run_ours(args):
             stage_sum[k] = stage_sum.get(k, 0.0) + v
     ctx.set_profiling(False)
     t_ms = sum(a.elapsed_time(b) for a, b in ev)
-    t_max = torch.tensor([t_ms], dtype=torch.float64, device=dev)
-    k_all = torch.tensor([float(K)], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-        dist.all_reduce(k_all, op=dist.ReduceOp.SUM)
-    t_max_s = float(t_max.item()) / 1e3
-    value = float(k_all.item()) * args.steps / t_max_s
-    ms_step = 1e3 * t_max_s / args.steps
 
     # End to end through the public API with HOST buffers (pinned), copies inside.
     host_in = [torch.from_numpy(a).pin_memory().numpy() for a in
@@ -387,10 +399,9 @@ def run_ours(args):
         got = ctx.match_host(*host_in, out=host_out[:K])
         e2e_t += time.perf_counter() - t0
     assert len(got) == K
-    e2e_t_all = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(e2e_t_all, op=dist.ReduceOp.MAX)
-    e2e_value = float(k_all.item()) * e2e_steps / float(e2e_t_all.item())
+    tot = job_totals(t_ms, K, args.steps, e2e_t, e2e_steps, world, dev)
+    value, ms_step, e2e_value = tot["value"], tot["ms_per_step"], tot["e2e_value"]
+    t_max_s = tot["t_max_s"]
 
     # Roofline of the dominant stage (per-stage CUDA events on the launching stream).
     stage_avg = {k: v / args.steps for k, v in stage_sum.items()}

@@ -43,17 +43,37 @@ def _save(path: str, cache: dict):
     os.replace(tmp, path)
 
 
-def tune(ctx, tensors, reps: int = 5, cache_path: str = DEFAULT_CACHE) -> dict:
-    """Times every candidate for the workload `tensors` (d, n, m CUDA tensors), applies
-    the best values to `ctx`, caches them and returns {name: value, ..., "key": key}."""
+def cuda_timer(ctx, tensors, K: int, reps: int) -> float:
+    """Median device time (ms) of `reps` ddm_match calls, CUDA events on the
+    context's stream, after one warm-up call."""
     import torch
+    out = torch.empty((max(K, 1), 2), dtype=torch.int32, device=tensors[0].device)
+    ctx.match_into(out[:K], *tensors)
+    ms = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        ctx.match_into(out[:K], *tensors)
+        e1.record(ctx.stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return statistics.median(ms)
+
+
+def _gpu_name(ctx) -> str:
+    import torch
+    return torch.cuda.get_device_name(ctx.device)
+
+
+def tune(ctx, tensors, reps: int = 5, cache_path: str = DEFAULT_CACHE, gpu: str | None = None,
+         timer=cuda_timer) -> dict:
+    """Times every candidate for the workload `tensors` (d, n, m CUDA tensors), applies
+    the best values to `ctx`, caches them and returns {name: value, ..., "key": key}.
+    `timer(ctx, tensors, K, reps)` returns the time of one candidate in ms."""
     K = ctx.count(*tensors)
     d, n = tensors[0].shape
     N = n + tensors[2].shape[1]
-    gpu = torch.cuda.get_device_name(ctx.device)
-    key = workload_key(gpu, d, N, K)
-    out = torch.empty((max(K, 1), 2), dtype=torch.int32, device=tensors[0].device)
-    stream = ctx.stream
+    key = workload_key(gpu if gpu is not None else _gpu_name(ctx), d, N, K)
     chosen = {"key": key}
     for param, values in CANDIDATES.items():
         if not APPLIES[param](d):
@@ -61,16 +81,7 @@ def tune(ctx, tensors, reps: int = 5, cache_path: str = DEFAULT_CACHE) -> dict:
         best, best_ms, times = None, float("inf"), {}
         for v in values:
             ctx.set_param(param, v)
-            ctx.match_into(out[:K], *tensors)
-            ms = []
-            for _ in range(reps):
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                ctx.match_into(out[:K], *tensors)
-                e1.record(stream)
-                e1.synchronize()
-                ms.append(e0.elapsed_time(e1))
-            times[str(v)] = statistics.median(ms)
+            times[str(v)] = timer(ctx, tensors, K, reps)
             if times[str(v)] < best_ms:
                 best, best_ms = v, times[str(v)]
         ctx.set_param(param, best)
@@ -82,13 +93,13 @@ def tune(ctx, tensors, reps: int = 5, cache_path: str = DEFAULT_CACHE) -> dict:
     return chosen
 
 
-def apply_cached(ctx, tensors, K: int | None = None, cache_path: str = DEFAULT_CACHE) -> bool:
+def apply_cached(ctx, tensors, K: int | None = None, cache_path: str = DEFAULT_CACHE,
+                 gpu: str | None = None) -> bool:
     """Applies cached tunables for this workload class, if any; returns whether it did."""
-    import torch
     if K is None:
         K = ctx.count(*tensors)
     d, n = tensors[0].shape
-    key = workload_key(torch.cuda.get_device_name(ctx.device), d, n + tensors[2].shape[1], K)
+    key = workload_key(gpu if gpu is not None else _gpu_name(ctx), d, n + tensors[2].shape[1], K)
     entry = _load(cache_path).get(key)
     if not entry:
         return False

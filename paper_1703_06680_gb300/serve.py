@@ -61,11 +61,35 @@ class Simulation:
         self.session.close()
 
 
-class Server:
-    def __init__(self, sims: list[Simulation], slots: int = 4, out_budget_bytes: int = 4 << 30,
-                 device: int = 0):
+class CudaBackend:
+    """Device side of a server slot: its stream and the output buffers."""
+
+    def __init__(self, device: int = 0):
         import torch
         self.torch = torch
+        self.device = device
+
+    def stream(self):
+        return self.torch.cuda.Stream(device=self.device)
+
+    def bind(self):
+        self.torch.cuda.set_device(self.device)
+
+    def alloc_pairs(self, K: int, stream):
+        with self.torch.cuda.stream(stream):
+            return self.torch.empty((max(K, 1), 2), dtype=self.torch.int32, device=self.device)
+
+    def to_host(self, pairs):
+        return pairs.cpu().numpy()
+
+    def synchronize(self, stream):
+        stream.synchronize()
+
+
+class Server:
+    def __init__(self, sims: list[Simulation], slots: int = 4, out_budget_bytes: int = 4 << 30,
+                 device: int = 0, backend=None):
+        self.backend = backend if backend is not None else CudaBackend(device)
         self.sims = sims
         self.device = device
         self.budget = out_budget_bytes
@@ -74,7 +98,7 @@ class Server:
         self.cv = threading.Condition()
         self.stop = False
         self.completed: list[Request] = []
-        self.streams = [torch.cuda.Stream(device=device) for _ in range(slots)]
+        self.streams = [self.backend.stream() for _ in range(slots)]
         self.workers = [threading.Thread(target=self._work, args=(k,), daemon=True)
                         for k in range(slots)]
         for w in self.workers:
@@ -126,9 +150,9 @@ class Server:
             self.cv.notify_all()
 
     def _work(self, slot: int):
-        torch = self.torch
+        be = self.backend
         stream = self.streams[slot]
-        torch.cuda.set_device(self.device)
+        be.bind()
         while True:
             req = self._take()
             if req is None:
@@ -140,14 +164,13 @@ class Server:
                 sess = sim.session
                 sess.drift(sim.seed, req.step, sim.sigma, stream=stream)
                 K = sess.count(stream=stream)
-                reserved = 8 * K
-                self._admit(reserved)
-                with torch.cuda.stream(stream):
-                    out = torch.empty((max(K, 1), 2), dtype=torch.int32, device=self.device)
+                self._admit(8 * K)
+                reserved = 8 * K  # only what was admitted is released
+                out = be.alloc_pairs(K, stream)
                 req.K = sess.emit(out[:K], stream=stream)
                 if req.keep_pairs:
-                    req.pairs = out[:K].cpu().numpy()
-                stream.synchronize()
+                    req.pairs = be.to_host(out[:K])
+                be.synchronize(stream)
                 del out
             except Exception as exc:  # reported through the request
                 req.error = exc

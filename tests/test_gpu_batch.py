@@ -79,3 +79,25 @@ def test_batch_full_size_sampled(ctx):
     rng = np.random.default_rng(4096)
     sample = sorted(rng.choice(4096, size=24, replace=False).tolist())
     check_batch(ctx, regs, sample=sample)
+
+
+@pytest.mark.parametrize("d", [1, 2])
+def test_autotune_on_gpu_keeps_results(tmp_path, d):
+    # The tuner times every candidate through the library; whatever it picks,
+    # results stay identical to the oracle's, and the cache re-applies it.
+    import paper_1703_06680_gb300 as ddm
+    from paper_1703_06680_gb300 import autotune
+    ddm.build_library()
+    reg = synth.large_1d(1.0, N=100_000) if d == 1 else synth.large_nd(2, 1.0, N=60_000)
+    want = oracle.sbm(reg)
+    t = to_dev(reg)
+    cache = str(tmp_path / "tune.json")
+    with ddm.Context(0) as ctx:
+        chosen = autotune.tune(ctx, t, reps=2, cache_path=cache)
+        name = "win_shift" if d == 1 else "nd_path"
+        assert chosen[name] in autotune.CANDIDATES[
+            autotune.PARAM_WIN_SHIFT if d == 1 else autotune.PARAM_ND_PATH]
+        assert np.array_equal(ctx.match(*t).cpu().numpy(), want)
+    with ddm.Context(0) as ctx2:
+        assert autotune.apply_cached(ctx2, t, cache_path=cache)
+        assert np.array_equal(ctx2.match(*t).cpu().numpy(), want)
