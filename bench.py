@@ -35,7 +35,12 @@ import numpy as np  # noqa: E402
 import synth  # noqa: E402
 
 L2_FLUSH_BYTES = 256 << 20
-REF_SAMPLE_SUBS = 250_000   # oracle sample: first 250k subscriptions x all updates
+REF_SAMPLE_SUBS = 250_000   # oracle sample: first 250k subscriptions x all updates (d = 1)
+REF_SAMPLE_SUBS_ND = 20_000  # d > 1: the dimension-0 candidates per subscription are many more
+
+
+def ref_sample_subs(args) -> int:
+    return REF_SAMPLE_SUBS if args.d == 1 else REF_SAMPLE_SUBS_ND
 
 
 def parse_args():
@@ -46,6 +51,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--alpha", type=float, default=100.0)
     ap.add_argument("--N", type=int, default=1_000_000)
+    ap.add_argument("--d", type=int, default=1, help="dimensions (1 = the headline workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
@@ -63,12 +69,15 @@ def peaks():
 
 
 def workload(args, rank: int):
-    return synth.large_1d(args.alpha, replica=rank, N=args.N)
+    d = getattr(args, "d", 1)
+    if d == 1:
+        return synth.large_1d(args.alpha, replica=rank, N=args.N)
+    return synth.large_nd(d, args.alpha, replica=rank, N=args.N)
 
 
 def workload_name(args):
-    return (f"d=1, N={args.N:.0e} ({args.N // 2} subs + {args.N - args.N // 2} upds), "
-            f"alpha={args.alpha:g}, enumerate (sorted pair list)")
+    return (f"d={getattr(args, 'd', 1)}, N={args.N:.0e} ({args.N // 2} subs + "
+            f"{args.N - args.N // 2} upds), alpha={args.alpha:g}, enumerate (sorted pair list)")
 
 
 class ClockSampler:
@@ -113,10 +122,10 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def cpu_baseline(reg, seconds: float):
+def cpu_baseline(reg, seconds: float, nsub: int = REF_SAMPLE_SUBS):
     import oracle
-    sample = synth.Regions(reg.sub_lo[:, :REF_SAMPLE_SUBS].copy(),
-                           reg.sub_hi[:, :REF_SAMPLE_SUBS].copy(), reg.upd_lo, reg.upd_hi)
+    sample = synth.Regions(reg.sub_lo[:, :nsub].copy(),
+                           reg.sub_hi[:, :nsub].copy(), reg.upd_lo, reg.upd_hi)
     times, K = [], 0
     t_end = time.perf_counter() + seconds
     while time.perf_counter() < t_end or not times:
@@ -124,7 +133,7 @@ def cpu_baseline(reg, seconds: float):
         K = len(oracle.sbm(sample))
         times.append(time.perf_counter() - t0)
     return {"value": K / statistics.mean(times), "unit": "pairs/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {REF_SAMPLE_SUBS} subscriptions x all {reg.m} updates of the "
+            "sample": f"first {nsub} subscriptions x all {reg.m} updates of the "
                       f"same workload (K={K}), serial C Algorithm 4 + pair sort, "
                       f"{len(times)} runs, host cpu_count={os.cpu_count()}"}
 
@@ -135,8 +144,9 @@ def run_reference(args):
         return
     import oracle
     reg = workload(args, 0)
-    sample = synth.Regions(reg.sub_lo[:, :REF_SAMPLE_SUBS].copy(),
-                           reg.sub_hi[:, :REF_SAMPLE_SUBS].copy(), reg.upd_lo, reg.upd_hi)
+    nsub = ref_sample_subs(args)
+    sample = synth.Regions(reg.sub_lo[:, :nsub].copy(),
+                           reg.sub_hi[:, :nsub].copy(), reg.upd_lo, reg.upd_hi)
     for _ in range(args.warmup):
         oracle.sbm(sample)
     times, K = [], 0
@@ -151,10 +161,10 @@ def run_reference(args):
             "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_name(args) + f"; each step a bounded sample: first "
-                                                         f"{REF_SAMPLE_SUBS} subscriptions",
-                       "N": args.N, "d": 1, "alpha": args.alpha, "K_sample": K},
+                                                         f"{nsub} subscriptions",
+                       "N": args.N, "d": args.d, "alpha": args.alpha, "K_sample": K},
             "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": 1, "kind": "oracle",
-                             "sample": f"first {REF_SAMPLE_SUBS} subscriptions x all updates"},
+                             "sample": f"first {nsub} subscriptions x all updates"},
             "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -425,14 +435,14 @@ def run_ours(args):
     if os.path.exists(prof_txt):
         with open(prof_txt) as fh:
             traffic = json.load(fh).get(top)
-    path_bytes = 8 * N * 1 + 8 * K
+    path_bytes = 8 * N * args.d + 8 * K
     line = {
         "metric": "matched pairs/s", "value": value, "unit": "pairs/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic",
-        "config": {"workload": workload_name(args), "N": N, "d": 1, "alpha": args.alpha, "K": K,
-                   "seed": synth.seed_for(1, rank),
+        "config": {"workload": workload_name(args), "N": N, "d": args.d, "alpha": args.alpha, "K": K,
+                   "seed": synth.seed_for(1 if args.d == 1 else 2, rank),
                    "l2": f"{L2_FLUSH_BYTES >> 20} MiB buffer written between timed steps"},
         "regions_per_s": N * world * args.steps / t_max_s,
         "roofline": {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": hbm,
@@ -442,7 +452,7 @@ def run_ours(args):
                           "frac": path_bytes / (ms_step * 1e-3) / 1e9 / hbm},
         "stages_ms": stage_avg,
         "stages_note": "per-stage events on every boundary, in a second pass of the same steps",
-        "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": 4 * 2 * (n + m),
+        "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": 4 * 2 * (n + m) * args.d,
                 "d2h_bytes_per_step": 8 * K},
         "gpu_launches": launches,
         "clocks": clocks,
@@ -453,7 +463,7 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_served:
         line["served"] = bench_served(dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(reg, args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(reg, args.cpu_seconds, ref_sample_subs(args))
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -58,14 +58,15 @@ def test_job_totals_single_rank_needs_no_process_group():
 
 def test_ranks_match_different_replicas():
     import bench
-    args = argparse.Namespace(alpha=1.0, N=2000)
-    a, b = bench.workload(args, 0), bench.workload(args, 1)
-    assert a.sub_lo.shape == b.sub_lo.shape
-    assert not np.array_equal(a.sub_lo, b.sub_lo)
+    for d in (1, 3):
+        args = argparse.Namespace(alpha=1.0, N=2000, d=d)
+        a, b = bench.workload(args, 0), bench.workload(args, 1)
+        assert a.sub_lo.shape == b.sub_lo.shape == (d, 1000)
+        assert not np.array_equal(a.sub_lo, b.sub_lo)
 
 
 def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     import bench
     monkeypatch.setenv("RANK", "1")
-    bench.run_reference(argparse.Namespace(alpha=1.0, N=2000, steps=1, warmup=0, gpus=2))
+    bench.run_reference(argparse.Namespace(alpha=1.0, N=2000, d=1, steps=1, warmup=0, gpus=2))
     assert capsys.readouterr().out == ""
