@@ -247,8 +247,9 @@ __global__ void __launch_bounds__(WIN_BLOCK) k_emit_window(EmitArgs a, DevStatus
             const unsigned b1 = __ballot_sync(0xffffffffu, pass1);
             const int n0 = __popc(b0), n1 = __popc(b1);
             if (out + n0 + n1 > end) break;  // uniform: never write past the segment
-            if (pass0) out[__popc(b0 & lt)] = make_int2(i, (int32_t)((uint32_t)(kv0 >> 32) - j_base));
-            if (pass1) out[n0 + __popc(b1 & lt)] = make_int2(i, (int32_t)((uint32_t)(kv1 >> 32) - j_base));
+            // Streaming stores: the pairs are written once and not read back here.
+            if (pass0) __stcs(&out[__popc(b0 & lt)], make_int2(i, (int32_t)((uint32_t)(kv0 >> 32) - j_base)));
+            if (pass1) __stcs(&out[n0 + __popc(b1 & lt)], make_int2(i, (int32_t)((uint32_t)(kv1 >> 32) - j_base)));
             out += n0 + n1;
         }
         for (; kk < Wpad; kk += 32) {
@@ -256,7 +257,7 @@ __global__ void __launch_bounds__(WIN_BLOCK) k_emit_window(EmitArgs a, DevStatus
             const bool pass = ((uint32_t)kv < ph) & (spay[kk] > pl);
             const unsigned b = __ballot_sync(0xffffffffu, pass);
             if (out + __popc(b) > end) break;
-            if (pass) out[__popc(b & lt)] = make_int2(i, (int32_t)((uint32_t)(kv >> 32) - j_base));
+            if (pass) __stcs(&out[__popc(b & lt)], make_int2(i, (int32_t)((uint32_t)(kv >> 32) - j_base)));
             out += __popc(b);
         }
         if (lane == 0 && (out != end || kk < Wpad)) raise_error(st, DDM_ERR_INTERNAL, 12);
