@@ -253,37 +253,47 @@ def bench_served(dev, requests: int = 96, slots: int = 4, load: float = 0.8):
     served_sat_pairs = sum(r.K for r in sat) / sat_wall
     for s_ in sims:
         s_.close()
-    rate = load * capacity
-    gaps = rng.exponential(1.0 / rate, size=requests)
-    offsets = np.cumsum(gaps)
+    def at_load(lf: float):
+        rate_ = lf * capacity
+        offsets = np.cumsum(np.random.default_rng(int(lf * 1000)).exponential(1.0 / rate_,
+                                                                              size=requests))
+        # served: continuous batching at the offered load
+        sims = make_sims()
+        server = Server(sims, slots=slots)
+        t0 = time.perf_counter()
+        sreqs = []
+        for k, off in zip(order, offsets):
+            now = time.perf_counter() - t0
+            if off > now:
+                time.sleep(off - now)
+            sreqs.append(server.submit(int(k), arrival=t0 + off))
+        for r in sreqs:
+            r.done.wait(600)
+        served_wall = max(r.finish for r in sreqs) - t0
+        server.close()
+        srv = latency_summary(sreqs, served_wall)
+        for s_ in sims:
+            s_.close()
+        # plain at the same offered load (queueing included)
+        sims = make_sims()
+        t0 = time.perf_counter()
+        preqs = [Request(sim=int(k), arrival=t0 + off) for k, off in zip(order, offsets)]
+        run_plain(sims, preqs)
+        plain_wall = max(r.finish for r in preqs) - t0
+        pln = latency_summary(preqs, plain_wall)
+        for s_ in sims:
+            s_.close()
+        return rate_, srv, pln
 
-    # 2) served: continuous batching at the offered load
-    sims = make_sims()
-    server = Server(sims, slots=slots)
-    t0 = time.perf_counter()
-    sreqs = []
-    for k, off in zip(order, offsets):
-        now = time.perf_counter() - t0
-        if off > now:
-            time.sleep(off - now)
-        sreqs.append(server.submit(int(k), arrival=t0 + off))
-    for r in sreqs:
-        r.done.wait(600)
-    served_wall = max(r.finish for r in sreqs) - t0
-    server.close()
-    served = latency_summary(sreqs, served_wall)
-    for s_ in sims:
-        s_.close()
-
-    # 3) plain at the same offered load (queueing included)
-    sims = make_sims()
-    t0 = time.perf_counter()
-    preqs = [Request(sim=int(k), arrival=t0 + off) for k, off in zip(order, offsets)]
-    run_plain(sims, preqs)
-    plain_wall = max(r.finish for r in preqs) - t0
-    plain = latency_summary(preqs, plain_wall)
-    for s_ in sims:
-        s_.close()
+    sweep = {}
+    for lf in (0.5, 0.8, 1.0):
+        r_, srv, pln = at_load(lf)
+        sweep[str(lf)] = {"offered_rps": r_, "served_p50_ms": srv["p50_ms"],
+                          "served_p99_ms": srv["p99_ms"], "plain_p50_ms": pln["p50_ms"],
+                          "plain_p99_ms": pln["p99_ms"],
+                          "p99_speedup": pln["p99_ms"] / srv["p99_ms"] if srv["p99_ms"] else None}
+        if lf == load:
+            rate, served, plain = r_, srv, pln
     torch.cuda.empty_cache()
     return {"workload": "64 simulations, N log-uniform in [1e3, 1e6], d in {1,2,3}, "
                         "alpha in {0.01,1,100}, drift N(0, 0.1 side) per step, Poisson arrivals",
@@ -294,6 +304,7 @@ def bench_served(dev, requests: int = 96, slots: int = 4, load: float = 0.8):
                           "plain_rps": capacity, "served_rps": requests / sat_wall,
                           "throughput_speedup": served_sat_pairs / plain_sat_pairs},
             "p99_speedup": plain["p99_ms"] / served["p99_ms"] if served["p99_ms"] else None,
+            "load_sweep": sweep,
             "throughput_speedup": served["pairs_per_s"] / plain["pairs_per_s"]
             if plain["pairs_per_s"] else None}
 
@@ -458,6 +469,13 @@ def run_ours(args):
         "clocks": clocks,
         "wall_s_timed": wall,
     }
+    if args.d > 1:
+        # d > 1 is bound by the per-candidate filter: report the dimension-0
+        # candidates (pairs that intersect in dimension 0, an exact d = 1 count of
+        # the projection) resolved per second.
+        K0 = ctx.count(*[t[:1] for t in t_in])
+        line["candidates"] = {"dim0_candidates": K0,
+                              "candidate_tests_per_s": K0 * world / t_max_s * args.steps}
     if rank == 0 and world == 1 and not args.no_batched:
         line["batched"] = bench_batched(ctx, dev)
     if rank == 0 and world == 1 and not args.no_served:

@@ -153,10 +153,22 @@ int ddm_count_noalloc(const ddm_regions *regions, void *cuda_stream, uint64_t *K
  *                         programmatic dependent launch, so that each grid is
  *                         scheduled while its predecessor finishes; 0 = plain
  *                         stream order.  Results are identical.
+ *   DDM_PARAM_SWEEP_DIM   0 (default) = sweep dimension 0 and filter the others
+ *                         in the given order; 1 = choose the order: before a
+ *                         d > 1 ddm_count / ddm_match / ddm_match_host call the
+ *                         library counts, for every dimension k alone, the pairs
+ *                         whose extents intersect in k (the d = 1 pipeline on
+ *                         that dimension: d extra synchronous count passes), then
+ *                         sweeps the dimension with the fewest and prunes on the
+ *                         next (the paper's Section 3 reduction makes every order
+ *                         correct).  Results are identical; the order used is
+ *                         reported in ddm_stats.dim_order.  Sessions and batched
+ *                         calls always use the given order.
  */
 #define DDM_PARAM_WIN_SHIFT 1
 #define DDM_PARAM_ND_PATH 2
 #define DDM_PARAM_PDL 3
+#define DDM_PARAM_SWEEP_DIM 4
 int ddm_set_param(ddm_ctx *ctx, int param, int64_t value);
 
 /*
@@ -181,6 +193,10 @@ typedef struct {
     uint64_t launches;
     uint64_t calls;
     float stage_ms[DDM_STAGES];
+    /* Dimension order of the last plain call: dim_order[0] is the swept
+     * dimension, dim_order[1] the pruning one (identity unless
+     * DDM_PARAM_SWEEP_DIM = 1 reordered a d > 1 call). */
+    uint32_t dim_order[DDM_MAX_DIMS];
 } ddm_stats;
 
 int ddm_set_profiling(ddm_ctx *ctx, int enable);

@@ -7,5 +7,5 @@ Matching for Data Distribution Management on Shared-Memory Multiprocessors"
 include/ddm.h; this package is its thin Python binding.
 """
 from ._lib import (CapacityError, Context, DDMError, LIB_PATH, NOALLOC_MAX_REGIONS,  # noqa: F401
-                   Session, SIGNATURES, count_noalloc, load_library, STAGE_NAMES, PARAM_PDL)
+                   Session, SIGNATURES, count_noalloc, load_library, STAGE_NAMES, PARAM_PDL, PARAM_SWEEP_DIM)
 from .build import build as build_library  # noqa: F401

@@ -28,6 +28,7 @@ MAX_DIMS = 8
 PARAM_WIN_SHIFT = 1
 PARAM_ND_PATH = 2
 PARAM_PDL = 3
+PARAM_SWEEP_DIM = 4
 
 
 class DDMError(RuntimeError):
@@ -44,7 +45,7 @@ class CapacityError(DDMError):
 
 class Stats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_uint64), ("calls", ctypes.c_uint64),
-                ("stage_ms", ctypes.c_float * 8)]
+                ("stage_ms", ctypes.c_float * 8), ("dim_order", ctypes.c_uint32 * 8)]
 
 
 STAGE_NAMES = ["keybuild", "radix_sort", "sweep_scan", "counts", "offsets", "emit_setup", "emit",
@@ -233,7 +234,8 @@ class Context:
         s = Stats()
         self._check(self._lib.ddm_get_stats(self._h, ctypes.byref(s)))
         return {"launches": int(s.launches), "calls": int(s.calls),
-                "stage_ms": dict(zip(STAGE_NAMES, [float(x) for x in s.stage_ms]))}
+                "stage_ms": dict(zip(STAGE_NAMES, [float(x) for x in s.stage_ms])),
+                "dim_order": [int(x) for x in s.dim_order]}
 
     # -- entry points ----------------------------------------------------------
     def count(self, sub_lo, sub_hi, upd_lo, upd_hi) -> int:

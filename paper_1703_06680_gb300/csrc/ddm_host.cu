@@ -43,6 +43,7 @@ struct ddm_ctx {
     int win_shift = 8;                            // DDM_PARAM_WIN_SHIFT
     int nd_path = 0;                              // DDM_PARAM_ND_PATH
     bool pdl = true;                              // DDM_PARAM_PDL
+    int sweep_dim = 0;                            // DDM_PARAM_SWEEP_DIM
     cudaEvent_t ev[DDM_STAGES + 1] = {};
 };
 
@@ -587,6 +588,11 @@ int ddm_set_param(ddm_ctx* c, int param, int64_t value) {
         c->nd_path = (int)value;
         return DDM_OK;
     }
+    if (param == DDM_PARAM_SWEEP_DIM) {
+        if (value < 0 || value > 1) return fail(c, DDM_ERR_INVALID, "sweep dim must be 0 or 1");
+        c->sweep_dim = (int)value;
+        return DDM_OK;
+    }
     if (param == DDM_PARAM_PDL) {
         if (value < 0 || value > 1) return fail(c, DDM_ERR_INVALID, "pdl must be 0 or 1");
         c->pdl = value != 0;
@@ -601,12 +607,61 @@ int ddm_get_stats(const ddm_ctx* c, ddm_stats* out) {
     return DDM_OK;
 }
 
+// Dimension order of a plain call (DDM_PARAM_SWEEP_DIM).  Section 3 of the
+// paper reduces d dimensions to the logical "and" of d one-dimensional tests,
+// so any order gives the same pairs; the cost, though, grows with the pairs
+// that intersect in the swept dimension (every one is a candidate of the
+// filter) and, for the tiled join, in the pruning dimension.  With the
+// automatic choice each dimension's one-dimensional pair count is computed
+// exactly (a d = 1 count pass) and the dimensions are taken in increasing
+// order of it.  `out` receives the reordered descriptor; `hold` owns its
+// pointer arrays.
+int order_dims(ddm_ctx* c, const ddm_regions* r, ddm_regions* out,
+               std::vector<const float*>& hold) {
+    *out = *r;
+    for (int k = 0; k < DDM_MAX_DIMS; ++k) c->stats.dim_order[k] = (uint32_t)k;
+    const int d = r->d;
+    if (c->sweep_dim != 1 || d < 2 || r->n == 0 || r->m == 0) return DDM_OK;
+    std::vector<std::pair<uint64_t, int>> cnt(d);
+    for (int k = 0; k < d; ++k) {
+        ddm_regions r1{};
+        r1.d = 1; r1.n = r->n; r1.m = r->m;
+        r1.sub_lo = &r->sub_lo[k]; r1.sub_hi = &r->sub_hi[k];
+        r1.upd_lo = &r->upd_lo[k]; r1.upd_hi = &r->upd_hi[k];
+        uint64_t K = 0;
+        int rc = enqueue_plain(c, &r1, Mode::Count, nullptr, 0, nullptr);
+        if (rc) return rc;
+        rc = finish(c, &K);
+        if (rc) return rc;
+        cnt[k] = {K, k};
+    }
+    std::stable_sort(cnt.begin(), cnt.end());
+    hold.assign(4 * (size_t)d, nullptr);
+    for (int k = 0; k < d; ++k) {
+        const int src = cnt[k].second;
+        hold[k] = r->sub_lo[src];
+        hold[d + k] = r->sub_hi[src];
+        hold[2 * d + k] = r->upd_lo[src];
+        hold[3 * d + k] = r->upd_hi[src];
+        c->stats.dim_order[k] = (uint32_t)src;
+    }
+    out->sub_lo = &hold[0];
+    out->sub_hi = &hold[d];
+    out->upd_lo = &hold[2 * d];
+    out->upd_hi = &hold[3 * d];
+    return DDM_OK;
+}
+
 int ddm_count(ddm_ctx* c, const ddm_regions* r, uint64_t* K_out) {
     if (!c) return DDM_ERR_INVALID;
     int rc = check_regions(c, r);
     if (rc) return rc;
     DeviceGuard g(c->device);
-    rc = enqueue_plain(c, r, Mode::Count, nullptr, 0, nullptr);
+    ddm_regions ro;
+    std::vector<const float*> hold;
+    rc = order_dims(c, r, &ro, hold);
+    if (rc) return rc;
+    rc = enqueue_plain(c, &ro, Mode::Count, nullptr, 0, nullptr);
     if (rc) return rc;
     return finish(c, K_out);
 }
@@ -617,7 +672,11 @@ int ddm_match(ddm_ctx* c, const ddm_regions* r, int32_t* pairs, uint64_t cap, ui
     if (rc) return rc;
     if (!pairs && cap > 0) return fail(c, DDM_ERR_INVALID, "pairs is NULL but cap > 0");
     DeviceGuard g(c->device);
-    rc = enqueue_plain(c, r, Mode::Match, pairs, cap, nullptr);
+    ddm_regions ro;
+    std::vector<const float*> hold;
+    rc = order_dims(c, r, &ro, hold);
+    if (rc) return rc;
+    rc = enqueue_plain(c, &ro, Mode::Match, pairs, cap, nullptr);
     if (rc) return rc;
     return finish(c, K_out);
 }
@@ -651,11 +710,15 @@ int ddm_match_host(ddm_ctx* c, const ddm_regions* r, int32_t* pairs, uint64_t ca
             dp[a * d + k] = dst;
         }
     }
-    ddm_regions dr = *r;
-    dr.sub_lo = &dp[0];
-    dr.sub_hi = &dp[d];
-    dr.upd_lo = &dp[2 * d];
-    dr.upd_hi = &dp[3 * d];
+    ddm_regions dr0 = *r;
+    dr0.sub_lo = &dp[0];
+    dr0.sub_hi = &dp[d];
+    dr0.upd_lo = &dp[2 * d];
+    dr0.upd_hi = &dp[3 * d];
+    ddm_regions dr;
+    std::vector<const float*> hold;
+    rc = order_dims(c, &dr0, &dr, hold);
+    if (rc) return rc;
     // Run the pipeline up to the exact K, size the device output, then emit.
     Job job;
     job.d = dr.d; job.n = dr.n; job.m = dr.m; job.r = &dr;

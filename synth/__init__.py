@@ -101,6 +101,16 @@ def make_regions(d: int, n: int, m: int, side: float, seed: int,
     return Regions(s_lo, s_hi, u_lo, u_hi)
 
 
+def make_regions_aniso(n: int, m: int, sides, seed: int, L: float = ROUTING_SPACE) -> Regions:
+    """Uniform placement on [0, L)^d with a side of its own per dimension
+    (dimension k drawn as a one-dimensional instance with side sides[k] and
+    seed + k): extents that are long along some dimensions and short along
+    others, for the choice of the swept dimension."""
+    parts = [make_regions(1, n, m, float(sd), seed + k, L) for k, sd in enumerate(sides)]
+    return Regions(*(np.concatenate([getattr(p, f) for p in parts], axis=0)
+                     for f in ("sub_lo", "sub_hi", "upd_lo", "upd_hi")))
+
+
 def side_for(alpha: float, N: int, d: int, L: float = ROUTING_SPACE) -> float:
     """Side length giving overlapping degree alpha for N extents in d dimensions."""
     if d == 1:

@@ -253,3 +253,32 @@ def test_pdl_off_and_profiling_modes(d, alpha):
     finally:
         c.set_profiling(False)
         c.close()
+
+
+@pytest.mark.parametrize("sides", [(5.0e4, 20.0, 2.0e3), (500.0, 5.0e4, 5.0e3), (3.0e3, 3.0e3)])
+def test_sweep_dimension_choice(sides):
+    # Any dimension order gives the same pairs (Section 3); with the automatic
+    # choice the library sweeps the dimension with the fewest one-dimensional
+    # intersections, which the oracle's per-dimension counts predict exactly.
+    import paper_1703_06680_gb300 as ddm
+    reg = synth.make_regions_aniso(20_000, 25_000, sides, 4242)
+    d = reg.d
+    want = oracle.sbm(reg)
+    one_d = [oracle.sbm_count(synth.Regions(reg.sub_lo[k:k + 1], reg.sub_hi[k:k + 1],
+                                            reg.upd_lo[k:k + 1], reg.upd_hi[k:k + 1]))
+             for k in range(d)]
+    expected = sorted(range(d), key=lambda k: (one_d[k], k))
+    c = ddm.Context(0)
+    try:
+        for mode in (0, 1):
+            c.set_param(ddm.PARAM_SWEEP_DIM, mode)
+            assert np.array_equal(gpu_pairs(c, reg), want), mode
+            assert c.stats()["dim_order"][:d] == (expected if mode == 1 else list(range(d)))
+            assert c.count(*to_dev(reg)) == len(want)
+            host = c.match_host(reg.sub_lo, reg.sub_hi, reg.upd_lo, reg.upd_hi,
+                                cap=len(want) + 1)
+            assert np.array_equal(host, want)
+        with pytest.raises(ddm.DDMError):
+            c.set_param(ddm.PARAM_SWEEP_DIM, 2)
+    finally:
+        c.close()
