@@ -70,6 +70,7 @@ def test_tune_d2_uses_strategy_only_and_merges_cache(tmp_path):
 
     chosen = autotune.tune(ctx, tensors(2, 50, 60), cache_path=str(cache), gpu="G", timer=timer)
     assert chosen["nd_path"] == 2 and "win_shift" not in chosen
+    assert chosen["sweep_dim"] == 0                   # equal times: the first candidate
     stored = json.loads(cache.read_text())
     assert stored["other"] == {"win_shift": 7}       # earlier entries kept
     assert stored[chosen["key"]]["nd_path"] == 2
