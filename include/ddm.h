@@ -260,6 +260,28 @@ int ddm_session_emit(ddm_session *s, void *cuda_stream, int32_t *pairs, uint64_t
                      uint64_t *K_out);
 
 /*
+ * Incremental matching: the change report of one timestep.  After
+ * ddm_session_count, computes this timestep's pairs into session-owned device
+ * memory and compares them with the pairs of the previous successful
+ * ddm_session_emit_delta call (an empty list before the first one):
+ *   added   (DEVICE, 2 * cap_added int32)   pairs present now and not before,
+ *   removed (DEVICE, 2 * cap_removed int32) pairs present before and not now,
+ * both sorted lexicographically; *n_added / *n_removed receive their numbers.
+ * Bounds: n_added <= K of this timestep, n_removed <= K of the previous one.
+ * If either list does not fit, returns DDM_ERR_CAPACITY with both numbers set
+ * and keeps the new timestep pending: calling ddm_session_emit_delta again,
+ * without a new count, writes the same report into larger buffers.  On
+ * success the current pairs become the reference of the next call.  The
+ * session then holds two pair lists (16 K bytes) and their offsets; memory is
+ * taken on first use.  Synchronous.  Other errors as for ddm_session_emit.
+ * The paper recomputes the full match every timestep; reporting changes is
+ * the dynamic DDM it names as future work (Section 6).
+ */
+int ddm_session_emit_delta(ddm_session *s, void *cuda_stream, int32_t *added, uint64_t cap_added,
+                           int32_t *removed, uint64_t cap_removed, uint64_t *n_added,
+                           uint64_t *n_removed);
+
+/*
  * Diagnostic view of the sweep stages for dimension 0 (the sorted endpoint
  * list T of Algorithm 4 and the active-set sizes it maintains), for tests.
  * All outputs are DEVICE memory, E = 2(n+m) entries unless noted:

@@ -86,6 +86,8 @@ SIGNATURES = {
     "ddm_session_drift": (ctypes.c_int, [_P, _P, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double]),
     "ddm_session_count": (ctypes.c_int, [_P, _P, _U64P]),
     "ddm_session_emit": (ctypes.c_int, [_P, _P, _P, ctypes.c_uint64, _U64P]),
+    "ddm_session_emit_delta": (ctypes.c_int, [_P, _P, _P, ctypes.c_uint64, _P, ctypes.c_uint64,
+                                              _U64P, _U64P]),
     "ddm_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(Stats)]),
 }
 
@@ -375,6 +377,8 @@ class Session:
         if rc != DDM_OK:
             raise DDMError(rc, "ddm_session_create failed")
         self._h = h
+        self._K_last = 0   # K of the last count()
+        self._K_ref = 0    # K of the reference list of emit_delta()
 
     def close(self):
         if getattr(self, "_h", None):
@@ -406,6 +410,7 @@ class Session:
     def count(self, stream=None) -> int:
         K = ctypes.c_uint64(0)
         self._check(self._lib.ddm_session_count(self._h, self._stream(stream), ctypes.byref(K)))
+        self._K_last = int(K.value)
         return int(K.value)
 
     def emit(self, out, stream=None) -> int:
@@ -417,6 +422,26 @@ class Session:
                                         ctypes.byref(K))
         self._check(rc, K.value)
         return int(K.value)
+
+    def emit_delta(self, added=None, removed=None, stream=None):
+        """Change report of the last count() against the previous emit_delta():
+        returns (added, removed) as (rows, 2) int32 CUDA tensors, each sorted.  Given
+        output tensors are filled and sliced; otherwise they are allocated at the
+        bounds (this timestep's K and the previous report's K)."""
+        import torch
+        dev = torch.device("cuda", self.device)
+        if added is None:
+            added = torch.empty((max(self._K_last, 1), 2), dtype=torch.int32, device=dev)
+        if removed is None:
+            removed = torch.empty((max(self._K_ref, 1), 2), dtype=torch.int32, device=dev)
+        na, nr = ctypes.c_uint64(0), ctypes.c_uint64(0)
+        rc = self._lib.ddm_session_emit_delta(
+            self._h, self._stream(stream), ctypes.c_void_p(added.data_ptr()), added.shape[0],
+            ctypes.c_void_p(removed.data_ptr()), removed.shape[0], ctypes.byref(na),
+            ctypes.byref(nr))
+        self._check(rc, max(na.value, nr.value))
+        self._K_ref = self._K_last
+        return added[:na.value], removed[:nr.value]
 
     def coords(self):
         """Copies of the resident coordinates as (d, count) float32 CUDA tensors."""

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "batch.cuh"
+#include "delta.cuh"
 #include "drift.cuh"
 #include "emit.cuh"
 #include "sort.cuh"
@@ -782,6 +783,19 @@ struct ddm_session {
     ddm_regions regions{};
     bool counted = false;     // a pipeline prefix is held in the workspace
     uint64_t K = 0;
+    // Incremental matching (ddm_session_emit_delta): two pair lists with their
+    // offsets; `ref` indexes the reference (previous) list, the other one
+    // receives the new timestep.
+    char* list[2] = {};
+    size_t list_size[2] = {};
+    char* loff[2] = {};
+    size_t loff_size[2] = {};
+    char* dwork = nullptr;    // per-sub counts and offsets of the report, scan status
+    size_t dwork_size = 0;
+    int ref = 0;
+    bool have_ref = false;    // a reference list exists (else: empty)
+    bool pending = false;     // new list computed, report not yet delivered
+    uint64_t K_ref = 0, K_new = 0;
 };
 
 namespace {
@@ -849,6 +863,11 @@ int ddm_session_destroy(ddm_session* s) {
     if (s->ctx) {
         DeviceGuard g(s->ctx->device);
         if (s->coords) cudaFree(s->coords);  // every session call is synchronous
+        for (int k = 0; k < 2; ++k) {
+            if (s->list[k]) cudaFree(s->list[k]);
+            if (s->loff[k]) cudaFree(s->loff[k]);
+        }
+        if (s->dwork) cudaFree(s->dwork);
         ddm_destroy(s->ctx);
     }
     delete s;
@@ -889,6 +908,7 @@ int ddm_session_count(ddm_session* s, void* stream, uint64_t* K_out) {
     DeviceGuard g(c->device);
     c->stream = reinterpret_cast<cudaStream_t>(stream);
     s->counted = false;
+    s->pending = false;  // a new timestep replaces an undelivered change report
     int rc = enqueue(c, session_job(s), Mode::Match, nullptr, 0, nullptr, Phase::Prefix);
     if (rc) return rc;
     uint64_t K = 0;
@@ -913,6 +933,105 @@ int ddm_session_emit(ddm_session* s, void* stream, int32_t* pairs, uint64_t cap,
     int rc = enqueue(c, session_job(s), Mode::Match, pairs, cap, nullptr, Phase::Suffix);
     if (rc) return rc;
     return finish(c, K_out);
+}
+
+int ddm_session_emit_delta(ddm_session* s, void* stream, int32_t* added, uint64_t cap_added,
+                           int32_t* removed, uint64_t cap_removed, uint64_t* n_added,
+                           uint64_t* n_removed) {
+    if (!s) return DDM_ERR_INVALID;
+    ddm_ctx* c = s->ctx;
+    DeviceGuard g(c->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    c->stream = st;
+    const Job job = session_job(s);
+    const int64_t n = job.n;
+    const int cur = s->ref ^ 1;
+    int rc;
+    if (s->counted) {  // this timestep's pairs into the session's list
+        rc = ensure(c, &s->list[cur], &s->list_size[cur], std::max<size_t>(16, 8 * s->K));
+        if (rc) return rc;
+        rc = ensure(c, &s->loff[cur], &s->loff_size[cur], 8 * (size_t)(n + 1));
+        if (rc) return rc;
+        s->counted = false;
+        rc = enqueue(c, job, Mode::Match, reinterpret_cast<int32_t*>(s->list[cur]), s->K, nullptr,
+                     Phase::Suffix);
+        if (rc) return rc;
+        Plan pl;  // the layout the emission just used: its offsets off[0..n]
+        pl.layout(c->ws, job.d, job.n, job.m, Mode::Match, job.num_inst, c->win_shift, c->nd_path);
+        CK(cudaMemcpyAsync(s->loff[cur], pl.off, 8 * (size_t)(n + 1), cudaMemcpyDeviceToDevice, st));
+        rc = finish(c, nullptr);
+        if (rc) return rc;
+        s->K_new = s->K;
+        s->pending = true;
+    }
+    if (!s->pending)
+        return fail(c, DDM_ERR_INVALID, "ddm_session_emit_delta needs ddm_session_count first");
+    if (!s->have_ref) {  // before the first report: an empty reference list
+        rc = ensure(c, &s->list[s->ref], &s->list_size[s->ref], 16);
+        if (rc) return rc;
+        rc = ensure(c, &s->loff[s->ref], &s->loff_size[s->ref], 8 * (size_t)(n + 1));
+        if (rc) return rc;
+        CK(cudaMemsetAsync(s->loff[s->ref], 0, 8 * (size_t)(n + 1), st));
+        s->K_ref = 0;
+        s->have_ref = true;
+    }
+    // Work area: counts u32[n] x 2, offsets u64[n + 1] x 2, scan status x 2.
+    const size_t stat_words = (size_t)ceil_div((uint64_t)n, OFF_TILE) + 2;
+    Carve cv;  // sizes only
+    cv.take<uint32_t>(n);
+    cv.take<uint32_t>(n);
+    cv.take<unsigned long long>(n + 1);
+    cv.take<unsigned long long>(n + 1);
+    const size_t stat_off = (cv.off + 255) & ~(size_t)255;  // where take() puts the status
+    cv.take<unsigned long long>(stat_words);
+    cv.take<unsigned long long>(stat_words);
+    rc = ensure(c, &s->dwork, &s->dwork_size, cv.off);
+    if (rc) return rc;
+    Carve real;
+    real.base = s->dwork;
+    uint32_t* add_cnt = real.take<uint32_t>(n);
+    uint32_t* rem_cnt = real.take<uint32_t>(n);
+    unsigned long long* add_off = real.take<unsigned long long>(n + 1);
+    unsigned long long* rem_off = real.take<unsigned long long>(n + 1);
+    unsigned long long* st_add = real.take<unsigned long long>(stat_words);
+    unsigned long long* st_rem = real.take<unsigned long long>(stat_words);
+    if ((char*)st_add != s->dwork + stat_off) return fail(c, DDM_ERR_INTERNAL, "work layout");
+    CK(cudaMemsetAsync(s->dwork + stat_off, 0, cv.off - stat_off, st));
+    CK(cudaMemsetAsync(c->dstat, 0, sizeof(DevStatus), st));
+    PdlScope pdl_scope(c->pdl);
+    DeltaArgs da{};
+    da.n = n;
+    da.prev = reinterpret_cast<const int32_t*>(s->list[s->ref]);
+    da.prev_off = reinterpret_cast<const unsigned long long*>(s->loff[s->ref]);
+    da.cur = reinterpret_cast<const int32_t*>(s->list[cur]);
+    da.cur_off = reinterpret_cast<const unsigned long long*>(s->loff[cur]);
+    da.add_cnt = add_cnt;
+    da.rem_cnt = rem_cnt;
+    c->stats.launches += launch_delta(da, false, c->dstat, st);
+    c->stats.launches += launch_offsets(add_cnt, n, add_off, ~0ull, &c->dstat->aux[0], st_add,
+                                        c->dstat, st);
+    c->stats.launches += launch_offsets(rem_cnt, n, rem_off, ~0ull, &c->dstat->aux[1], st_rem,
+                                        c->dstat, st);
+    rc = finish(c, nullptr);
+    if (rc) return rc;
+    const uint64_t na = c->hstat->aux[0], nr = c->hstat->aux[1];
+    if (n_added) *n_added = na;
+    if (n_removed) *n_removed = nr;
+    if (na > cap_added || nr > cap_removed)
+        return fail(c, DDM_ERR_CAPACITY, "change report does not fit: " + std::to_string(na) +
+                                             " added, " + std::to_string(nr) + " removed");
+    if ((na && !added) || (nr && !removed)) return fail(c, DDM_ERR_INVALID, "output is NULL");
+    da.add_off = add_off;
+    da.rem_off = rem_off;
+    da.added = added;
+    da.removed = removed;
+    c->stats.launches += launch_delta(da, true, c->dstat, st);
+    rc = finish(c, nullptr);
+    if (rc) return rc;
+    s->ref = cur;  // the new list is the reference of the next report
+    s->K_ref = s->K_new;
+    s->pending = false;
+    return DDM_OK;
 }
 
 int ddm_debug_sweep(ddm_ctx* c, const ddm_regions* r, uint32_t* sorted_who,

@@ -134,3 +134,56 @@ def test_mix_matches_oracle(ddm):
         assert np.array_equal(r.pairs, oracle.sbm(hosts[r.sim])), (r.sim, r.step)
     for o in objs:
         o.close()
+
+
+def _rows_minus(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Rows of the (k, 2) int32 array a that are not rows of b, sorted."""
+    ka = (a[:, 0].astype(np.int64) << 32) | a[:, 1].astype(np.int64)
+    kb = (b[:, 0].astype(np.int64) << 32) | b[:, 1].astype(np.int64)
+    k = np.setdiff1d(ka, kb)
+    return np.stack([(k >> 32).astype(np.int32), (k & 0xFFFFFFFF).astype(np.int32)], axis=1)
+
+
+def test_emit_delta_matches_oracle_differences(ddm):
+    # Every report equals the set differences of the oracle's pair lists of two
+    # consecutive timesteps (first report: everything is added).
+    for sim in small_sims(6, seed=11):
+        sess = ddm.Session(*to_dev(sim["reg"]))
+        host = sim["reg"]
+        prev = np.zeros((0, 2), np.int32)
+        for step in range(4):
+            sess.drift(sim["seed"], step, sim["sigma"])
+            host = synth.drift(host, sim["seed"], step, sim["sigma"])
+            want = oracle.sbm(host)
+            assert sess.count() == len(want)
+            added, removed = sess.emit_delta()
+            assert np.array_equal(added.cpu().numpy(), _rows_minus(want, prev)), step
+            assert np.array_equal(removed.cpu().numpy(), _rows_minus(prev, want)), step
+            prev = want
+        sess.close()
+
+
+def test_emit_delta_no_motion_and_capacity_retry(ddm):
+    import torch
+    reg = synth.make_regions(2, 3000, 3500, 3000.0, 5151)
+    sess = ddm.Session(*to_dev(reg))
+    with pytest.raises(ddm.DDMError):
+        sess.emit_delta()                          # no count yet
+    K = sess.count()
+    added, removed = sess.emit_delta()
+    assert len(added) == K and len(removed) == 0
+    sess.drift(1, 0, 0.0)                          # no motion: nothing changes
+    sess.count()
+    added, removed = sess.emit_delta()
+    assert len(added) == 0 and len(removed) == 0
+    host = synth.drift(reg, 9, 1, 400.0)
+    sess.drift(9, 1, 400.0)
+    sess.count()
+    small = torch.empty((1, 2), dtype=torch.int32, device="cuda:0")
+    with pytest.raises(ddm.CapacityError):
+        sess.emit_delta(small, small)
+    added, removed = sess.emit_delta()             # the pending report, into larger buffers
+    want_prev, want = oracle.sbm(reg), oracle.sbm(host)
+    assert np.array_equal(added.cpu().numpy(), _rows_minus(want, want_prev))
+    assert np.array_equal(removed.cpu().numpy(), _rows_minus(want_prev, want))
+    sess.close()
