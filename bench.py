@@ -213,6 +213,53 @@ def bench_batched(ctx, dev, steps: int = 3):
             "speedup_vs_plain": pw / bw}
 
 
+def bench_incremental(args, dev, steps: int = 10):
+    """The headline workload as a session: every timestep drifts the extents by
+    N(0, 0.01 side) and reports only the pairs that appeared or disappeared
+    (ddm_session_emit_delta), against count + full emission of the same timestep."""
+    import torch
+    import paper_1703_06680_gb300 as ddm
+    reg = workload(args, 0)
+    t_in = [torch.from_numpy(a).to(dev) for a in (reg.sub_lo, reg.sub_hi, reg.upd_lo, reg.upd_hi)]
+    sess = ddm.Session(*t_in)
+    sigma = 0.01 * synth.side_for(args.alpha, args.N, args.d)
+    sess.count()
+    sess.emit_delta()
+    stream = torch.cuda.current_stream(dev)
+    t_delta, added, removed, K = 0.0, 0, 0, 0
+    for s in range(steps):
+        sess.drift(1703, s, sigma)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        K = sess.count()
+        a, r = sess.emit_delta()
+        e1.record(stream)
+        e1.synchronize()
+        t_delta += e0.elapsed_time(e1)
+        added += len(a)
+        removed += len(r)
+    out = torch.empty((max(K, 1), 2), dtype=torch.int32, device=dev)
+    t_full = 0.0
+    for s in range(steps):
+        sess.drift(1703, 1000 + s, sigma)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        K2 = sess.count()
+        if K2 > out.shape[0]:
+            out = torch.empty((K2, 2), dtype=torch.int32, device=dev)
+        sess.emit(out[:K2])
+        e1.record(stream)
+        e1.synchronize()
+        t_full += e0.elapsed_time(e1)
+    sess.close()
+    return {"workload": workload_name(args) + ", session with drift N(0, 0.01 side) per step",
+            "steps": steps, "K": K, "report_ms": t_delta / steps, "full_emit_ms": t_full / steps,
+            "added_per_step": added / steps, "removed_per_step": removed / steps,
+            "report_bytes_per_step": 8 * (added + removed) / steps, "full_bytes_per_step": 8 * K}
+
+
 def bench_served(dev, requests: int = 96, slots: int = 4, load: float = 0.8):
     """64 simulations (N log-uniform in [1e3, 1e6], d and alpha uniform), drift between
     timesteps, Poisson arrivals at `load` x the plain path's measured capacity."""
@@ -480,6 +527,7 @@ def run_ours(args):
         line["batched"] = bench_batched(ctx, dev)
     if rank == 0 and world == 1 and not args.no_served:
         line["served"] = bench_served(dev)
+        line["incremental"] = bench_incremental(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(reg, args.cpu_seconds, ref_sample_subs(args))
     if rank == 0:
