@@ -272,8 +272,8 @@ __global__ void __launch_bounds__(EMIT_BLOCK) k_segsort_warp(EmitArgs a, DevStat
 
 // One block per long segment: LSD radix sort of the update-id column, 8 bits
 // per pass, using the segment's own subscription-id column as the ping-pong
-// buffer; the subscription ids are rewritten at the end.  Stable ranking as in
-// the onesweep pass (match_any within a warp, warp-ordered chunks).
+// buffer; the subscription ids are rewritten at the end.  Stable ranking:
+// peers of equal digits found with match_any within a warp, warp-ordered chunks.
 __global__ void __launch_bounds__(BIG_BLOCK) k_segsort_big(EmitArgs a, DevStatus* st) {
     pdl_begin();
     constexpr int WARPS = BIG_BLOCK / 32;

@@ -56,7 +56,7 @@ int launch_keybuild_d0(const float* sub_lo, const float* sub_hi, const float* up
 }
 
 // ---------------------------------------------------------------------------
-// a2: onesweep pass
+// a2: one pass per digit (upsweep histogram, downsweep ranking and scatter)
 // ---------------------------------------------------------------------------
 
 // Exclusive scan of one value per thread over a 256-thread block.

@@ -1,4 +1,4 @@
-// Endpoint key build (a1) and onesweep LSD radix sort (a2): interfaces.
+// Endpoint key build (a1) and LSD radix sort (a2): interfaces.
 #pragma once
 
 #include <cstdint>
