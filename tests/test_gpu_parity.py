@@ -282,3 +282,11 @@ def test_sweep_dimension_choice(sides):
             c.set_param(ddm.PARAM_SWEEP_DIM, 2)
     finally:
         c.close()
+
+
+def test_plain_sort_beyond_fused_offsets(ctx):
+    # E = 6e6 endpoints: over 1024 sort tiles, so the 32-bit sort takes the flat
+    # decoupled-look-back scan between upsweep and downsweep instead of the
+    # in-downsweep group sums; the offsets scan over 1.5e6 subscriptions needs
+    # several look-back rounds.
+    assert_parity(ctx, synth.large_1d(1.0, N=3_000_000))
