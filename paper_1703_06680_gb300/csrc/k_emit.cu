@@ -256,7 +256,8 @@ __global__ void __launch_bounds__(EMIT_BLOCK) k_segsort_warp(EmitArgs a, DevStat
         for (uint32_t size = 2; size <= P; size <<= 1) {
             for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
                 for (uint32_t t = lane; t < P / 2; t += 32) {
-                    const uint32_t lo = 2 * stride * (t / stride) + (t % stride);
+                    // 2 * stride * (t / stride) + t % stride, stride a power of two
+                    const uint32_t lo = ((t & ~(stride - 1)) << 1) | (t & (stride - 1));
                     const uint32_t hi = lo + stride;
                     const bool up = (lo & size) == 0;
                     const uint32_t x = buf[lo], y = buf[hi];
