@@ -290,3 +290,38 @@ def test_plain_sort_beyond_fused_offsets(ctx):
     # in-downsweep group sums; the offsets scan over 1.5e6 subscriptions needs
     # several look-back rounds.
     assert_parity(ctx, synth.large_1d(1.0, N=3_000_000))
+
+
+@pytest.mark.parametrize("d,alpha", [(1, 100.0), (2, 100.0), (3, 1.0)])
+def test_swap_symmetry_and_dimension_monotonicity(ctx, d, alpha):
+    # Exchanging the roles of subscriptions and updates transposes the pair set
+    # (Algorithm 1 is symmetric); dropping a dimension can only add pairs
+    # (Section 3's logical and).
+    reg = synth.large_1d(alpha, N=100_000) if d == 1 else synth.large_nd(d, alpha, N=60_000)
+    got = gpu_pairs(ctx, reg)
+    sw = gpu_pairs(ctx, reg.swapped())
+    assert len(sw) == len(got)
+    back = sw[:, ::-1]
+    order = np.lexsort((back[:, 1], back[:, 0]))
+    assert np.array_equal(back[order], got)
+    prev = len(got)
+    for k in range(d - 1, 0, -1):
+        K = ctx.count(*to_dev(reg.subset_dims(k)))
+        assert K >= prev
+        prev = K
+
+
+def test_memory_budget_exhaustion_is_reported():
+    # A context whose scratch budget is too small fails with DDM_ERR_NOMEM
+    # (no device fault), and the same GPU keeps working afterwards.
+    import paper_1703_06680_gb300 as ddm
+    reg = synth.large_1d(1.0, N=200_000)
+    small = ddm.Context(0, mem_budget=1 << 20)
+    try:
+        with pytest.raises(ddm.DDMError) as e:
+            small.count(*to_dev(reg))
+        assert e.value.code == ddm._lib.DDM_ERR_NOMEM
+    finally:
+        small.close()
+    with ddm.Context(0) as c:
+        assert c.count(*to_dev(reg)) == oracle.sbm_count(reg)
