@@ -171,7 +171,6 @@ struct Plan {
     unsigned long long* scan_status;
     unsigned long long* off_status;
     uint32_t* cursor_b;
-    uint32_t* big_count;
     // window path (d = 1, match) and tiled join (d > 1)
     bool window, join;
     int win_shift;
@@ -192,7 +191,7 @@ struct Plan {
     void *keys0, *keys1;
     uint32_t *vals0, *vals1;
     Records rec;
-    uint32_t *cnt, *cnt_a, *upd_cnt, *big_list;
+    uint32_t *cnt, *cnt_a, *upd_cnt;
     unsigned long long* off;
     uint2 *subK, *updK;
     // batch
@@ -220,7 +219,6 @@ struct Plan {
         scan_status = cv.take<unsigned long long>(3 * (ceil_div(E, SCAN_TILE) + 1) + 1);
         off_status = cv.take<unsigned long long>(ceil_div(n, OFF_TILE) + 2);
         cursor_b = cv.take<uint32_t>(mode == Mode::Match ? n : 0);
-        big_count = cv.take<uint32_t>(2);
         window = mode == Mode::Match && d == 1;
         join = d > 1 && mode != Mode::Debug && nd_path != 2;
         const bool lists = window || join;
@@ -260,7 +258,6 @@ struct Plan {
         cnt = cv.take<uint32_t>(n);
         cnt_a = cv.take<uint32_t>(d > 1 ? n : 0);
         upd_cnt = nullptr;
-        big_list = cv.take<uint32_t>(mode == Mode::Match ? n : 0);
         off = cv.take<unsigned long long>(n + 1);
         subK = cv.take<uint2>(d > 1 ? (size_t)(d - 1) * n : 0);
         updK = cv.take<uint2>(d > 1 ? (size_t)(d - 1) * m : 0);
@@ -373,7 +370,6 @@ int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
     a.cnt = pl.cnt; a.off = pl.off; a.cnt_a = pl.cnt_a; a.cursor_b = pl.cursor_b;
     a.subK = pl.subK; a.updK = pl.updK;
     a.pairs = pairs; a.cap = cap;
-    a.big_list = pl.big_list; a.big_count = pl.big_count;
     a.id_bits = id_bits(pl.m);
     a.inst_sub_base = batch ? pl.n_base : nullptr;
     a.inst_upd_base = batch ? pl.m_base : nullptr;

@@ -30,8 +30,6 @@ struct EmitArgs {
     uint2* updK;                    // (d-1) x m keys of dims 1.., in upd_order layout
     int32_t* pairs;                 // 2 * cap ints
     unsigned long long cap;
-    uint32_t* big_list;             // subscriptions whose segment needs the block sort
-    uint32_t* big_count;            // [0] = list length, [1] = work counter (zeroed)
     int id_bits;                    // bits of the largest update id (radix passes)
     // Batched mode: ids are written local to their instance (see batch code).
     const int64_t* inst_sub_base;   // NULL in plain mode

@@ -96,18 +96,16 @@ __device__ __forceinline__ void put_pair(const EmitArgs& a, unsigned long long p
 // WRITE = false: count survivors (d > 1 only).
 // ---------------------------------------------------------------------------
 template <bool WRITE, bool FILTER>
-__global__ void __launch_bounds__(EMIT_BLOCK) k_class_a(EmitArgs a, DevStatus* st) {
-    pdl_begin();
-    if (read_error(st)) return;
-    if (a.flag && *(volatile uint32_t*)a.num_flagged == 0u) return;
+__device__ __forceinline__ void class_a_body(const EmitArgs& a, DevStatus* st, uint32_t bid,
+                                             uint32_t nblocks) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    const int64_t warps = (int64_t)gridDim.x * (EMIT_BLOCK / 32);
+    const int64_t warps = (int64_t)nblocks * (EMIT_BLOCK / 32);
     // Subscriptions in id order: neighbouring warps fill neighbouring output
     // segments.  (Visiting them in lower-endpoint order would let neighbouring
     // warps share candidate keys in L1; measured, that only pays for the long
     // ranges of d >= 3, which the tiled join serves by default.)
-    for (int64_t i = ((int64_t)blockIdx.x * EMIT_BLOCK + threadIdx.x) >> 5; i < a.n; i += warps) {
+    for (int64_t i = ((int64_t)bid * EMIT_BLOCK + threadIdx.x) >> 5; i < a.n; i += warps) {
         if (a.flag && !a.flag[i]) continue;
         const uint32_t A = a.rec.s_lo[i].y, B = a.rec.s_hi[i].y;
         if (A > B || B > (uint64_t)a.m) {  // guard against an upstream fault
@@ -146,15 +144,13 @@ __global__ void __launch_bounds__(EMIT_BLOCK) k_class_a(EmitArgs a, DevStatus* s
 // Class (b): one warp per update, SloOrder[A_j .. B_j).
 // ---------------------------------------------------------------------------
 template <bool WRITE, bool FILTER>
-__global__ void __launch_bounds__(EMIT_BLOCK) k_class_b(EmitArgs a, DevStatus* st) {
-    pdl_begin();
-    if (read_error(st)) return;
-    if (a.flag && *(volatile uint32_t*)a.num_flagged == 0u) return;
+__device__ __forceinline__ void class_b_body(const EmitArgs& a, DevStatus* st, uint32_t bid,
+                                             uint32_t nblocks) {
     const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (EMIT_BLOCK / 32);
+    const int64_t warps = (int64_t)nblocks * (EMIT_BLOCK / 32);
     // Updates in id order: neighbouring updates in stream order would target the
     // same subscriptions' counters at once (atomic contention).
-    for (int64_t j = ((int64_t)blockIdx.x * EMIT_BLOCK + threadIdx.x) >> 5; j < a.m; j += warps) {
+    for (int64_t j = ((int64_t)bid * EMIT_BLOCK + threadIdx.x) >> 5; j < a.m; j += warps) {
         const uint32_t A = a.rec.u_lo[j].y, B = a.rec.u_hi[j].y;
         if (A > B || B > (uint64_t)a.n) {  // guard against an upstream fault
             if (lane == 0) raise_error(st, DDM_ERR_INTERNAL, 9);
@@ -184,6 +180,37 @@ __global__ void __launch_bounds__(EMIT_BLOCK) k_class_b(EmitArgs a, DevStatus* s
     }
 }
 
+// Count pass: class (a) stores each subscription's count, class (b) then adds
+// to it, so the two run as consecutive kernels.
+template <bool FILTER>
+__global__ void __launch_bounds__(EMIT_BLOCK) k_class_a_count(EmitArgs a, DevStatus* st) {
+    pdl_begin();
+    if (read_error(st)) return;
+    if (a.flag && *(volatile uint32_t*)a.num_flagged == 0u) return;
+    class_a_body<false, FILTER>(a, st, blockIdx.x, gridDim.x);
+}
+template <bool FILTER>
+__global__ void __launch_bounds__(EMIT_BLOCK) k_class_b_count(EmitArgs a, DevStatus* st) {
+    pdl_begin();
+    if (read_error(st)) return;
+    if (a.flag && *(volatile uint32_t*)a.num_flagged == 0u) return;
+    class_b_body<false, FILTER>(a, st, blockIdx.x, gridDim.x);
+}
+
+// Write pass: both classes in one launch, blocks [0, ga) for class (a) and
+// [ga, ga + gb) for class (b).  Class (a) fills the front of a segment from
+// off[i], class (b) the back from off[i] + cnt_a[i] through its cursors: the
+// roles share no data written in this launch.
+template <bool FILTER>
+__global__ void __launch_bounds__(EMIT_BLOCK) k_class_ab_write(EmitArgs a, DevStatus* st,
+                                                               uint32_t ga, uint32_t gb) {
+    pdl_begin();
+    if (read_error(st)) return;
+    if (a.flag && *(volatile uint32_t*)a.num_flagged == 0u) return;
+    if (blockIdx.x < ga) class_a_body<true, FILTER>(a, st, blockIdx.x, ga);
+    else class_b_body<true, FILTER>(a, st, blockIdx.x - ga, gb);
+}
+
 // One warp per item, grid-stride; at most 8 blocks of 256 threads per SM.
 static unsigned warp_grid(int64_t items) {
     int64_t g = ceil_div((uint64_t)items, EMIT_BLOCK / 32);
@@ -201,8 +228,8 @@ int launch_permute_keys(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
 int launch_filter_count(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
     int launches = 0;
     const unsigned ga = a.flag ? 152u : warp_grid(a.n), gb = a.flag ? 152u : warp_grid(a.m);
-    if (a.n > 0) launch_k(k_class_a<false, true>, ga, EMIT_BLOCK, 0, s, a, st), ++launches;
-    if (a.m > 0) launch_k(k_class_b<false, true>, gb, EMIT_BLOCK, 0, s, a, st), ++launches;
+    if (a.n > 0) launch_k(k_class_a_count<true>, ga, EMIT_BLOCK, 0, s, a, st), ++launches;
+    if (a.m > 0) launch_k(k_class_b_count<true>, gb, EMIT_BLOCK, 0, s, a, st), ++launches;
     return launches;
 }
 
@@ -213,41 +240,39 @@ static unsigned fallback_grid(const EmitArgs& a, int64_t items) {
 }
 
 int launch_emit_ranges(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
-    int launches = 0;
+    if (a.n == 0 && a.m == 0) return 0;
     if (a.d > 1) {
-        const unsigned ga = a.flag ? 152u : warp_grid(a.n), gb = a.flag ? 152u : warp_grid(a.m);
-        if (a.n > 0) launch_k(k_class_a<true, true>, ga, EMIT_BLOCK, 0, s, a, st), ++launches;
-        if (a.m > 0) launch_k(k_class_b<true, true>, gb, EMIT_BLOCK, 0, s, a, st), ++launches;
+        const unsigned ga = a.n > 0 ? (a.flag ? 152u : warp_grid(a.n)) : 0u;
+        const unsigned gb = a.m > 0 ? (a.flag ? 152u : warp_grid(a.m)) : 0u;
+        launch_k(k_class_ab_write<true>, ga + gb, EMIT_BLOCK, 0, s, a, st, ga, gb);
     } else {
-        if (a.n > 0)
-            launch_k(k_class_a<true, false>, fallback_grid(a, a.n), EMIT_BLOCK, 0, s, a, st), ++launches;
-        if (a.m > 0)
-            launch_k(k_class_b<true, false>, fallback_grid(a, a.m), EMIT_BLOCK, 0, s, a, st), ++launches;
+        const unsigned ga = a.n > 0 ? fallback_grid(a, a.n) : 0u;
+        const unsigned gb = a.m > 0 ? fallback_grid(a, a.m) : 0u;
+        launch_k(k_class_ab_write<false>, ga + gb, EMIT_BLOCK, 0, s, a, st, ga, gb);
     }
-    return launches;
+    return 1;
 }
 
 // ---------------------------------------------------------------------------
-// Per-segment sort by update id.  Segments of up to WARP_SORT_MAX pairs are
-// sorted by one warp (bitonic network in shared memory); longer ones are
-// queued for k_segsort_big.
+// Per-segment sort by update id, in one launch.  Blocks [0, gw) sort the
+// segments of up to WARP_SORT_MAX pairs, one warp each (bitonic network in
+// shared memory).  Blocks [gw, gw + gbig) find the longer segments themselves
+// (256 subscriptions per scan step) and sort each with the whole block.  A
+// segment is sorted when flags are off (every segment), when every segment is
+// requested (sort_all), or when its subscription is flagged.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(EMIT_BLOCK) k_segsort_warp(EmitArgs a, DevStatus* st) {
-    pdl_begin();
-    __shared__ uint32_t buf_all[EMIT_BLOCK / 32][WARP_SORT_MAX];
-    if (read_error(st)) return;
-    if (a.flag && !a.sort_all && *(volatile uint32_t*)a.num_flagged == 0u) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t* buf = buf_all[warp];
-    const int64_t warps = (int64_t)gridDim.x * (EMIT_BLOCK / 32);
-    for (int64_t i = ((int64_t)blockIdx.x * EMIT_BLOCK + threadIdx.x) >> 5; i < a.n; i += warps) {
-        if (a.flag && !a.sort_all && !a.flag[i]) continue;
+__device__ __forceinline__ bool segment_wanted(const EmitArgs& a, int64_t i) {
+    return !a.flag || a.sort_all || a.flag[i];
+}
+
+__device__ __forceinline__ void segsort_warp_body(const EmitArgs& a, uint32_t* buf, uint32_t bid,
+                                                  uint32_t nblocks) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)nblocks * (EMIT_BLOCK / 32);
+    for (int64_t i = ((int64_t)bid * EMIT_BLOCK + threadIdx.x) >> 5; i < a.n; i += warps) {
+        if (!segment_wanted(a, i)) continue;
         const uint32_t c = a.cnt[i];
-        if (c < 2) continue;
-        if (c > WARP_SORT_MAX) {
-            if (lane == 0) a.big_list[atomicAdd(&a.big_count[0], 1u)] = (uint32_t)i;
-            continue;
-        }
+        if (c < 2 || c > WARP_SORT_MAX) continue;  // longer ones: the block role
         int32_t* seg = a.pairs + 2 * a.off[i];
         uint32_t P = 2;
         while (P < c) P <<= 1;
@@ -271,114 +296,138 @@ __global__ void __launch_bounds__(EMIT_BLOCK) k_segsort_warp(EmitArgs a, DevStat
     }
 }
 
-// One block per long segment: LSD radix sort of the update-id column, 8 bits
-// per pass, using the segment's own subscription-id column as the ping-pong
-// buffer; the subscription ids are rewritten at the end.  Stable ranking:
-// peers of equal digits found with match_any within a warp, warp-ordered chunks.
-__global__ void __launch_bounds__(BIG_BLOCK) k_segsort_big(EmitArgs a, DevStatus* st) {
-    pdl_begin();
+struct BigSortSmem {
+    uint32_t hist[256];
+    uint32_t bucket[256];
+    uint32_t whist[BIG_BLOCK / 32][256];
+    uint32_t list[BIG_BLOCK];  // long segments found in one scan step
+    uint32_t nlist;
+};
+
+// One long segment, sorted by the whole block: LSD radix sort of the update-id
+// column, 8 bits per pass, using the segment's own subscription-id column as
+// the ping-pong buffer; the subscription ids are rewritten at the end.
+// Stable ranking: peers of equal digits found with match_any within a warp,
+// warp-ordered chunks.
+__device__ void segsort_big_one(const EmitArgs& a, BigSortSmem& sm, uint32_t i) {
     constexpr int WARPS = BIG_BLOCK / 32;
     constexpr int CHUNK = BIG_BLOCK * BIG_ITEMS;
-    __shared__ uint32_t hist[256];
-    __shared__ uint32_t bucket[256];
-    __shared__ uint32_t whist[WARPS][256];
-    __shared__ uint32_t seg_id;
-    if (read_error(st)) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned lt = (1u << lane) - 1u;
     const int passes = (a.id_bits + 7) / 8;
-    for (;;) {
+    const uint32_t c = a.cnt[i];
+    int32_t* seg = a.pairs + 2 * a.off[i];
+    for (int p = 0; p < passes; ++p) {
+        const int src = (p & 1) ? 0 : 1, dst = 1 - src;  // column offsets
+        const int shift = 8 * p;
+        sm.hist[tid] = 0;
         __syncthreads();
-        if (tid == 0) {
-            uint32_t t = atomicAdd(&a.big_count[1], 1u);
-            seg_id = t < a.big_count[0] ? a.big_list[t] : 0xFFFFFFFFu;
+        for (uint32_t k = tid; k < c; k += BIG_BLOCK)
+            atomicAdd(&sm.hist[((uint32_t)seg[2 * k + src] >> shift) & 0xFF], 1u);
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t run = 0;
+            for (int b0 = 0; b0 < 256; b0 += 32) {
+                uint32_t v = sm.hist[b0 + lane], x = v;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= o) x += y;
+                }
+                sm.bucket[b0 + lane] = run + x - v;
+                run += __shfl_sync(0xffffffffu, x, 31);
+            }
         }
         __syncthreads();
-        if (seg_id == 0xFFFFFFFFu) return;
-        const uint32_t i = seg_id;
-        const uint32_t c = a.cnt[i];
-        int32_t* seg = a.pairs + 2 * a.off[i];
-        for (int p = 0; p < passes; ++p) {
-            const int src = (p & 1) ? 0 : 1, dst = 1 - src;  // column offsets
-            const int shift = 8 * p;
-            hist[tid] = 0;
+        for (uint32_t c0 = 0; c0 < c; c0 += CHUNK) {
+            for (int t = tid; t < WARPS * 256; t += BIG_BLOCK) (&sm.whist[0][0])[t] = 0;
             __syncthreads();
-            for (uint32_t k = tid; k < c; k += BIG_BLOCK)
-                atomicAdd(&hist[((uint32_t)seg[2 * k + src] >> shift) & 0xFF], 1u);
+            uint32_t val[BIG_ITEMS], dg[BIG_ITEMS], rk[BIG_ITEMS];
+            const uint32_t wb = c0 + warp * 32 * BIG_ITEMS;
+#pragma unroll
+            for (int it = 0; it < BIG_ITEMS; ++it) {
+                const uint32_t k = wb + it * 32 + lane;
+                val[it] = k < c ? (uint32_t)seg[2 * k + src] : 0xFFFFFFFFu;
+                dg[it] = (val[it] >> shift) & 0xFF;
+                const unsigned peers = __match_any_sync(0xffffffffu, dg[it]);
+                const uint32_t cc = sm.whist[warp][dg[it]];
+                __syncwarp();
+                if (lane == __ffs(peers) - 1) sm.whist[warp][dg[it]] = cc + __popc(peers);
+                __syncwarp();
+                rk[it] = cc + __popc(peers & lt);
+            }
             __syncthreads();
-            if (warp == 0) {
+            {   // per digit: exclusive prefix over warps, chunk total
                 uint32_t run = 0;
-                for (int b0 = 0; b0 < 256; b0 += 32) {
-                    uint32_t v = hist[b0 + lane], x = v;
 #pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-                        if (lane >= o) x += y;
-                    }
-                    bucket[b0 + lane] = run + x - v;
-                    run += __shfl_sync(0xffffffffu, x, 31);
+                for (int w = 0; w < WARPS; ++w) {
+                    uint32_t x = sm.whist[w][tid];
+                    sm.whist[w][tid] = run;
+                    run += x;
+                }
+                sm.hist[tid] = run;  // chunk count of digit tid (tail items sit in digit 255 last)
+            }
+            __syncthreads();
+#pragma unroll
+            for (int it = 0; it < BIG_ITEMS; ++it) {
+                const uint32_t k = wb + it * 32 + lane;
+                if (k < c) {
+                    const uint32_t pos = sm.bucket[dg[it]] + sm.whist[warp][dg[it]] + rk[it];
+                    seg[2 * pos + dst] = (int32_t)val[it];
                 }
             }
             __syncthreads();
-            for (uint32_t c0 = 0; c0 < c; c0 += CHUNK) {
-                for (int t = tid; t < WARPS * 256; t += BIG_BLOCK) (&whist[0][0])[t] = 0;
-                __syncthreads();
-                uint32_t val[BIG_ITEMS], dg[BIG_ITEMS], rk[BIG_ITEMS];
-                const uint32_t wb = c0 + warp * 32 * BIG_ITEMS;
-#pragma unroll
-                for (int it = 0; it < BIG_ITEMS; ++it) {
-                    const uint32_t k = wb + it * 32 + lane;
-                    val[it] = k < c ? (uint32_t)seg[2 * k + src] : 0xFFFFFFFFu;
-                    dg[it] = (val[it] >> shift) & 0xFF;
-                    const unsigned peers = __match_any_sync(0xffffffffu, dg[it]);
-                    const uint32_t cc = whist[warp][dg[it]];
-                    __syncwarp();
-                    if (lane == __ffs(peers) - 1) whist[warp][dg[it]] = cc + __popc(peers);
-                    __syncwarp();
-                    rk[it] = cc + __popc(peers & lt);
-                }
-                __syncthreads();
-                {   // per digit: exclusive prefix over warps, chunk total
-                    uint32_t run = 0;
-#pragma unroll
-                    for (int w = 0; w < WARPS; ++w) {
-                        uint32_t x = whist[w][tid];
-                        whist[w][tid] = run;
-                        run += x;
-                    }
-                    hist[tid] = run;  // chunk count of digit tid (tail items sit in digit 255 last)
-                }
-                __syncthreads();
-#pragma unroll
-                for (int it = 0; it < BIG_ITEMS; ++it) {
-                    const uint32_t k = wb + it * 32 + lane;
-                    if (k < c) {
-                        const uint32_t pos = bucket[dg[it]] + whist[warp][dg[it]] + rk[it];
-                        seg[2 * pos + dst] = (int32_t)val[it];
-                    }
-                }
-                __syncthreads();
-                bucket[tid] += hist[tid];
-                __syncthreads();
-            }
+            sm.bucket[tid] += sm.hist[tid];
             __syncthreads();
         }
-        // Result is in column (passes odd ? 0 : 1); move it to column 1 and
-        // restore the subscription ids in column 0.
-        int32_t out_i = (int32_t)i;
-        if (a.inst_sub_base) out_i = (int32_t)(i - a.inst_sub_base[inst_of(a.inst_sub_base, a.num_inst, i)]);
-        for (uint32_t k = tid; k < c; k += BIG_BLOCK) {
-            if (passes & 1) seg[2 * k + 1] = seg[2 * k];
-            seg[2 * k] = out_i;
-        }
+        __syncthreads();
+    }
+    // Result is in column (passes odd ? 0 : 1); move it to column 1 and
+    // restore the subscription ids in column 0.
+    int32_t out_i = (int32_t)i;
+    if (a.inst_sub_base) out_i = (int32_t)(i - a.inst_sub_base[inst_of(a.inst_sub_base, a.num_inst, i)]);
+    for (uint32_t k = tid; k < c; k += BIG_BLOCK) {
+        if (passes & 1) seg[2 * k + 1] = seg[2 * k];
+        seg[2 * k] = out_i;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(EMIT_BLOCK) k_segsort(EmitArgs a, DevStatus* st, uint32_t gw,
+                                                        uint32_t gbig) {
+    static_assert(EMIT_BLOCK == BIG_BLOCK, "one block size for both roles");
+    pdl_begin();
+    __shared__ __align__(16) unsigned char smem[sizeof(BigSortSmem) > 4 * WARP_SORT_MAX *
+                                                                         (EMIT_BLOCK / 32)
+                                                    ? sizeof(BigSortSmem)
+                                                    : 4 * WARP_SORT_MAX * (EMIT_BLOCK / 32)];
+    if (read_error(st)) return;
+    if (a.flag && !a.sort_all && *(volatile uint32_t*)a.num_flagged == 0u) return;
+    if (blockIdx.x < gw) {
+        uint32_t* buf = reinterpret_cast<uint32_t*>(smem) + (threadIdx.x >> 5) * WARP_SORT_MAX;
+        segsort_warp_body(a, buf, blockIdx.x, gw);
+        return;
+    }
+    BigSortSmem& sm = *reinterpret_cast<BigSortSmem*>(smem);
+    const uint32_t bid = blockIdx.x - gw;
+    for (int64_t base = (int64_t)bid * BIG_BLOCK; base < a.n; base += (int64_t)gbig * BIG_BLOCK) {
+        if (threadIdx.x == 0) sm.nlist = 0;
+        __syncthreads();
+        const int64_t i = base + threadIdx.x;
+        if (i < a.n && segment_wanted(a, i) && a.cnt[i] > WARP_SORT_MAX)
+            sm.list[atomicAdd(&sm.nlist, 1u)] = (uint32_t)i;
+        __syncthreads();
+        const uint32_t nl = sm.nlist;
+        for (uint32_t q = 0; q < nl; ++q) segsort_big_one(a, sm, sm.list[q]);
+        __syncthreads();
     }
 }
 
 int launch_segment_sort(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
     if (a.n == 0) return 0;
-    launch_k(k_segsort_warp, fallback_grid(a, a.n), EMIT_BLOCK, 0, s, a, st);
-    launch_k(k_segsort_big, 152, BIG_BLOCK, 0, s, a, st);
-    return 2;
+    const unsigned gw = fallback_grid(a, a.n), gbig = 152;
+    launch_k(k_segsort, gw + gbig, EMIT_BLOCK, 0, s, a, st, gw, gbig);
+    return 1;
 }
 
 }  // namespace ddm
