@@ -149,6 +149,8 @@ __global__ void __launch_bounds__(DELTA_BLOCK) k_delta(DeltaArgs a, DevStatus* s
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t warps = (int64_t)gridDim.x * DELTA_WARPS;
     for (int64_t i = (int64_t)blockIdx.x * DELTA_WARPS + warp; i < a.n; i += warps) {
+        if (WRITE && a.add_off[i + 1] == a.add_off[i] && a.rem_off[i + 1] == a.rem_off[i])
+            continue;  // the count pass found nothing to report for this subscription
         const uint64_t pa0 = a.prev_off[i], pa1 = a.prev_off[i + 1];
         const uint64_t cb0 = a.cur_off[i], cb1 = a.cur_off[i + 1];
         if (pa1 < pa0 || cb1 < cb0) {

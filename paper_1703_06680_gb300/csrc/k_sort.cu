@@ -12,6 +12,8 @@
 // GPU an LSD radix sort on order-preserving integer keys is the natural
 // replacement.  Stability of the LSD passes keeps the [lowers | uppers]
 // layout order among equal coordinates.
+#include <atomic>
+
 #include "sort.cuh"
 #include "sweep.cuh"
 
@@ -290,13 +292,13 @@ int launch_radix_sort(KeyT* keys0, uint32_t* vals0, KeyT* keys1, uint32_t* vals1
     const uint64_t cells = tiles * RADIX;
     const int smem = (int)sizeof(DownSmem<KeyT, ITEMS>);
     // The dynamic shared-memory opt-in is per device; set it once for each.
-    static unsigned long long attr_set = 0;
+    static std::atomic<unsigned long long> attr_set{0};  // server threads launch concurrently
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64 || !(attr_set & (1ull << dev))) {
+    if (dev < 0 || dev >= 64 || !(attr_set.load() & (1ull << dev))) {
         cudaFuncSetAttribute(k_downsweep<KeyT, ITEMS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              smem);
-        if (dev >= 0 && dev < 64) attr_set |= 1ull << dev;
+        if (dev >= 0 && dev < 64) attr_set.fetch_or(1ull << dev);
     }
     const bool fused = sc.grp && tiles <= SORT_FUSED_MAX_TILES;
     int launches = 0;
