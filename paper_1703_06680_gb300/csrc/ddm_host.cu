@@ -400,27 +400,26 @@ int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
                                 pl.n, pl.m, (uint32_t*)pl.keys0, pl.vals0, c->dstat, s);
     }
     mark(c, 1);
-    if (batch) {
-        L += launch_radix_sort<unsigned long long>(
-            (unsigned long long*)pl.keys0, pl.vals0, (unsigned long long*)pl.keys1, pl.vals1, pl.E,
-            pl.passes, pl.sort, true, c->dstat, s);
-    } else {
-        L += launch_radix_sort<uint32_t>((uint32_t*)pl.keys0, pl.vals0, (uint32_t*)pl.keys1,
-                                         pl.vals1, pl.E, pl.passes, pl.sort, true, c->dstat, s);
-    }
-    mark(c, 2);
     // The sweep scan writes one 16-byte rank record per endpoint at a random
     // id.  Into sectors absent from L2 such partial writes cost a DRAM read
     // each; clearing the record tables first (full-sector writes) leaves them
-    // resident in L2.  Measured: scan 57 -> 44 us including the clear, for
-    // E = 2e6.  (Overlapping the clear with the sort on a second stream was
-    // no faster: it slows key build and sort by as much as it saves.)
-    // (The tables start 256-byte aligned and the next buffer starts 256-byte
-    // aligned too, so rounding up to 16-byte words stays inside them.)
-    {
-        const size_t rec_bytes = (size_t)((char*)(rec.upd_order + pl.m) - (char*)rec.s_lo);
-        if (pl.E > 0) L += launch_clear16(rec.s_lo, (rec_bytes + 15) / 16, s);
+    // resident in L2 (scan 57 -> 44 us, clear included, for E = 2e6).  The
+    // blocks of the sort's last pass do the clear while their tiles load.
+    // (Overlapping it with the sort on a second stream was no faster.)  The
+    // tables start 256-byte aligned and the next buffer starts 256-byte
+    // aligned too, so rounding up to 16-byte words stays inside them.
+    const size_t rec_words =
+        ((size_t)((char*)(rec.upd_order + pl.m) - (char*)rec.s_lo) + 15) / 16;
+    if (batch) {
+        L += launch_radix_sort<unsigned long long>(
+            (unsigned long long*)pl.keys0, pl.vals0, (unsigned long long*)pl.keys1, pl.vals1, pl.E,
+            pl.passes, pl.sort, true, c->dstat, s, rec.s_lo, rec_words);
+    } else {
+        L += launch_radix_sort<uint32_t>((uint32_t*)pl.keys0, pl.vals0, (uint32_t*)pl.keys1,
+                                         pl.vals1, pl.E, pl.passes, pl.sort, true, c->dstat, s,
+                                         rec.s_lo, rec_words);
     }
+    mark(c, 2);
     L += launch_sweep_scan(vals_sorted, pl.E, pl.n, pl.m, rec, pl.scan_status, c->dstat, s);
     mark(c, 3);
     // d = 1: the counts are formed inside the offsets scan (one kernel for a4

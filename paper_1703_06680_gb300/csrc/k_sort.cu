@@ -163,7 +163,8 @@ __global__ void __launch_bounds__(SORT_BLOCK, 3)
 k_downsweep(const KeyT* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
             KeyT* __restrict__ keys_out, uint32_t* __restrict__ vals_out, uint32_t E, int shift,
             const unsigned long long* __restrict__ base, const uint32_t* __restrict__ tile_hist,
-            const uint32_t* __restrict__ grp, uint32_t tiles, int write_keys, DevStatus* st) {
+            const uint32_t* __restrict__ grp, uint32_t tiles, int write_keys,
+            uint4* __restrict__ clr, uint64_t clr_words, DevStatus* st) {
     pdl_begin();
     using Smem = DownSmem<KeyT, ITEMS>;
     constexpr int TILE = Smem::TILE;
@@ -197,12 +198,18 @@ k_downsweep(const KeyT* __restrict__ keys_in, const uint32_t* __restrict__ vals_
         sm.gbase[tid] = (uint32_t)base[(uint64_t)tid * tiles + tile];
     }
     __syncthreads();
+    if (full && tid == 0) {
+        mbar_expect_tx(&sm.bar, TILE * (sizeof(KeyT) + sizeof(uint32_t)));
+        tma_load_1d(sm.keys, keys_in + tbase, TILE * sizeof(KeyT), &sm.bar);
+        tma_load_1d(sm.vals_raw, vals_in + tbase, TILE * sizeof(uint32_t), &sm.bar);
+    }
+    if (clr) {  // this block's share of a zero fill, while the tile is in flight
+        const uint64_t share = (clr_words + gridDim.x - 1) / gridDim.x;
+        const uint64_t c0 = (uint64_t)blockIdx.x * share;
+        const uint64_t c1 = c0 + share < clr_words ? c0 + share : clr_words;
+        for (uint64_t i = c0 + tid; i < c1; i += SORT_BLOCK) clr[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
     if (full) {
-        if (tid == 0) {
-            mbar_expect_tx(&sm.bar, TILE * (sizeof(KeyT) + sizeof(uint32_t)));
-            tma_load_1d(sm.keys, keys_in + tbase, TILE * sizeof(KeyT), &sm.bar);
-            tma_load_1d(sm.vals_raw, vals_in + tbase, TILE * sizeof(uint32_t), &sm.bar);
-        }
         mbar_wait_bounded(&sm.bar, 0, st, 14);
     } else {
         for (int i = tid; i < TILE; i += SORT_BLOCK) {
@@ -283,7 +290,7 @@ k_downsweep(const KeyT* __restrict__ keys_in, const uint32_t* __restrict__ vals_
 template <typename KeyT>
 int launch_radix_sort(KeyT* keys0, uint32_t* vals0, KeyT* keys1, uint32_t* vals1, uint64_t E,
                       int passes, const SortScratch& sc, bool skip_last_keys, DevStatus* st,
-                      cudaStream_t s) {
+                      cudaStream_t s, void* clear_ptr, uint64_t clear_words) {
     if (E == 0) return 0;
     constexpr int ITEMS = sort_items<KeyT>();
     const uint64_t tiles = sort_tiles<KeyT>(E);
@@ -311,19 +318,23 @@ int launch_radix_sort(KeyT* keys0, uint32_t* vals0, KeyT* keys1, uint32_t* vals1
         if (!fused)
             launches += launch_offsets(sc.tile_hist, (int64_t)cells, sc.offs, ~0ull, sc.total,
                                        sc.status + (size_t)p * sort_status_stride(E), st, s);
+        const bool last = p == passes - 1;
         launch_k(k_downsweep<KeyT, ITEMS>, (unsigned)tiles, SORT_BLOCK, smem, s, kb[p & 1],
                  vb[p & 1], kb[(p + 1) & 1], vb[(p + 1) & 1], (uint32_t)E, 8 * p, sc.offs,
-                 sc.tile_hist, grp, (uint32_t)tiles, write_keys, st);
+                 sc.tile_hist, grp, (uint32_t)tiles, write_keys,
+                 last ? static_cast<uint4*>(clear_ptr) : static_cast<uint4*>(nullptr),
+                 last ? clear_words : 0ull, st);
         ++launches;
     }
     return launches;
 }
 
 template int launch_radix_sort<uint32_t>(uint32_t*, uint32_t*, uint32_t*, uint32_t*, uint64_t,
-                                         int, const SortScratch&, bool, DevStatus*, cudaStream_t);
+                                         int, const SortScratch&, bool, DevStatus*, cudaStream_t,
+                                         void*, uint64_t);
 template int launch_radix_sort<unsigned long long>(unsigned long long*, uint32_t*,
                                                    unsigned long long*, uint32_t*, uint64_t, int,
                                                    const SortScratch&, bool, DevStatus*,
-                                                   cudaStream_t);
+                                                   cudaStream_t, void*, uint64_t);
 
 }  // namespace ddm

@@ -151,24 +151,6 @@ int launch_sweep_scan(const uint32_t* vals, uint64_t E, int64_t n, int64_t m, co
     return 1;
 }
 
-// Zero fill of `words` 16-byte words, used to make the record tables resident
-// in L2 before the scan's scattered writes (a kernel rather than a memset, so
-// that it takes part in programmatic dependent launch).
-__global__ void k_clear16(uint4* __restrict__ p, uint64_t words) {
-    pdl_begin();
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words;
-         i += (uint64_t)gridDim.x * blockDim.x)
-        p[i] = make_uint4(0u, 0u, 0u, 0u);
-}
-
-int launch_clear16(void* p, uint64_t words, cudaStream_t s) {
-    if (words == 0) return 0;
-    const uint64_t g = ceil_div(words, 256ull * 4);
-    launch_k(k_clear16, (unsigned)(g < 1 ? 1 : (g > 152 * 8 ? 152 * 8 : g)), 256, 0, s,
-             static_cast<uint4*>(p), words);
-    return 1;
-}
-
 // ---------------------------------------------------------------------------
 // a4
 // ---------------------------------------------------------------------------

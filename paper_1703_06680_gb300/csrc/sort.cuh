@@ -71,9 +71,12 @@ int launch_keybuild_d0(const float* sub_lo, const float* sub_hi, const float* up
 // Stable LSD radix sort of E (key, val) pairs by the low `passes` * 8 key bits.
 // The result ends in (keys[r], vals[r]) with r = passes % 2 (buffer 0 = the
 // input).  When `skip_last_keys` is set the last pass writes only values.
+// clear_ptr/clear_words (16-byte words, may be NULL/0): a buffer that the last
+// pass's blocks zero while their tiles load (the rank-record tables of the
+// sweep scan that follows).
 template <typename KeyT>
 int launch_radix_sort(KeyT* keys0, uint32_t* vals0, KeyT* keys1, uint32_t* vals1, uint64_t E,
                       int passes, const SortScratch& sc, bool skip_last_keys, DevStatus* st,
-                      cudaStream_t s);
+                      cudaStream_t s, void* clear_ptr = nullptr, uint64_t clear_words = 0);
 
 }  // namespace ddm

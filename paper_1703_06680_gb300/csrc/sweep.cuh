@@ -42,9 +42,6 @@ struct Records {
 int launch_sweep_scan(const uint32_t* vals, uint64_t E, int64_t n, int64_t m, const Records& rec,
                        unsigned long long* status, DevStatus* st, cudaStream_t s);
 
-// Zeroes `words` 16-byte words at p (16-byte aligned).
-int launch_clear16(void* p, uint64_t words, cudaStream_t s);
-
 // cnt[i] = B_i - C_i; optional upd_cnt[j] = B_j - C_j.
 int launch_rank_count(const Records& rec, int64_t n, int64_t m, uint32_t* cnt,
                        uint32_t* upd_cnt, DevStatus* st, cudaStream_t s);
