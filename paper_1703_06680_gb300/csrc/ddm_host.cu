@@ -791,6 +791,15 @@ struct ddm_session {
     bool have_ref = false;    // a reference list exists (else: empty)
     bool pending = false;     // new list computed, report not yet delivered
     uint64_t K_ref = 0, K_new = 0;
+    // The count phase as a CUDA graph: a session's shapes, coordinates and
+    // workspace do not change, so after one direct run the kernels of
+    // ddm_session_count are captured once and then replayed with a single
+    // launch (host launch overhead dominates small requests).
+    cudaGraphExec_t prefix_exec = nullptr;
+    const char* prefix_ws = nullptr;  // workspace the graph was captured against
+    uint64_t prefix_launches = 0;     // kernels in the graph
+    int prefix_runs = 0;              // direct runs so far
+    bool no_graph = false;            // capture failed once: stay direct
 };
 
 namespace {
@@ -863,6 +872,7 @@ int ddm_session_destroy(ddm_session* s) {
             if (s->loff[k]) cudaFree(s->loff[k]);
         }
         if (s->dwork) cudaFree(s->dwork);
+        if (s->prefix_exec) cudaGraphExecDestroy(s->prefix_exec);
         ddm_destroy(s->ctx);
     }
     delete s;
@@ -897,6 +907,46 @@ int ddm_session_drift(ddm_session* s, void* stream, uint64_t seed, uint64_t step
     return DDM_OK;
 }
 
+// The count phase of a session on c->stream: replayed from its graph when one
+// exists, captured after the first direct run, direct otherwise (legacy default
+// stream, profiling, or a capture that failed).
+static int session_prefix(ddm_session* s) {
+    ddm_ctx* c = s->ctx;
+    const Job job = session_job(s);
+    const bool graphable = c->stream != nullptr && !c->prof && !s->no_graph;
+    if (s->prefix_exec && (!graphable || s->prefix_ws != c->ws)) {
+        cudaGraphExecDestroy(s->prefix_exec);
+        s->prefix_exec = nullptr;
+    }
+    if (graphable && !s->prefix_exec && s->prefix_runs >= 1) {
+        cudaGraph_t graph = nullptr;
+        const uint64_t l0 = c->stats.launches, calls0 = c->stats.calls;
+        bool ok = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        int rc = ok ? enqueue(c, job, Mode::Match, nullptr, 0, nullptr, Phase::Prefix) : DDM_OK;
+        ok = ok && cudaStreamEndCapture(c->stream, &graph) == cudaSuccess && rc == DDM_OK && graph;
+        if (ok) ok = cudaGraphInstantiate(&s->prefix_exec, graph, 0) == cudaSuccess;
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        if (ok) {
+            s->prefix_ws = c->ws;
+            s->prefix_launches = c->stats.launches - l0;
+        } else {
+            s->prefix_exec = nullptr;
+            s->no_graph = true;
+        }
+        c->stats.launches = l0;  // counted when the graph runs
+        c->stats.calls = calls0;
+    }
+    if (s->prefix_exec) {
+        CK(cudaGraphLaunch(s->prefix_exec, c->stream));
+        c->stats.launches += s->prefix_launches;
+        c->stats.calls++;
+        return DDM_OK;
+    }
+    s->prefix_runs++;
+    return enqueue(c, job, Mode::Match, nullptr, 0, nullptr, Phase::Prefix);
+}
+
 int ddm_session_count(ddm_session* s, void* stream, uint64_t* K_out) {
     if (!s) return DDM_ERR_INVALID;
     ddm_ctx* c = s->ctx;
@@ -904,7 +954,7 @@ int ddm_session_count(ddm_session* s, void* stream, uint64_t* K_out) {
     c->stream = reinterpret_cast<cudaStream_t>(stream);
     s->counted = false;
     s->pending = false;  // a new timestep replaces an undelivered change report
-    int rc = enqueue(c, session_job(s), Mode::Match, nullptr, 0, nullptr, Phase::Prefix);
+    int rc = session_prefix(s);
     if (rc) return rc;
     uint64_t K = 0;
     rc = finish(c, &K);
