@@ -101,7 +101,8 @@ int ddm_count(ddm_ctx *ctx, const ddm_regions *regions, uint64_t *K_out);
  * All intersecting pairs (Section 3), as K interleaved int32 pairs
  * pairs[2k] = i (subscription id), pairs[2k+1] = j (update id), sorted
  * lexicographically by (i, j); each pair appears once.  `pairs` is DEVICE
- * memory for 2 * cap int32 values.  If K > cap nothing is written, *K_out = K
+ * memory for 2 * cap int32 values, 8-byte aligned (else DDM_ERR_INVALID).
+ * If K > cap nothing is written, *K_out = K
  * and DDM_ERR_CAPACITY is returned, so the caller can retry with a larger
  * buffer.  Synchronous, like ddm_count.
  */
@@ -144,7 +145,7 @@ int ddm_count_noalloc(const ddm_regions *regions, void *cuda_stream, uint64_t *K
 /*
  * Tunables of a context (read by the autotuner; defaults are used otherwise).
  *   DDM_PARAM_WIN_SHIFT   log2 of the window length of the d = 1 emission, in
- *                         sorted-stream positions: 6 .. 9 (default 8).
+ *                         sorted-stream positions: 6 .. 10 (default 10).
  * Returns DDM_ERR_INVALID for an unknown parameter or a value out of range.
  *   DDM_PARAM_ND_PATH     strategy for d > 1: 0 = automatic (default: the tiled
  *                         join with dimension-1 pruning, measured faster on

@@ -16,7 +16,7 @@ import statistics
 from ._lib import PARAM_ND_PATH, PARAM_SWEEP_DIM, PARAM_WIN_SHIFT
 
 # Candidate values per tunable, and which dimensionalities a tunable affects.
-CANDIDATES = {PARAM_WIN_SHIFT: (7, 8, 9), PARAM_ND_PATH: (1, 2), PARAM_SWEEP_DIM: (0, 1)}
+CANDIDATES = {PARAM_WIN_SHIFT: (8, 9, 10), PARAM_ND_PATH: (1, 2), PARAM_SWEEP_DIM: (0, 1)}
 NAMES = {PARAM_WIN_SHIFT: "win_shift", PARAM_ND_PATH: "nd_path", PARAM_SWEEP_DIM: "sweep_dim"}
 APPLIES = {PARAM_WIN_SHIFT: lambda d: d == 1, PARAM_ND_PATH: lambda d: d > 1,
            PARAM_SWEEP_DIM: lambda d: d > 1}

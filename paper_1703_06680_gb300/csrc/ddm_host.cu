@@ -41,7 +41,7 @@ struct ddm_ctx {
     ddm_stats stats{};
     int prof = 0;  // 0 off, 1 every stage boundary, 2 + k only around stage k
     unsigned long long* last_inst_off = nullptr;  // device, batched calls
-    int win_shift = 8;                            // DDM_PARAM_WIN_SHIFT
+    int win_shift = 10;                           // DDM_PARAM_WIN_SHIFT
     int nd_path = 0;                              // DDM_PARAM_ND_PATH
     bool pdl = true;                              // DDM_PARAM_PDL
     int sweep_dim = 0;                            // DDM_PARAM_SWEEP_DIM
@@ -185,6 +185,8 @@ struct Plan {
     unsigned long long* lw_off;
     uint4* lw;
     uint4* urank;
+    uint4* srank;
+    unsigned long long* soff;
     unsigned long long lw_cap;
     uint8_t* flag;
     // the rest
@@ -202,7 +204,7 @@ struct Plan {
     size_t total;
 
     void layout(char* base, int d_, int64_t n_, int64_t m_, Mode mode, int num_inst_,
-                int win_shift_ = 8, int nd_path = 0) {
+                int win_shift_ = 10, int nd_path = 0) {
         d = d_; n = n_; m = m_; E = 2 * (n + m); num_inst = num_inst_;
         const bool batch = num_inst > 0;
         passes = batch ? (int)ceil_div(32 + ceil_log2(num_inst), RADIX_BITS) : 4;
@@ -238,6 +240,8 @@ struct Plan {
         else lw_cap = 0;
         lw = cv.take<uint4>(lw_cap);
         urank = cv.take<uint4>(lists ? m : 0);
+        srank = cv.take<uint4>(window ? n : 0);
+        soff = cv.take<unsigned long long>(window ? n : 0);
         flag = cv.take<uint8_t>(lists ? n : 0);
         sort.tile_hist = cv.take<uint32_t>(stiles * RADIX);
         sort.offs = cv.take<unsigned long long>(stiles * RADIX + 1);
@@ -293,6 +297,9 @@ int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
     int rc = ensure(c, &c->ws, &c->ws_size, pl.total);
     if (rc) return rc;
     pl.layout(c->ws, job.d, job.n, job.m, mode, job.num_inst, c->win_shift, c->nd_path);
+    // Pairs are stored as 8-byte (i, j) units.
+    if (pairs && (reinterpret_cast<uintptr_t>(pairs) & 7u))
+        return fail(c, DDM_ERR_INVALID, "pairs must be 8-byte aligned");
     cudaStream_t s = c->stream;
     PdlScope pdl_scope(c->pdl);
     const bool batch = job.num_inst > 0;
@@ -387,6 +394,8 @@ int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
         a.lw_fill = pl.lw_fill;
         a.lw = pl.lw;
         a.urank = pl.urank;
+        a.srank = pl.window ? pl.srank : nullptr;
+        a.soff = pl.soff;
         a.lw_cap = pl.lw_cap;
     }
     a.vals = vals_sorted;
@@ -575,7 +584,7 @@ int ddm_set_profiling(ddm_ctx* c, int enable) {
 int ddm_set_param(ddm_ctx* c, int param, int64_t value) {
     if (!c) return DDM_ERR_INVALID;
     if (param == DDM_PARAM_WIN_SHIFT) {
-        if (value < 6 || value > 9) return fail(c, DDM_ERR_INVALID, "window shift must be 6..9");
+        if (value < 6 || value > 10) return fail(c, DDM_ERR_INVALID, "window shift must be 6..10");
         c->win_shift = (int)value;
         return DDM_OK;
     }

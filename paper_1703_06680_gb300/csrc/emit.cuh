@@ -49,6 +49,8 @@ struct EmitArgs {
     uint4* lw;                      // list storage {id, pos(U.hi), rank, 0}, lw_cap entries
     uint32_t lcap;                  // longest boundary list a window may use
     uint4* urank;                   // {id, pos(lo), pos(hi), 0} by lower-endpoint rank, m
+    uint4* srank;                   // window path: {id, pos(lo), pos(hi), cnt} by rank, n (or NULL)
+    unsigned long long* soff;       // window path: segment offset by rank, n
     unsigned long long lw_cap;
     const uint32_t* vals;           // sorted endpoint stream (payloads)
     bool sort_all;                  // segment sort every subscription, not only flagged ones

@@ -18,20 +18,36 @@
 // pos(S.lo) < pos(U.hi) (the closed-interval test of Algorithm 1 in stream
 // positions) and writes them in that order.
 //
+// A warp takes 32 consecutive subscriptions (by lower endpoint) and first
+// narrows W to the members that can meet any of them; it then filters that
+// list for two subscriptions at a time, testing 32 entries per step and
+// compacting the kept ones by ballot into each output segment.
+//
 // Subscriptions spanning more than LONG_SPAN positions, and windows whose
 // boundary list exceeds LCAP entries (or the list storage), are flagged and
 // served by the range path (k_emit.cu) followed by the per-segment sort.
+#include <atomic>
+
 #include "emit.cuh"
 
 namespace ddm {
 
-constexpr int WIN_BLOCK = 256;
+constexpr int WIN_BLOCK = 256;        // eight warps per window
+constexpr int WIN_WARPS = WIN_BLOCK / 32;
 // The longest boundary list a window may use is a.lcap (1024 on this path).
 constexpr uint32_t WCAP = 1024;       // candidates per window
 constexpr uint32_t LONG_SPAN = 512;   // positions; longer subscriptions use the range path
-constexpr int MAX_WIN_SHIFT = 9;      // windows of at most 512 positions
+constexpr int MAX_WIN_SHIFT = 10;     // windows of at most 1024 positions
 constexpr int NBUCKET = 256;          // buckets of the per-window id sort
-constexpr int WITEMS = WCAP / WIN_BLOCK;
+
+// Dynamic shared memory of k_emit_window.  The per-warp candidate lists
+// overlay the raw candidate array of the set-up.
+constexpr size_t WSM_RAW = (size_t)WCAP * 16;
+constexpr size_t WSM_WIDX = (size_t)WIN_WARPS * (WCAP + 32) * 2;
+constexpr size_t WSM_A = ((WSM_RAW > WSM_WIDX ? WSM_RAW : WSM_WIDX) + 15) & ~(size_t)15;
+constexpr size_t WSM_CAND = (size_t)(WCAP + 1) * 16;  // + one entry that no subscription keeps
+constexpr size_t WSM_BYB = (size_t)WCAP * 4;
+constexpr size_t WSM_TOTAL = WSM_A + WSM_CAND + WSM_BYB;
 
 __device__ __forceinline__ bool list_fits(const EmitArgs& a, uint32_t w, uint32_t s) {
     return s <= a.lcap && a.lw_off[w] + s <= a.lw_cap;
@@ -39,7 +55,8 @@ __device__ __forceinline__ bool list_fits(const EmitArgs& a, uint32_t w, uint32_
 
 // One pass over the updates in lower-endpoint order (rank r, id = upd_order[r]):
 //  - the rank table urank[r] = {id, pos(lo), pos(hi)}, so that windows read
-//    their candidates contiguously;
+//    their candidates contiguously (and, on the window path, the same for the
+//    subscriptions: srank[r] = {id, pos(lo), pos(hi), cnt}, soff[r] = off);
 //  - the boundary lists: U contributes {id, pos(U.hi), rank} to every boundary w*T
 //    with pos(U.lo) < w*T <= pos(U.hi) (the paper's UpdSet at that boundary).
 // The lanes of a warp hold consecutive ranks, whose lower endpoints are close
@@ -47,13 +64,26 @@ __device__ __forceinline__ bool list_fits(const EmitArgs& a, uint32_t w, uint32_
 // union of its lanes' boundary ranges and reserves the slots of all lanes
 // crossing boundary w with one atomic (order inside a list is irrelevant: the
 // window kernel sorts its candidates by id).
-__global__ void k_tile_active(EmitArgs a, DevStatus* st) {
+// Blocks [0, gu) take the updates, blocks [gu, gridDim.x) the subscriptions.
+__global__ void k_tile_active(EmitArgs a, DevStatus* st, unsigned gu) {
     pdl_begin();
     if (read_error(st)) return;
+    if (blockIdx.x >= gu) {
+        // Window path: the subscriptions in lower-endpoint order with what the
+        // emission needs of each, so that a window reads its own contiguously.
+        const int64_t sstride = (int64_t)(gridDim.x - gu) * blockDim.x;
+        for (int64_t r = (int64_t)(blockIdx.x - gu) * blockDim.x + threadIdx.x; r < a.n;
+             r += sstride) {
+            const uint32_t i = a.rec.sub_order[r];
+            a.srank[r] = make_uint4(i, a.rec.s_lo[i].x, a.rec.s_hi[i].x, a.cnt[i]);
+            a.soff[r] = a.off[i];
+        }
+        return;
+    }
     const int S = a.win_shift;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t stride = (int64_t)gu * blockDim.x;
     for (int64_t r0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); r0 < a.m;
          r0 += stride) {
         const int64_t r = r0 + lane;
@@ -90,85 +120,179 @@ __global__ void k_tile_active(EmitArgs a, DevStatus* st) {
     }
 }
 
-__global__ void __launch_bounds__(WIN_BLOCK) k_emit_window(EmitArgs a, DevStatus* st) {
+// Candidate read by 32-bit shared-window address.  The candidate array does
+// not change while the filter runs, so the read is declared free of side
+// effects and the compiler may overlap the reads of successive steps.
+__device__ __forceinline__ uint4 lds_cand(uint32_t addr) {
+    uint4 v;
+    asm("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr));
+    return v;
+}
+
+// One subscription of the filter: its bounds, output id, id base and next
+// free slot of its segment.
+struct FilterSub {
+    uint32_t pl, ph;
+    int32_t i;
+    uint32_t jb;
+    int2* out;
+};
+
+// Keeps the list entries (candidate indices; pos(lo) < ph and pl < pos(hi))
+// of two subscriptions, 32 entries per step.  The caller guarantees room for
+// a whole list after each segment start.
+__device__ __forceinline__ void filter_pair(const uint16_t* list, uint32_t cand_s, uint32_t n32,
+                                            FilterSub& A, FilterSub& B, int lane) {
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll 2
+    for (uint32_t kk = lane; kk < n32; kk += 32) {
+        const uint4 c = lds_cand(cand_s + 16u * list[kk]);
+        const bool a = c.y < A.ph && c.z > A.pl;
+        const bool b = c.y < B.ph && c.z > B.pl;
+        const unsigned ma = __ballot_sync(0xffffffffu, a);
+        const unsigned mb = __ballot_sync(0xffffffffu, b);
+        if (a) __stcs(&A.out[__popc(ma & lt)], make_int2(A.i, (int32_t)(c.x - A.jb)));
+        if (b) __stcs(&B.out[__popc(mb & lt)], make_int2(B.i, (int32_t)(c.x - B.jb)));
+        A.out += __popc(ma);
+        B.out += __popc(mb);
+    }
+}
+
+// The same for one subscription, never writing past `end`; returns the next
+// free slot, or nullptr if the segment would overflow.
+__device__ __forceinline__ int2* filter_checked(const uint16_t* list, uint32_t cand_s,
+                                                uint32_t n32, const FilterSub& x,
+                                                int2* const end, int lane) {
+    const unsigned lt = (1u << lane) - 1u;
+    int2* out = x.out;
+    for (uint32_t kk = lane; kk < n32; kk += 32) {
+        const uint4 c = lds_cand(cand_s + 16u * list[kk]);
+        const bool pass = c.y < x.ph && c.z > x.pl;
+        const unsigned bm = __ballot_sync(0xffffffffu, pass);
+        if (out + __popc(bm) > end) return nullptr;
+        if (pass) __stcs(&out[__popc(bm & lt)], make_int2(x.i, (int32_t)(c.x - x.jb)));
+        out += __popc(bm);
+    }
+    return out;
+}
+
+template <bool BATCHED>
+__global__ void __launch_bounds__(WIN_BLOCK, 4) k_emit_window(EmitArgs a, DevStatus* st) {
     pdl_begin();
-    constexpr uint32_t MAXSUB = 1u << MAX_WIN_SHIFT;
-    __shared__ unsigned long long skey[WCAP];  // (update id << 32) | pos(U.lo)
-    __shared__ uint32_t spay[WCAP];            // pos(U.hi)
-    __shared__ uint32_t s_id[MAXSUB], s_lo[MAXSUB], s_hi[MAXSUB], s_cnt[MAXSUB];
-    __shared__ unsigned long long s_off[MAXSUB];
-    __shared__ uint32_t bcnt[NBUCKET], bstart[NBUCKET], warp_tmp[16];
-    __shared__ uint32_t s_pmax, s_nreg;
-    if (read_error(st)) return;
+    extern __shared__ __align__(16) unsigned char wsm[];
+    uint4* const raw = reinterpret_cast<uint4*>(wsm);                 // set-up: {id, lo, hi, rank}
+    uint16_t* const widx = reinterpret_cast<uint16_t*>(wsm);          // filter: candidate lists
+    uint4* const cand = reinterpret_cast<uint4*>(wsm + WSM_A);        // {id, lo, hi, 0} by id
+    uint32_t* const byb = reinterpret_cast<uint32_t*>(wsm + WSM_A + WSM_CAND);  // ids by bucket
+    __shared__ uint32_t bcnt[NBUCKET], bstart[NBUCKET], warp_tmp[WIN_WARPS];
+    __shared__ uint32_t s_pmax, s_nlow;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned lt = (1u << lane) - 1u;
     const uint32_t w = blockIdx.x;
     const int S = a.win_shift;
+    // Every global read of the set-up is issued in two dependent rounds.
+    // Round 1: the window's counters, the list offset, and the counters at the
+    // farthest boundary a regular subscription of this window can reach (it
+    // starts before (w+1)T and spans at most LONG_SPAN positions).
+    const uint32_t reach = (LONG_SPAN + (1u << S) - 1u) >> S;
+    const uint32_t wl = min(w + 1 + reach, a.num_win);
     const uint4 t0 = a.windows[w], t1 = a.windows[w + 1];
-    const uint32_t r0 = t0.x, ns = t1.x - t0.x;  // subscriptions starting in this window
+    const uint32_t u_lim = a.windows[wl].y;
+    const unsigned long long lwo = a.lw_off[w];
+    // An earlier stage's error leaves the counters meaningless: no read below.
+    const uint32_t ns = read_error(st) ? 0u : t1.x - t0.x;  // subscriptions starting here
     if (ns == 0) return;
-    if (ns > MAXSUB) {
-        if (tid == 0) raise_error(st, DDM_ERR_INTERNAL, 11);
-        return;
-    }
-    if (tid == 0) { s_pmax = 0; s_nreg = 0; }
-    bcnt[tid] = 0;
+    const uint32_t r0 = t0.x, u0 = t0.y, lw_n = t0.y - t0.z;
+    const bool lfit = lw_n <= a.lcap && lwo + lw_n <= a.lw_cap;
+    // Candidate k of W is list entry k for k < lw_n, else rank entry
+    // u0 + k - lw_n; the rank entries that may start before pmax are
+    // [u0, u_lim), and at most WCAP candidates are loaded.
+    const uint32_t nspec = u_lim - u0;
+    const uint64_t nall = (uint64_t)lw_n + nspec;
+    const uint32_t nload = lfit ? (uint32_t)(nall < WCAP ? nall : WCAP) : 0u;
+    if (tid == 0) { s_pmax = 0; s_nlow = 0; }
+    for (int b = tid; b < NBUCKET; b += WIN_BLOCK) bcnt[b] = 0;
     __syncthreads();
-    for (uint32_t k = tid; k < ns; k += WIN_BLOCK) {
-        const uint32_t i = a.rec.sub_order[r0 + k];
-        const uint32_t pl = a.rec.s_lo[i].x, ph = a.rec.s_hi[i].x;
-        s_id[k] = i; s_lo[k] = pl; s_hi[k] = ph;
-        s_off[k] = a.off[i];
-        s_cnt[k] = a.cnt[i];
-        if (ph - pl <= LONG_SPAN) atomicMax(&s_pmax, ph);
+    // Round 2: the window's subscriptions (rank-ordered table; a first flag
+    // for each: 1 = longer than LONG_SPAN), the boundary list and the rank
+    // entries after the boundary.
+    {
+        uint32_t pm = 0, nlong = 0;
+        for (uint32_t k = tid; k < ns; k += WIN_BLOCK) {
+            const uint4 e = a.srank[r0 + k];
+            const bool lng = e.z - e.y > LONG_SPAN;
+            a.flag[e.x] = lng ? 1 : 0;
+            nlong += lng;
+            if (!lng) pm = max(pm, e.z);
+        }
+        pm = __reduce_max_sync(0xffffffffu, pm);
+        nlong = __reduce_add_sync(0xffffffffu, nlong);
+        if (lane == 0) {
+            if (pm) atomicMax(&s_pmax, pm);
+            if (nlong) atomicAdd(a.num_flagged, nlong);
+        }
     }
-    __syncthreads();
-    const uint32_t lw_n = t0.y - t0.z;
-    const uint32_t wend = min(max((s_pmax >> S) + 1, w + 1), a.num_win);
-    const uint32_t u0 = t0.y;
-    // Updates starting in [wT, pmax): the rank table is sorted by pos(lo), so
-    // the count of entries of [u0, cUlo(wend * T)) below pmax is the exact
-    // length of the range (one parallel pass, no search).
-    const uint32_t u1 = a.windows[wend].y;
-    uint32_t nlow = 0;
-    for (uint32_t r = u0; r < u1; r += WIN_BLOCK)
-        nlow += __syncthreads_count(r + tid < u1 && a.urank[r + tid].y < s_pmax);
-    const uint32_t W = lw_n + nlow;
-    const bool overflow = !list_fits(a, w, lw_n) || W > WCAP;
-    // Flags: 1 = served by the range path.
-    for (uint32_t k = tid; k < ns; k += WIN_BLOCK) {
-        const bool lng = overflow || (s_hi[k] - s_lo[k] > LONG_SPAN);
-        a.flag[s_id[k]] = lng ? 1 : 0;
-        if (lng) atomicAdd(a.num_flagged, 1u);
-        else atomicAdd(&s_nreg, 1u);
-    }
-    if (overflow) return;
-
-    // Candidate set W (boundary list, then updates starting in [wT, wend*T)),
-    // held in registers: WITEMS per thread.
-    const int bshift = a.id_bits > 8 ? a.id_bits - 8 : 0;
-    unsigned long long key[WITEMS];
-    uint32_t pay[WITEMS], bk[WITEMS], rk[WITEMS];
+    for (uint32_t k0 = 0; k0 < nload; k0 += 4 * WIN_BLOCK) {
+        uint4 e[4];
 #pragma unroll
-    for (int it = 0; it < WITEMS; ++it) {
-        const uint32_t k = tid + it * WIN_BLOCK;
-        if (k < W) {
-            uint32_t id, pl;
-            if (k < lw_n) {
-                const uint4 e = a.lw[a.lw_off[w] + k];
-                id = e.x; pl = 0u; pay[it] = e.y;  // starts before the window: pos(lo) < any pos(S.hi)
-            } else {
-                const uint4 e = a.urank[u0 + k - lw_n];
-                id = e.x; pl = e.y; pay[it] = e.z;
+        for (int it = 0; it < 4; ++it) {
+            const uint32_t k = k0 + tid + it * WIN_BLOCK;
+            e[it] = make_uint4(0u, 0u, 0u, 0u);
+            if (k < nload) {
+                if (k < lw_n) {  // starts before the window: pos(lo) < any pos(S.hi)
+                    const uint4 v = a.lw[lwo + k];
+                    e[it] = make_uint4(v.x, 0u, v.y, 0u);
+                } else {
+                    const uint4 v = a.urank[u0 + k - lw_n];
+                    e[it] = make_uint4(v.x, v.y, v.z, 0u);
+                }
             }
-            key[it] = ((unsigned long long)id << 32) | pl;
-            bk[it] = id >> bshift;
-            rk[it] = atomicAdd(&bcnt[bk[it]], 1u);
+        }
+#pragma unroll
+        for (int it = 0; it < 4; ++it) {
+            const uint32_t k = k0 + tid + it * WIN_BLOCK;
+            if (k < nload) raw[k] = e[it];
         }
     }
     __syncthreads();
-    // Bucket sort by the high id bits: bucket starts by a block scan, then the
-    // exact position inside a bucket by counting smaller keys among its members.
+    // Updates starting in [wT, pmax): the rank table is sorted by pos(lo), so
+    // the loaded entries below pmax are a prefix of it; their count is nlow.
+    const uint32_t pmax = s_pmax;
     {
+        uint32_t c = 0;
+        for (uint32_t k = lw_n + tid; k < nload; k += WIN_BLOCK) c += raw[k].y < pmax ? 1u : 0u;
+        c = __reduce_add_sync(0xffffffffu, c);
+        if (lane == 0 && c) atomicAdd(&s_nlow, c);
+    }
+    __syncthreads();
+    const uint32_t nlow = s_nlow;
+    const uint32_t W = lw_n + nlow;
+    // Only the first WCAP candidates were loaded: if all loaded rank entries
+    // qualify and more exist, W may exceed WCAP (treated as an overflow).
+    const uint32_t room = WCAP - min(lw_n, WCAP);
+    const bool clipped = nspec > room && nlow == room;
+    if (!lfit || W > WCAP || clipped) {
+        // The whole window goes to the range path.
+        uint32_t nreg = 0;
+        for (uint32_t k = tid; k < ns; k += WIN_BLOCK) {
+            const uint4 e = a.srank[r0 + k];
+            if (e.z - e.y <= LONG_SPAN) { a.flag[e.x] = 1; ++nreg; }
+        }
+        nreg = __reduce_add_sync(0xffffffffu, nreg);
+        if (lane == 0 && nreg) atomicAdd(a.num_flagged, nreg);
+        return;
+    }
+
+    // W sorted by id: bucket sort on the high id bits (bucket starts by a
+    // block scan, arrival rank in the bucket by a shared atomic), then the
+    // exact place inside a bucket by counting smaller ids among its members.
+    const int bshift = a.id_bits > 8 ? a.id_bits - 8 : 0;
+    for (uint32_t k = tid; k < W; k += WIN_BLOCK)
+        raw[k].w = atomicAdd(&bcnt[raw[k].x >> bshift], 1u);
+    __syncthreads();
+    {
+        static_assert(NBUCKET == WIN_BLOCK, "one bucket per thread");
         const uint32_t c = bcnt[tid];
         uint32_t x = c;
 #pragma unroll
@@ -180,88 +304,101 @@ __global__ void __launch_bounds__(WIN_BLOCK) k_emit_window(EmitArgs a, DevStatus
         __syncthreads();
         uint32_t before = 0;
 #pragma unroll
-        for (int q = 0; q < WIN_BLOCK / 32; ++q) before += q < warp ? warp_tmp[q] : 0u;
+        for (int q = 0; q < WIN_WARPS; ++q) before += q < warp ? warp_tmp[q] : 0u;
         bstart[tid] = before + x - c;
     }
     __syncthreads();
-#pragma unroll
-    for (int it = 0; it < WITEMS; ++it) {
-        const uint32_t k = tid + it * WIN_BLOCK;
-        if (k < W) skey[bstart[bk[it]] + rk[it]] = key[it];
+    for (uint32_t k = tid; k < W; k += WIN_BLOCK) {
+        const uint4 e = raw[k];
+        byb[bstart[e.x >> bshift] + e.w] = e.x;
     }
     __syncthreads();
-    uint32_t fin[WITEMS];
-#pragma unroll
-    for (int it = 0; it < WITEMS; ++it) {
-        const uint32_t k = tid + it * WIN_BLOCK;
-        if (k < W) {
-            const uint32_t s0 = bstart[bk[it]], c = bcnt[bk[it]];
-            uint32_t f = s0;
-            for (uint32_t q = s0; q < s0 + c; ++q) f += skey[q] < key[it];
-            fin[it] = f;
-        }
+    for (uint32_t k = tid; k < W; k += WIN_BLOCK) {
+        const uint4 e = raw[k];
+        const uint32_t b = e.x >> bshift, s0 = bstart[b], c = bcnt[b];
+        uint32_t f = s0;
+        for (uint32_t q = s0; q < s0 + c; ++q) f += byb[q] < e.x ? 1u : 0u;
+        cand[f] = make_uint4(e.x, e.y, e.z, 0u);
     }
     __syncthreads();
-#pragma unroll
-    for (int it = 0; it < WITEMS; ++it) {
-        const uint32_t k = tid + it * WIN_BLOCK;
-        if (k < W) {
-            skey[fin[it]] = key[it];
-            spay[fin[it]] = pay[it];
-        }
-    }
-    // Pad W to whole warps with entries that no subscription keeps
-    // (pos(lo) = 0xffffffff is never below a pos(S.hi)).
-    const uint32_t Wpad = (W + 31) & ~31u;
-    for (uint32_t k = W + tid; k < Wpad; k += WIN_BLOCK) {
-        skey[k] = ~0ull;
-        spay[k] = 0u;
-    }
-    __syncthreads();
-    if (s_nreg == 0) return;
 
-    // One warp per subscription: keep the members of W it intersects.
-    const unsigned lt = (1u << lane) - 1u;
-    for (uint32_t k = warp; k < ns; k += WIN_BLOCK / 32) {
-        const uint32_t pl = s_lo[k], ph = s_hi[k];
-        if (ph - pl > LONG_SPAN) continue;
-        int32_t i = (int32_t)s_id[k];
-        uint32_t j_base = 0;  // batched: ids are written local to the instance
-        if (a.inst_sub_base) {
-            const int b = inst_of(a.inst_sub_base, a.num_inst, i);
-            i -= (int32_t)a.inst_sub_base[b];
-            j_base = (uint32_t)a.inst_upd_base[b];
+    // Filter: warp g takes subscriptions 32g .. 32g+31 (by lower endpoint).
+    if (tid == 0) cand[WCAP] = make_uint4(0u, 0xffffffffu, 0u, 0u);  // pos(lo) = ~0: never kept
+    __syncthreads();
+    uint16_t* const my_widx = widx + warp * (WCAP + 32);
+    const uint32_t cand_s = (uint32_t)__cvta_generic_to_shared(cand);
+    int2* const pairs = reinterpret_cast<int2*>(a.pairs);
+    const uint32_t Wr = (W + 31) & ~31u;
+    bool bad = false;
+    for (uint32_t g = warp; g * 32 < ns; g += WIN_WARPS) {
+        const uint32_t k = g * 32 + lane;
+        uint4 e = make_uint4(0u, 0u, 0u, 0u);
+        unsigned long long off = 0;
+        if (k < ns) { e = a.srank[r0 + k]; off = a.soff[r0 + k]; }
+        const bool reg = k < ns && e.z - e.y <= LONG_SPAN;
+        // An idle lane tests [~0, 0]: pos(U.lo) < 0 never holds.
+        const uint32_t pl = reg ? e.y : 0xffffffffu, ph = reg ? e.z : 0u;
+        const uint32_t plmin = __reduce_min_sync(0xffffffffu, pl);
+        const uint32_t phmax = __reduce_max_sync(0xffffffffu, ph);
+        if (phmax == 0) continue;  // no regular subscription in this group
+        int32_t i_out = (int32_t)e.x;
+        uint32_t jb = 0;
+        if (BATCHED && reg) {  // ids are written local to their instance
+            const int b = inst_of(a.inst_sub_base, a.num_inst, i_out);
+            i_out -= (int32_t)a.inst_sub_base[b];
+            jb = (uint32_t)a.inst_upd_base[b];
         }
-        int2* out = reinterpret_cast<int2*>(a.pairs) + s_off[k];  // next free slot of the segment
-        int2* const end = out + s_cnt[k];
-        // Two 32-wide chunks per iteration for independent shared-memory loads.
-        // Wpad is a multiple of 32, so every loop condition and the capacity
-        // check are uniform across the warp.
-        uint32_t kk = lane;
-        for (; kk + 32 < Wpad; kk += 64) {
-            const unsigned long long kv0 = skey[kk], kv1 = skey[kk + 32];
-            const uint32_t p0 = spay[kk], p1 = spay[kk + 32];
-            const bool pass0 = ((uint32_t)kv0 < ph) & (p0 > pl);
-            const bool pass1 = ((uint32_t)kv1 < ph) & (p1 > pl);
-            const unsigned b0 = __ballot_sync(0xffffffffu, pass0);
-            const unsigned b1 = __ballot_sync(0xffffffffu, pass1);
-            const int n0 = __popc(b0), n1 = __popc(b1);
-            if (out + n0 + n1 > end) break;  // uniform: never write past the segment
-            // Streaming stores: the pairs are written once and not read back here.
-            if (pass0) __stcs(&out[__popc(b0 & lt)], make_int2(i, (int32_t)((uint32_t)(kv0 >> 32) - j_base)));
-            if (pass1) __stcs(&out[n0 + __popc(b1 & lt)], make_int2(i, (int32_t)((uint32_t)(kv1 >> 32) - j_base)));
-            out += n0 + n1;
+        const uint32_t cnt = reg ? e.w : 0u;
+        // The members of W that can meet some subscription of the group, in
+        // id order, padded to whole warps with the entry no one keeps.
+        uint32_t nq = 0;
+        for (uint32_t kk = lane; kk < Wr; kk += 32) {
+            bool pass = false;
+            if (kk < W) {
+                const uint4 c = cand[kk];
+                pass = c.y < phmax && c.z > plmin;
+            }
+            const unsigned bm = __ballot_sync(0xffffffffu, pass);
+            if (pass) my_widx[nq + __popc(bm & lt)] = (uint16_t)kk;
+            nq += __popc(bm);
         }
-        for (; kk < Wpad; kk += 32) {
-            const unsigned long long kv = skey[kk];
-            const bool pass = ((uint32_t)kv < ph) & (spay[kk] > pl);
-            const unsigned b = __ballot_sync(0xffffffffu, pass);
-            if (out + __popc(b) > end) break;
-            if (pass) __stcs(&out[__popc(b & lt)], make_int2(i, (int32_t)((uint32_t)(kv >> 32) - j_base)));
-            out += __popc(b);
+        const uint32_t nq32 = (nq + 31) & ~31u;
+        if (lane < nq32 - nq) my_widx[nq + lane] = (uint16_t)WCAP;
+        __syncwarp();
+        // Two subscriptions per pass over the list: each step loads one entry
+        // per lane and tests it against both; the kept ones are compacted by
+        // ballot into each segment, so every segment is written in id order.
+        const bool all_fit = __all_sync(0xffffffffu, off + nq <= a.cap);
+        for (int l = 0; l < 32; l += 2) {
+            FilterSub A, B;
+            A.ph = __shfl_sync(0xffffffffu, ph, l);
+            B.ph = __shfl_sync(0xffffffffu, ph, l + 1);
+            if ((A.ph | B.ph) == 0) continue;  // both idle or long
+            A.pl = __shfl_sync(0xffffffffu, pl, l);
+            B.pl = __shfl_sync(0xffffffffu, pl, l + 1);
+            A.i = __shfl_sync(0xffffffffu, i_out, l);
+            B.i = __shfl_sync(0xffffffffu, i_out, l + 1);
+            A.jb = BATCHED ? __shfl_sync(0xffffffffu, jb, l) : 0u;
+            B.jb = BATCHED ? __shfl_sync(0xffffffffu, jb, l + 1) : 0u;
+            const uint32_t cA = __shfl_sync(0xffffffffu, cnt, l);
+            const uint32_t cB = __shfl_sync(0xffffffffu, cnt, l + 1);
+            A.out = pairs + __shfl_sync(0xffffffffu, off, l);
+            B.out = pairs + __shfl_sync(0xffffffffu, off, l + 1);
+            int2* const endA = A.out + cA;
+            int2* const endB = B.out + cB;
+            if (all_fit) {
+                // No bound check per step: at most nq pairs each, and
+                // off + nq <= cap for every segment of the group.
+                filter_pair(my_widx, cand_s, nq32, A, B, lane);
+                if (A.out != endA || B.out != endB) bad = true;
+            } else {
+                if (filter_checked(my_widx, cand_s, nq32, A, endA, lane) != endA) bad = true;
+                if (filter_checked(my_widx, cand_s, nq32, B, endB, lane) != endB) bad = true;
+            }
         }
-        if (lane == 0 && (out != end || kk < Wpad)) raise_error(st, DDM_ERR_INTERNAL, 12);
+        __syncwarp();  // every lane is done with the list before the next group rebuilds it
     }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) raise_error(st, DDM_ERR_INTERNAL, 12);
 }
 
 static unsigned grid_for(uint64_t items, unsigned per_block, unsigned cap) {
@@ -270,15 +407,32 @@ static unsigned grid_for(uint64_t items, unsigned per_block, unsigned cap) {
 }
 
 int launch_tile_active(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
-    if (a.m == 0 || a.num_win == 0) return 0;
-    launch_k(k_tile_active, grid_for(a.m, 256, 152 * 16), 256, 0, s, a, st);
+    if (a.num_win == 0) return 0;
+    const unsigned gu = a.m ? grid_for((uint64_t)a.m, 256, 152 * 16) : 0u;
+    const unsigned gs = a.srank && a.n ? grid_for((uint64_t)a.n, 256, 152 * 8) : 0u;
+    if (gu + gs == 0) return 0;
+    launch_k(k_tile_active, gu + gs, 256, 0, s, a, st, gu);
     return 1;
+}
+
+template <bool BATCHED>
+static void launch_emit_window_t(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
+    static std::atomic<unsigned long long> attr_set{0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !(attr_set.load() & (1ull << dev))) {
+        cudaFuncSetAttribute(k_emit_window<BATCHED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)WSM_TOTAL);
+        if (dev >= 0 && dev < 64) attr_set.fetch_or(1ull << dev);
+    }
+    launch_k(k_emit_window<BATCHED>, a.num_win, WIN_BLOCK, WSM_TOTAL, s, a, st);
 }
 
 int launch_emit_window(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
     if (a.num_win == 0 || a.n == 0) return 0;
     if (a.win_shift > MAX_WIN_SHIFT) return -1;
-    launch_k(k_emit_window, a.num_win, WIN_BLOCK, 0, s, a, st);
+    if (a.inst_sub_base) launch_emit_window_t<true>(a, st, s);
+    else launch_emit_window_t<false>(a, st, s);
     return 1;
 }
 

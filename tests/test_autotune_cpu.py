@@ -38,21 +38,21 @@ def test_workload_key_buckets():
 def test_tune_picks_fastest_and_caches(tmp_path):
     cache = tmp_path / "tune.json"
     ctx = FakeCtx(K=1000)
-    fake_ms = {7: 3.0, 8: 1.0, 9: 2.0}
+    fake_ms = {8: 3.0, 9: 1.0, 10: 2.0}
 
     def timer(c, t, K, reps):
         return fake_ms[c.params[PARAM_WIN_SHIFT]]
 
     chosen = autotune.tune(ctx, tensors(1, 100, 100), cache_path=str(cache), gpu="G", timer=timer)
-    assert chosen["win_shift"] == 8 and ctx.params[PARAM_WIN_SHIFT] == 8
+    assert chosen["win_shift"] == 9 and ctx.params[PARAM_WIN_SHIFT] == 9
     assert PARAM_ND_PATH not in ctx.params            # d = 1: no d > 1 strategy
     stored = json.loads(cache.read_text())
-    assert stored[chosen["key"]]["win_shift"] == 8
-    assert stored[chosen["key"]]["win_shift_ms"] == {"7": 3.0, "8": 1.0, "9": 2.0}
+    assert stored[chosen["key"]]["win_shift"] == 9
+    assert stored[chosen["key"]]["win_shift_ms"] == {"8": 3.0, "9": 1.0, "10": 2.0}
 
     fresh = FakeCtx(K=1000)
     assert autotune.apply_cached(fresh, tensors(1, 100, 100), cache_path=str(cache), gpu="G")
-    assert fresh.params == {PARAM_WIN_SHIFT: 8}
+    assert fresh.params == {PARAM_WIN_SHIFT: 9}
     # another workload class or GPU: nothing cached
     assert not autotune.apply_cached(FakeCtx(K=10**6), tensors(1, 100, 100),
                                      cache_path=str(cache), gpu="G")
