@@ -19,7 +19,8 @@
 // positions) and writes them in that order.
 //
 // A warp takes 32 consecutive subscriptions (by lower endpoint) and first
-// narrows W to the members that can meet any of them; it then filters that
+// copies the members of W that can meet any of them into a list of its own
+// (8-byte entries, positions relative to the window); it then filters that
 // list for two subscriptions at a time, testing 32 entries per step and
 // compacting the kept ones by ballot into each output segment.
 //
@@ -40,12 +41,21 @@ constexpr uint32_t LONG_SPAN = 512;   // positions; longer subscriptions use the
 constexpr int MAX_WIN_SHIFT = 10;     // windows of at most 1024 positions
 constexpr int NBUCKET = 256;          // buckets of the per-window id sort
 
+constexpr uint32_t LCAP_W = 512;      // entries of a warp's candidate list (longer: in pieces)
+
+// Candidates in the filter are 8 bytes: {update id, (hi << 16) | lo}, with lo
+// and hi the stream positions relative to the window start wT.  lo is 0 for
+// updates starting before the window and below T + LONG_SPAN otherwise; hi is
+// clamped to 0xffff, which is above every subscription's lower position.
+constexpr uint32_t REL_MAX = 0xffffu;
+static_assert((1u << MAX_WIN_SHIFT) + LONG_SPAN < REL_MAX, "relative positions fit 16 bits");
+
 // Dynamic shared memory of k_emit_window.  The per-warp candidate lists
 // overlay the raw candidate array of the set-up.
 constexpr size_t WSM_RAW = (size_t)WCAP * 16;
-constexpr size_t WSM_WIDX = (size_t)WIN_WARPS * (WCAP + 32) * 2;
-constexpr size_t WSM_A = ((WSM_RAW > WSM_WIDX ? WSM_RAW : WSM_WIDX) + 15) & ~(size_t)15;
-constexpr size_t WSM_CAND = (size_t)(WCAP + 1) * 16;  // + one entry that no subscription keeps
+constexpr size_t WSM_LIST = (size_t)WIN_WARPS * (LCAP_W + 32) * 8;
+constexpr size_t WSM_A = ((WSM_RAW > WSM_LIST ? WSM_RAW : WSM_LIST) + 15) & ~(size_t)15;
+constexpr size_t WSM_CAND = (size_t)WCAP * 8;
 constexpr size_t WSM_BYB = (size_t)WCAP * 4;
 constexpr size_t WSM_TOTAL = WSM_A + WSM_CAND + WSM_BYB;
 
@@ -120,18 +130,8 @@ __global__ void k_tile_active(EmitArgs a, DevStatus* st, unsigned gu) {
     }
 }
 
-// Candidate read by 32-bit shared-window address.  The candidate array does
-// not change while the filter runs, so the read is declared free of side
-// effects and the compiler may overlap the reads of successive steps.
-__device__ __forceinline__ uint4 lds_cand(uint32_t addr) {
-    uint4 v;
-    asm("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
-        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr));
-    return v;
-}
-
-// One subscription of the filter: its bounds, output id, id base and next
-// free slot of its segment.
+// One subscription of the filter: its relative bounds, output id, id base
+// and next free slot of its segment.
 struct FilterSub {
     uint32_t pl, ph;
     int32_t i;
@@ -139,17 +139,18 @@ struct FilterSub {
     int2* out;
 };
 
-// Keeps the list entries (candidate indices; pos(lo) < ph and pl < pos(hi))
+// Keeps the list entries (pos(lo) < ph and pl < pos(hi), relative positions)
 // of two subscriptions, 32 entries per step.  The caller guarantees room for
-// a whole list after each segment start.
-__device__ __forceinline__ void filter_pair(const uint16_t* list, uint32_t cand_s, uint32_t n32,
-                                            FilterSub& A, FilterSub& B, int lane) {
+// a whole list after each segment's next free slot.
+__device__ __forceinline__ void filter_pair(const uint2* list, uint32_t n32, FilterSub& A,
+                                            FilterSub& B, int lane) {
     const unsigned lt = (1u << lane) - 1u;
 #pragma unroll 2
     for (uint32_t kk = lane; kk < n32; kk += 32) {
-        const uint4 c = lds_cand(cand_s + 16u * list[kk]);
-        const bool a = c.y < A.ph && c.z > A.pl;
-        const bool b = c.y < B.ph && c.z > B.pl;
+        const uint2 c = list[kk];
+        const uint32_t lo = c.y & 0xffffu, hi = c.y >> 16;
+        const bool a = lo < A.ph && hi > A.pl;
+        const bool b = lo < B.ph && hi > B.pl;
         const unsigned ma = __ballot_sync(0xffffffffu, a);
         const unsigned mb = __ballot_sync(0xffffffffu, b);
         if (a) __stcs(&A.out[__popc(ma & lt)], make_int2(A.i, (int32_t)(c.x - A.jb)));
@@ -159,22 +160,23 @@ __device__ __forceinline__ void filter_pair(const uint16_t* list, uint32_t cand_
     }
 }
 
-// The same for one subscription, never writing past `end`; returns the next
-// free slot, or nullptr if the segment would overflow.
-__device__ __forceinline__ int2* filter_checked(const uint16_t* list, uint32_t cand_s,
-                                                uint32_t n32, const FilterSub& x,
-                                                int2* const end, int lane) {
+// The same for one subscription, never writing past `end`: advances x.out
+// and returns false if the segment would overflow (x.out then stops there).
+__device__ __forceinline__ bool filter_checked(const uint2* list, uint32_t n32, FilterSub& x,
+                                               int2* const end, int lane) {
     const unsigned lt = (1u << lane) - 1u;
-    int2* out = x.out;
     for (uint32_t kk = lane; kk < n32; kk += 32) {
-        const uint4 c = lds_cand(cand_s + 16u * list[kk]);
-        const bool pass = c.y < x.ph && c.z > x.pl;
+        const uint2 c = list[kk];
+        const bool pass = (c.y & 0xffffu) < x.ph && (c.y >> 16) > x.pl;
         const unsigned bm = __ballot_sync(0xffffffffu, pass);
-        if (out + __popc(bm) > end) return nullptr;
-        if (pass) __stcs(&out[__popc(bm & lt)], make_int2(x.i, (int32_t)(c.x - x.jb)));
-        out += __popc(bm);
+        if (x.out + __popc(bm) > end) {
+            x.out = end;
+            return false;
+        }
+        if (pass) __stcs(&x.out[__popc(bm & lt)], make_int2(x.i, (int32_t)(c.x - x.jb)));
+        x.out += __popc(bm);
     }
-    return out;
+    return true;
 }
 
 template <bool BATCHED>
@@ -182,8 +184,8 @@ __global__ void __launch_bounds__(WIN_BLOCK, 4) k_emit_window(EmitArgs a, DevSta
     pdl_begin();
     extern __shared__ __align__(16) unsigned char wsm[];
     uint4* const raw = reinterpret_cast<uint4*>(wsm);                 // set-up: {id, lo, hi, rank}
-    uint16_t* const widx = reinterpret_cast<uint16_t*>(wsm);          // filter: candidate lists
-    uint4* const cand = reinterpret_cast<uint4*>(wsm + WSM_A);        // {id, lo, hi, 0} by id
+    uint2* const lists = reinterpret_cast<uint2*>(wsm);               // filter: per-warp lists
+    uint2* const cand = reinterpret_cast<uint2*>(wsm + WSM_A);        // packed candidates by id
     uint32_t* const byb = reinterpret_cast<uint32_t*>(wsm + WSM_A + WSM_CAND);  // ids by bucket
     __shared__ uint32_t bcnt[NBUCKET], bstart[NBUCKET], warp_tmp[WIN_WARPS];
     __shared__ uint32_t s_pmax, s_nlow;
@@ -191,6 +193,7 @@ __global__ void __launch_bounds__(WIN_BLOCK, 4) k_emit_window(EmitArgs a, DevSta
     const unsigned lt = (1u << lane) - 1u;
     const uint32_t w = blockIdx.x;
     const int S = a.win_shift;
+    const uint32_t wT = w << S;  // the window's first stream position
     // Every global read of the set-up is issued in two dependent rounds.
     // Round 1: the window's counters, the list offset, and the counters at the
     // farthest boundary a regular subscription of this window can reach (it
@@ -318,17 +321,17 @@ __global__ void __launch_bounds__(WIN_BLOCK, 4) k_emit_window(EmitArgs a, DevSta
         const uint32_t b = e.x >> bshift, s0 = bstart[b], c = bcnt[b];
         uint32_t f = s0;
         for (uint32_t q = s0; q < s0 + c; ++q) f += byb[q] < e.x ? 1u : 0u;
-        cand[f] = make_uint4(e.x, e.y, e.z, 0u);
+        // Relative positions (list entries have lo = 0: before the window).
+        const uint32_t lo = e.y ? e.y - wT : 0u;
+        const uint32_t hi = min(e.z - wT, REL_MAX);
+        cand[f] = make_uint2(e.x, (hi << 16) | lo);
     }
     __syncthreads();
 
     // Filter: warp g takes subscriptions 32g .. 32g+31 (by lower endpoint).
-    if (tid == 0) cand[WCAP] = make_uint4(0u, 0xffffffffu, 0u, 0u);  // pos(lo) = ~0: never kept
-    __syncthreads();
-    uint16_t* const my_widx = widx + warp * (WCAP + 32);
-    const uint32_t cand_s = (uint32_t)__cvta_generic_to_shared(cand);
-    int2* const pairs = reinterpret_cast<int2*>(a.pairs);
+    uint2* const my_list = lists + warp * (LCAP_W + 32);
     const uint32_t Wr = (W + 31) & ~31u;
+    int2* const pairs = reinterpret_cast<int2*>(a.pairs);
     bool bad = false;
     for (uint32_t g = warp; g * 32 < ns; g += WIN_WARPS) {
         const uint32_t k = g * 32 + lane;
@@ -336,8 +339,8 @@ __global__ void __launch_bounds__(WIN_BLOCK, 4) k_emit_window(EmitArgs a, DevSta
         unsigned long long off = 0;
         if (k < ns) { e = a.srank[r0 + k]; off = a.soff[r0 + k]; }
         const bool reg = k < ns && e.z - e.y <= LONG_SPAN;
-        // An idle lane tests [~0, 0]: pos(U.lo) < 0 never holds.
-        const uint32_t pl = reg ? e.y : 0xffffffffu, ph = reg ? e.z : 0u;
+        // Relative bounds; an idle lane tests [0xffff, 0]: lo < 0 never holds.
+        const uint32_t pl = reg ? e.y - wT : REL_MAX, ph = reg ? e.z - wT : 0u;
         const uint32_t plmin = __reduce_min_sync(0xffffffffu, pl);
         const uint32_t phmax = __reduce_max_sync(0xffffffffu, ph);
         if (phmax == 0) continue;  // no regular subscription in this group
@@ -348,55 +351,62 @@ __global__ void __launch_bounds__(WIN_BLOCK, 4) k_emit_window(EmitArgs a, DevSta
             i_out -= (int32_t)a.inst_sub_base[b];
             jb = (uint32_t)a.inst_upd_base[b];
         }
-        const uint32_t cnt = reg ? e.w : 0u;
+        int2* my_out = pairs + off;  // next free slot of this lane's segment
+        int2* const my_end = my_out + (reg ? e.w : 0u);
+        // Without a bound check per step: a subscription keeps at most W
+        // candidates, and off + W <= cap for every segment of the group.
+        const bool all_fit = __all_sync(0xffffffffu, off + W <= a.cap);
         // The members of W that can meet some subscription of the group, in
-        // id order, padded to whole warps with the entry no one keeps.
-        uint32_t nq = 0;
-        for (uint32_t kk = lane; kk < Wr; kk += 32) {
-            bool pass = false;
-            if (kk < W) {
-                const uint4 c = cand[kk];
-                pass = c.y < phmax && c.z > plmin;
+        // id order, copied into the warp's list; more than LCAP_W of them are
+        // filtered in pieces (each piece in id order after the previous one).
+        for (uint32_t kk0 = 0; kk0 < Wr;) {
+            uint32_t nq = 0;
+            for (; kk0 < Wr && nq + 32 <= LCAP_W; kk0 += 32) {
+                const uint32_t kk = kk0 + lane;
+                uint2 c = make_uint2(0u, 0u);
+                bool pass = false;
+                if (kk < W) {
+                    c = cand[kk];
+                    pass = (c.y & 0xffffu) < phmax && (c.y >> 16) > plmin;
+                }
+                const unsigned bm = __ballot_sync(0xffffffffu, pass);
+                if (pass) my_list[nq + __popc(bm & lt)] = c;
+                nq += __popc(bm);
             }
-            const unsigned bm = __ballot_sync(0xffffffffu, pass);
-            if (pass) my_widx[nq + __popc(bm & lt)] = (uint16_t)kk;
-            nq += __popc(bm);
-        }
-        const uint32_t nq32 = (nq + 31) & ~31u;
-        if (lane < nq32 - nq) my_widx[nq + lane] = (uint16_t)WCAP;
-        __syncwarp();
-        // Two subscriptions per pass over the list: each step loads one entry
-        // per lane and tests it against both; the kept ones are compacted by
-        // ballot into each segment, so every segment is written in id order.
-        const bool all_fit = __all_sync(0xffffffffu, off + nq <= a.cap);
-        for (int l = 0; l < 32; l += 2) {
-            FilterSub A, B;
-            A.ph = __shfl_sync(0xffffffffu, ph, l);
-            B.ph = __shfl_sync(0xffffffffu, ph, l + 1);
-            if ((A.ph | B.ph) == 0) continue;  // both idle or long
-            A.pl = __shfl_sync(0xffffffffu, pl, l);
-            B.pl = __shfl_sync(0xffffffffu, pl, l + 1);
-            A.i = __shfl_sync(0xffffffffu, i_out, l);
-            B.i = __shfl_sync(0xffffffffu, i_out, l + 1);
-            A.jb = BATCHED ? __shfl_sync(0xffffffffu, jb, l) : 0u;
-            B.jb = BATCHED ? __shfl_sync(0xffffffffu, jb, l + 1) : 0u;
-            const uint32_t cA = __shfl_sync(0xffffffffu, cnt, l);
-            const uint32_t cB = __shfl_sync(0xffffffffu, cnt, l + 1);
-            A.out = pairs + __shfl_sync(0xffffffffu, off, l);
-            B.out = pairs + __shfl_sync(0xffffffffu, off, l + 1);
-            int2* const endA = A.out + cA;
-            int2* const endB = B.out + cB;
-            if (all_fit) {
-                // No bound check per step: at most nq pairs each, and
-                // off + nq <= cap for every segment of the group.
-                filter_pair(my_widx, cand_s, nq32, A, B, lane);
-                if (A.out != endA || B.out != endB) bad = true;
-            } else {
-                if (filter_checked(my_widx, cand_s, nq32, A, endA, lane) != endA) bad = true;
-                if (filter_checked(my_widx, cand_s, nq32, B, endB, lane) != endB) bad = true;
+            const uint32_t nq32 = (nq + 31) & ~31u;
+            // Padding that no subscription keeps (lo = 0xffff).
+            if (lane < nq32 - nq) my_list[nq + lane] = make_uint2(0u, REL_MAX);
+            __syncwarp();
+            // Two subscriptions per pass over the list: each step loads one
+            // entry per lane and tests it against both; the kept ones are
+            // compacted by ballot into each segment, in id order.
+            for (int l = 0; l < 32; l += 2) {
+                FilterSub A, B;
+                A.ph = __shfl_sync(0xffffffffu, ph, l);
+                B.ph = __shfl_sync(0xffffffffu, ph, l + 1);
+                if ((A.ph | B.ph) == 0) continue;  // both idle or long
+                A.pl = __shfl_sync(0xffffffffu, pl, l);
+                B.pl = __shfl_sync(0xffffffffu, pl, l + 1);
+                A.i = __shfl_sync(0xffffffffu, i_out, l);
+                B.i = __shfl_sync(0xffffffffu, i_out, l + 1);
+                A.jb = BATCHED ? __shfl_sync(0xffffffffu, jb, l) : 0u;
+                B.jb = BATCHED ? __shfl_sync(0xffffffffu, jb, l + 1) : 0u;
+                A.out = reinterpret_cast<int2*>(__shfl_sync(0xffffffffu, reinterpret_cast<uintptr_t>(my_out), l));
+                B.out = reinterpret_cast<int2*>(__shfl_sync(0xffffffffu, reinterpret_cast<uintptr_t>(my_out), l + 1));
+                if (all_fit) {
+                    filter_pair(my_list, nq32, A, B, lane);
+                } else {
+                    int2* const endA = reinterpret_cast<int2*>(__shfl_sync(0xffffffffu, reinterpret_cast<uintptr_t>(my_end), l));
+                    int2* const endB = reinterpret_cast<int2*>(__shfl_sync(0xffffffffu, reinterpret_cast<uintptr_t>(my_end), l + 1));
+                    if (!filter_checked(my_list, nq32, A, endA, lane)) bad = true;
+                    if (!filter_checked(my_list, nq32, B, endB, lane)) bad = true;
+                }
+                if (lane == l) my_out = A.out;
+                if (lane == l + 1) my_out = B.out;
             }
+            __syncwarp();  // every lane is done with the list before it is rebuilt
         }
-        __syncwarp();  // every lane is done with the list before the next group rebuilds it
+        if (my_out != my_end) bad = true;
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) raise_error(st, DDM_ERR_INTERNAL, 12);
 }
