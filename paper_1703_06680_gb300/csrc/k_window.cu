@@ -82,11 +82,23 @@ __global__ void k_tile_active(EmitArgs a, DevStatus* st, unsigned gu) {
         // Window path: the subscriptions in lower-endpoint order with what the
         // emission needs of each, so that a window reads its own contiguously.
         const int64_t sstride = (int64_t)(gridDim.x - gu) * blockDim.x;
+        // Two subscriptions per thread and iteration: all gathers in flight together.
         for (int64_t r = (int64_t)(blockIdx.x - gu) * blockDim.x + threadIdx.x; r < a.n;
-             r += sstride) {
+             r += 2 * sstride) {
+            const int64_t r2 = r + sstride;
+            const bool two = r2 < a.n;
             const uint32_t i = a.rec.sub_order[r];
-            a.srank[r] = make_uint4(i, a.rec.s_lo[i].x, a.rec.s_hi[i].x, a.cnt[i]);
-            a.soff[r] = a.off[i];
+            const uint32_t i2 = two ? a.rec.sub_order[r2] : i;
+            const uint32_t pl = a.rec.s_lo[i].x, ph = a.rec.s_hi[i].x, c = a.cnt[i];
+            const unsigned long long o = a.off[i];
+            const uint32_t pl2 = a.rec.s_lo[i2].x, ph2 = a.rec.s_hi[i2].x, c2 = a.cnt[i2];
+            const unsigned long long o2 = a.off[i2];
+            a.srank[r] = make_uint4(i, pl, ph, c);
+            a.soff[r] = o;
+            if (two) {
+                a.srank[r2] = make_uint4(i2, pl2, ph2, c2);
+                a.soff[r2] = o2;
+            }
         }
         return;
     }
@@ -419,7 +431,7 @@ static unsigned grid_for(uint64_t items, unsigned per_block, unsigned cap) {
 int launch_tile_active(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
     if (a.num_win == 0) return 0;
     const unsigned gu = a.m ? grid_for((uint64_t)a.m, 256, 152 * 16) : 0u;
-    const unsigned gs = a.srank && a.n ? grid_for((uint64_t)a.n, 256, 152 * 8) : 0u;
+    const unsigned gs = a.srank && a.n ? grid_for((uint64_t)a.n, 512, 152 * 8) : 0u;
     if (gu + gs == 0) return 0;
     launch_k(k_tile_active, gu + gs, 256, 0, s, a, st, gu);
     return 1;
