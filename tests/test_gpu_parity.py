@@ -325,3 +325,42 @@ def test_memory_budget_exhaustion_is_reported():
         small.close()
     with ddm.Context(0) as c:
         assert c.count(*to_dev(reg)) == oracle.sbm_count(reg)
+
+
+# --- window emission: long candidate lists, overflow, window sizes, alignment ---------
+
+@pytest.mark.parametrize("num_huge", [600, 1100])
+def test_window_long_candidate_lists(ctx, num_huge):
+    # Short subscriptions under num_huge updates that span the whole routing space:
+    # every boundary list holds them all.  600: each warp's candidate list is longer
+    # than one piece (filtered piece by piece, in id order); 1100: the boundary
+    # lists exceed their cap and the windows fall back to the range path.
+    base = synth.make_regions(1, 20_000, 2_000, 50.0, 77)
+    u_lo = np.concatenate([base.upd_lo, np.full((1, num_huge), -1.0, np.float32)], axis=1)
+    u_hi = np.concatenate([base.upd_hi, np.full((1, num_huge), 2.0e6, np.float32)], axis=1)
+    reg = synth.Regions(base.sub_lo, base.sub_hi, u_lo, u_hi)
+    assert_parity(ctx, reg)
+
+
+@pytest.mark.parametrize("shift", [6, 7, 8, 9, 10])
+def test_window_sizes(shift):
+    import paper_1703_06680_gb300 as ddm
+    reg = synth.large_1d(100.0, N=100_000)
+    want = oracle.sbm(reg)
+    with ddm.Context(0) as c:
+        c.set_param(ddm._lib.PARAM_WIN_SHIFT, shift)
+        assert np.array_equal(gpu_pairs(c, reg), want)
+
+
+def test_misaligned_pairs_rejected(ctx):
+    # Pairs are written as 8-byte units: a pointer 4 bytes off is refused before
+    # any launch, and the context stays usable.
+    import torch
+    import paper_1703_06680_gb300 as ddm
+    reg = synth.small_1d()
+    t = to_dev(reg)
+    K = ctx.count(*t)
+    buf = torch.empty(2 * K + 1, dtype=torch.int32, device=t[0].device)
+    with pytest.raises(ddm.DDMError):
+        ctx.match_into(buf[1:].view(K, 2), *t)
+    assert_parity(ctx, reg)
