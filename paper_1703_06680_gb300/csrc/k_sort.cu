@@ -142,9 +142,8 @@ struct DownSmem {
     static constexpr int TILE = SORT_BLOCK * ITEMS;
     KeyT keys[TILE];                          // raw tile, then keys in digit-major order
     uint32_t vals_raw[TILE];                  // raw tile values
-    union {
+    struct {
         uint32_t vals[TILE];                  // values in digit-major order (after ranking)
-        uint32_t peers[SORT_BLOCK / 32][RADIX];  // per-warp lane masks (during ranking)
     } u;
     uint32_t whist[SORT_BLOCK / 32][RADIX];   // per-warp digit counters
     uint32_t tile_start[RADIX];               // exclusive scan of tile counts over digits
@@ -175,11 +174,13 @@ k_downsweep(const KeyT* __restrict__ keys_in, const uint32_t* __restrict__ vals_
     const uint32_t tile = blockIdx.x;
     const uint64_t tbase = (uint64_t)tile * TILE;
     const bool full = tbase + TILE <= E;
-    if (tid == 0 && full) mbar_init(&sm.bar, 1);
-    for (int t = tid; t < WARPS * RADIX; t += SORT_BLOCK) {
-        (&sm.whist[0][0])[t] = 0;
-        (&sm.u.peers[0][0])[t] = 0;
+    if (tid == 0 && full) {  // the tile is in flight while the digit offsets are formed
+        mbar_init(&sm.bar, 1);
+        mbar_expect_tx(&sm.bar, TILE * (sizeof(KeyT) + sizeof(uint32_t)));
+        tma_load_1d(sm.keys, keys_in + tbase, TILE * sizeof(KeyT), &sm.bar);
+        tma_load_1d(sm.vals_raw, vals_in + tbase, TILE * sizeof(uint32_t), &sm.bar);
     }
+    for (int t = tid; t < WARPS * RADIX; t += SORT_BLOCK) (&sm.whist[0][0])[t] = 0;
     if (grp) {  // fused offsets (thread = digit)
         const uint32_t g = tile >> SORT_GROUP_SHIFT;
         const uint32_t ngroups = (tiles + (1u << SORT_GROUP_SHIFT) - 1) >> SORT_GROUP_SHIFT;
@@ -198,11 +199,6 @@ k_downsweep(const KeyT* __restrict__ keys_in, const uint32_t* __restrict__ vals_
         sm.gbase[tid] = (uint32_t)base[(uint64_t)tid * tiles + tile];
     }
     __syncthreads();
-    if (full && tid == 0) {
-        mbar_expect_tx(&sm.bar, TILE * (sizeof(KeyT) + sizeof(uint32_t)));
-        tma_load_1d(sm.keys, keys_in + tbase, TILE * sizeof(KeyT), &sm.bar);
-        tma_load_1d(sm.vals_raw, vals_in + tbase, TILE * sizeof(uint32_t), &sm.bar);
-    }
     if (clr) {  // this block's share of a zero fill, while the tile is in flight
         const uint64_t share = (clr_words + gridDim.x - 1) / gridDim.x;
         const uint64_t c0 = (uint64_t)blockIdx.x * share;
@@ -230,22 +226,23 @@ k_downsweep(const KeyT* __restrict__ keys_in, const uint32_t* __restrict__ vals_
         dig[i] = digit_of(key[i], shift);
     }
     // Stable ranking inside the warp, items in (i, lane) order: the lanes
-    // holding the same digit find each other through a per-warp mask word per
-    // digit (atomicOr of the lane bit); the lowest such lane advances the
-    // warp's counter for that digit and clears the mask.
+    // holding the same digit find each other with one ballot per digit bit
+    // (no shared-memory round trip); the lowest such lane advances the warp's
+    // counter for that digit.
     const unsigned lt = (1u << lane) - 1u;
     uint32_t* wh = sm.whist[warp];
-    uint32_t* pm = sm.u.peers[warp];
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
-        atomicOr(&pm[dig[i]], 1u << lane);
-        __syncwarp();
-        const unsigned peers = pm[dig[i]];
-        __syncwarp();
+        unsigned peers = 0xffffffffu;
+#pragma unroll
+        for (int b = 0; b < RADIX_BITS; ++b) {
+            const bool bit = (dig[i] >> b) & 1u;
+            const unsigned m = __ballot_sync(0xffffffffu, bit);
+            peers &= bit ? m : ~m;
+        }
         const int leader = __ffs(peers) - 1;
         uint32_t c = 0;
         if (lane == leader) {
-            pm[dig[i]] = 0u;
             c = wh[dig[i]];
             wh[dig[i]] = c + __popc(peers);
         }
