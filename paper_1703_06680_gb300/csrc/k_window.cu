@@ -24,9 +24,10 @@
 // list for two subscriptions at a time, testing 32 entries per step and
 // compacting the kept ones by ballot into each output segment.
 //
-// Subscriptions spanning more than LONG_SPAN positions, and windows whose
-// boundary list exceeds LCAP entries (or the list storage), are flagged and
-// served by the range path (k_emit.cu) followed by the per-segment sort.
+// Subscriptions spanning more than LONG_SPAN positions, and every subscription
+// of a window whose boundary list or candidate set exceeds WCAP entries (or
+// the list storage), are flagged and served by the range path (k_emit.cu)
+// followed by the per-segment sort.
 #include <atomic>
 
 #include "emit.cuh"
@@ -189,6 +190,11 @@ __device__ __forceinline__ bool filter_checked(const uint2* list, uint32_t n32, 
         x.out += __popc(bm);
     }
     return true;
+}
+
+// Lane l's segment pointer, to every lane.
+__device__ __forceinline__ int2* shfl_ptr(int2* p, int l) {
+    return reinterpret_cast<int2*>(__shfl_sync(0xffffffffu, reinterpret_cast<uintptr_t>(p), l));
 }
 
 template <bool BATCHED>
@@ -403,13 +409,13 @@ __global__ void __launch_bounds__(WIN_BLOCK, 4) k_emit_window(EmitArgs a, DevSta
                 B.i = __shfl_sync(0xffffffffu, i_out, l + 1);
                 A.jb = BATCHED ? __shfl_sync(0xffffffffu, jb, l) : 0u;
                 B.jb = BATCHED ? __shfl_sync(0xffffffffu, jb, l + 1) : 0u;
-                A.out = reinterpret_cast<int2*>(__shfl_sync(0xffffffffu, reinterpret_cast<uintptr_t>(my_out), l));
-                B.out = reinterpret_cast<int2*>(__shfl_sync(0xffffffffu, reinterpret_cast<uintptr_t>(my_out), l + 1));
+                A.out = shfl_ptr(my_out, l);
+                B.out = shfl_ptr(my_out, l + 1);
                 if (all_fit) {
                     filter_pair(my_list, nq32, A, B, lane);
                 } else {
-                    int2* const endA = reinterpret_cast<int2*>(__shfl_sync(0xffffffffu, reinterpret_cast<uintptr_t>(my_end), l));
-                    int2* const endB = reinterpret_cast<int2*>(__shfl_sync(0xffffffffu, reinterpret_cast<uintptr_t>(my_end), l + 1));
+                    int2* const endA = shfl_ptr(my_end, l);
+                    int2* const endB = shfl_ptr(my_end, l + 1);
                     if (!filter_checked(my_list, nq32, A, endA, lane)) bad = true;
                     if (!filter_checked(my_list, nq32, B, endB, lane)) bad = true;
                 }
