@@ -1,4 +1,4 @@
-// a1: endpoint key build with fused digit histograms.
+// a1: endpoint key build.
 // a2: LSD radix sort, 8-bit digits, per pass: tile digit histograms (upsweep),
 //     the (digit, tile) output bases -- for up to 1024 tiles computed inside
 //     the downsweep from group sums, else by one flat exclusive scan of the
@@ -24,24 +24,70 @@ namespace ddm {
 // ---------------------------------------------------------------------------
 constexpr int KB_BLOCK = 256;
 
+// Four consecutive regions of one set per thread: 16-byte loads and stores
+// where the quad is whole and the arrays line up, scalar accesses otherwise
+// (the ragged end of each set, caller arrays or output offsets that are not
+// 16-byte aligned).
+__device__ __forceinline__ void st_u32x4(uint32_t* p, const uint32_t (&v)[4]) {
+    *reinterpret_cast<uint4*>(p) = make_uint4(v[0], v[1], v[2], v[3]);
+}
+
 __global__ void __launch_bounds__(KB_BLOCK)
 k_keybuild_d0(const float* __restrict__ sub_lo, const float* __restrict__ sub_hi,
               const float* __restrict__ upd_lo, const float* __restrict__ upd_hi, int64_t n,
               int64_t m, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, DevStatus* st) {
     pdl_begin();
     const int64_t R = n + m;
+    const int64_t qs = (n + 3) >> 2, qall = qs + ((m + 3) >> 2);  // quads of subs, then of updates
     bool bad = false;
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < R;
-         r += (int64_t)gridDim.x * blockDim.x) {
-        const bool upd = r >= n;
-        const int64_t id = upd ? r - n : r;
-        const float lo = upd ? upd_lo[id] : sub_lo[id];
-        const float hi = upd ? upd_hi[id] : sub_hi[id];
-        bad |= is_nan_bits(lo) || is_nan_bits(hi) || !(lo <= hi);
-        keys[r] = float_key(lo);
-        keys[R + r] = float_key(hi);
-        vals[r] = payload(upd ? KIND_ULO : KIND_SLO, (uint32_t)id);
-        vals[R + r] = payload(upd ? KIND_UHI : KIND_SHI, (uint32_t)id);
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < qall;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const bool upd = q >= qs;
+        const int64_t id0 = (upd ? q - qs : q) << 2;
+        const int64_t left = (upd ? m : n) - id0;
+        const int c = left < 4 ? (int)left : 4;
+        const float* plo = (upd ? upd_lo : sub_lo) + id0;
+        const float* phi = (upd ? upd_hi : sub_hi) + id0;
+        float lo[4], hi[4];
+        const uintptr_t in_bits = reinterpret_cast<uintptr_t>(plo) | reinterpret_cast<uintptr_t>(phi);
+        if (c == 4 && (in_bits & 15u) == 0) {
+            const float4 a = *reinterpret_cast<const float4*>(plo);
+            const float4 b = *reinterpret_cast<const float4*>(phi);
+            lo[0] = a.x; lo[1] = a.y; lo[2] = a.z; lo[3] = a.w;
+            hi[0] = b.x; hi[1] = b.y; hi[2] = b.z; hi[3] = b.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                lo[k] = k < c ? plo[k] : 0.f;
+                hi[k] = k < c ? phi[k] : 0.f;
+            }
+        }
+        uint32_t kl[4], kh[4], vl[4], vh[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (k < c) bad |= is_nan_bits(lo[k]) || is_nan_bits(hi[k]) || !(lo[k] <= hi[k]);
+            kl[k] = float_key(lo[k]);
+            kh[k] = float_key(hi[k]);
+            vl[k] = payload(upd ? KIND_ULO : KIND_SLO, (uint32_t)(id0 + k));
+            vh[k] = payload(upd ? KIND_UHI : KIND_SHI, (uint32_t)(id0 + k));
+        }
+        const int64_t r = (upd ? n : 0) + id0;  // layout [S lo | U lo | S hi | U hi]
+        if (c == 4 && ((r | R) & 3) == 0) {     // keys and vals start 256-byte aligned
+            st_u32x4(keys + r, kl);
+            st_u32x4(keys + R + r, kh);
+            st_u32x4(vals + r, vl);
+            st_u32x4(vals + R + r, vh);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (k < c) {
+                    keys[r + k] = kl[k];
+                    keys[R + r + k] = kh[k];
+                    vals[r + k] = vl[k];
+                    vals[R + r + k] = vh[k];
+                }
+            }
+        }
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0) raise_error(st, DDM_ERR_INVALID, 1);
 }
@@ -51,7 +97,8 @@ int launch_keybuild_d0(const float* sub_lo, const float* sub_hi, const float* up
                        DevStatus* st, cudaStream_t s) {
     const int64_t R = n + m;
     if (R == 0) return 0;
-    int grid = (int)ceil_div((uint64_t)R, (uint64_t)KB_BLOCK * 4);
+    const uint64_t quads = (uint64_t)((n + 3) >> 2) + (uint64_t)((m + 3) >> 2);
+    int grid = (int)ceil_div(quads, (uint64_t)KB_BLOCK);
     grid = grid < 1 ? 1 : (grid > 152 * 16 ? 152 * 16 : grid);
     launch_k(k_keybuild_d0, grid, KB_BLOCK, 0, s, sub_lo, sub_hi, upd_lo, upd_hi, n, m, keys, vals, st);
     return 1;
