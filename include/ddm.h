@@ -213,9 +213,9 @@ int ddm_get_stats(const ddm_ctx *ctx, ddm_stats *out);
  * all of them, with no per-instance launches.  Instance b's pairs, with ids
  * local to instance b and sorted lexicographically, occupy pairs[2*o[b] ..
  * 2*o[b+1]) where o = inst_offsets, a HOST array of num + 1 values (o[0] = 0,
- * o[num] = K).  `pairs` is DEVICE memory for 2 * cap int32; with pairs == NULL
- * only the counts (inst_offsets and K) are computed.  Capacity rule as in
- * ddm_match.  Limits: 0 <= num <= DDM_MAX_BATCH; the instances' regions
+ * o[num] = K).  `pairs` is DEVICE memory for 2 * cap int32, 8-byte aligned
+ * (else DDM_ERR_INVALID); with pairs == NULL only the counts (inst_offsets and
+ * K) are computed.  Capacity rule as in ddm_match.  Limits: 0 <= num <= DDM_MAX_BATCH; the instances' regions
  * together obey DDM_MAX_REGIONS.  Synchronous.
  */
 #define DDM_MAX_BATCH (1 << 20)
@@ -239,8 +239,9 @@ int ddm_match_batch(ddm_ctx *ctx, int num, const ddm_regions *inst, int32_t *pai
  *   ddm_session_count    runs the pipeline up to the exact K (sort, sweep scan,
  *                        counts, offsets) and keeps that state; returns K.
  *   ddm_session_emit     after ddm_session_count: writes the K sorted pairs into
- *                        `pairs` (DEVICE, 2 * cap int32) from the kept state,
- *                        without sorting again.  K > cap -> DDM_ERR_CAPACITY.
+ *                        `pairs` (DEVICE, 2 * cap int32, 8-byte aligned) from
+ *                        the kept state, without sorting again.
+ *                        K > cap -> DDM_ERR_CAPACITY.
  *
  * Between count and emit a caller can reserve exactly 8 K bytes of output
  * (admission by memory).  Every call takes the CUDA stream to run on (NULL =
