@@ -77,9 +77,12 @@ typedef struct {
 /*
  * Creates a context on CUDA device `device`, bound to `cuda_stream` (a
  * cudaStream_t; NULL means the legacy default stream).  All of the context's
- * kernels run on that stream.  mem_budget_bytes caps the scratch memory the
- * context may hold (0 = no cap); scratch is kept between calls and grows on
- * demand.  Returns DDM_OK and *out, or an error code (then *out is NULL).
+ * kernels run on that stream.  mem_budget_bytes caps the device memory the
+ * context may hold (0 = no cap): its pipeline workspace and the staging
+ * buffers of ddm_match_host, together; scratch is kept between calls and
+ * grows on demand.  A call whose scratch would exceed the cap fails with
+ * DDM_ERR_NOMEM before any launch.  Returns DDM_OK and *out, or an error code
+ * (then *out is NULL).
  */
 int ddm_create(ddm_ctx **out, int device, void *cuda_stream, size_t mem_budget_bytes);
 
@@ -122,22 +125,26 @@ int ddm_match_host(ddm_ctx *ctx, const ddm_regions *regions, int32_t *pairs, uin
 /*
  * ddm_count without any allocation.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory -- code that
- * runs where cudaMalloc is unavailable or forbidden (a host callback, a
- * custom allocator that owns all device memory, a simulation loop that must
- * not allocate after start-up).  It needs no context: it runs on the CURRENT
- * device and on `cuda_stream` (NULL = legacy default stream), and returns the
- * same K as ddm_count for the same DEVICE coordinates.
+ * runs where cudaMalloc is unavailable or forbidden (a custom allocator that
+ * owns all device memory, a simulation loop that must not allocate after
+ * start-up, a process whose device memory is pinned down by other users).
+ * It needs no context: it runs on the CURRENT device and on `cuda_stream`
+ * (NULL = legacy default stream), and returns the same K as ddm_count for the
+ * same DEVICE coordinates.
  *
  * All scratch lives in one fixed 24 MiB __device__ array inside the library,
  * held by every GPU that loads the library until the process exits.  The call
  * makes no cudaMalloc/cudaFree and no other allocation.  Limit: n + m <=
- * DDM_NOALLOC_MAX_REGIONS; larger instances (and bad arguments) return
- * DDM_ERR_INVALID without touching the GPU.  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress); make that
- * first call before any stream capture.  All calls share the array: calls
- * that overlap on the GPU (two streams, two threads) race and give wrong
- * results, so serialise them.  Synchronous: returns after the stream has
- * finished the work.  Errors as for ddm_count.
+ * DDM_NOALLOC_MAX_REGIONS, for every d up to DDM_MAX_DIMS; larger instances
+ * (and bad arguments) return DDM_ERR_INVALID without touching the GPU.  Every
+ * call looks up the array's device address on the current device
+ * (cudaGetSymbolAddress, which allocates nothing), so no address is kept
+ * across calls.  All calls share the array: calls that overlap on the GPU
+ * (two streams, two threads) race and give wrong results, so serialise them.
+ * Synchronous: the call waits for its stream (cudaStreamSynchronize), so it
+ * must not be made from a host function running on a stream
+ * (cudaLaunchHostFunc, stream callbacks), where CUDA calls are not allowed.
+ * Errors as for ddm_count.
  */
 #define DDM_NOALLOC_MAX_REGIONS ((int64_t)1 << 17)
 int ddm_count_noalloc(const ddm_regions *regions, void *cuda_stream, uint64_t *K_out);
@@ -243,6 +250,11 @@ int ddm_match_batch(ddm_ctx *ctx, int num, const ddm_regions *inst, int32_t *pai
  *                        the kept state, without sorting again.
  *                        K > cap -> DDM_ERR_CAPACITY.
  *
+ * mem_budget_bytes (0 = no cap) caps ALL device memory the session holds:
+ * its resident coordinates, its pipeline workspace and the pair lists and
+ * offsets of ddm_session_emit_delta; a call that would exceed it fails with
+ * DDM_ERR_NOMEM (ddm_session_create too, if the coordinates alone exceed it).
+ *
  * Between count and emit a caller can reserve exactly 8 K bytes of output
  * (admission by memory).  Every call takes the CUDA stream to run on (NULL =
  * legacy default stream) and is synchronous.  A session must not be used by
@@ -299,6 +311,22 @@ int ddm_session_emit_delta(ddm_session *s, void *cuda_stream, int32_t *added, ui
 int ddm_debug_sweep(ddm_ctx *ctx, const ddm_regions *regions, uint32_t *sorted_who,
                     uint32_t *subset_size, uint32_t *updset_size, uint32_t *sub_count,
                     uint32_t *upd_count);
+
+/*
+ * Self-test of the bounded device-side waits (for tests).  Every wait in the
+ * library's kernels gives up after a bounded number of polls, records
+ * DDM_ERR_DEVICE_TIMEOUT and returns, so that a lost hand-off cannot hang the
+ * GPU.  This call runs one of those wait helpers against a hand-off that never
+ * happens, with at most `spin_limit` polls (1 .. 65536, a few milliseconds):
+ *   which = 0  the decoupled look-back of the scans, waiting for a
+ *              predecessor tile that never publishes;
+ *   which = 1  the mbarrier wait of the bulk copies, waiting for transaction
+ *              bytes that never arrive (no copy is issued).
+ * Expected result: DDM_ERR_DEVICE_TIMEOUT, with the context still usable for
+ * the next call.  DDM_ERR_INVALID for other `which` or limits.  Synchronous.
+ * The paper has no counterpart (its multicore algorithm has no device waits).
+ */
+int ddm_debug_wait_timeout(ddm_ctx *ctx, int which, uint32_t spin_limit);
 
 #ifdef __cplusplus
 }

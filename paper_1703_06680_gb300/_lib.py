@@ -89,6 +89,7 @@ SIGNATURES = {
     "ddm_session_emit_delta": (ctypes.c_int, [_P, _P, _P, ctypes.c_uint64, _P, ctypes.c_uint64,
                                               _U64P, _U64P]),
     "ddm_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(Stats)]),
+    "ddm_debug_wait_timeout": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_uint32]),
 }
 
 
@@ -348,6 +349,12 @@ class Context:
                                        ctypes.c_void_p(offs.ctypes.data), ctypes.byref(K))
         self._check(rc, K.value)
         return out[:K.value], offs
+
+    def debug_wait_timeout(self, which: int, spin_limit: int = 4096):
+        """ddm_debug_wait_timeout: runs a bounded device wait against a hand-off that
+        never comes (0 = look-back, 1 = mbarrier); raises DDMError (expected code
+        DDM_ERR_DEVICE_TIMEOUT)."""
+        self._check(self._lib.ddm_debug_wait_timeout(self._h, int(which), int(spin_limit)))
 
     def debug_sweep(self, sub_lo, sub_hi, upd_lo, upd_hi):
         """ddm_debug_sweep: (sorted_who, subset_size, updset_size, sub_count, upd_count)."""

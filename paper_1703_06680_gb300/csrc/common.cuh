@@ -128,7 +128,9 @@ __device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned l
 // Every device-side wait is bounded: after SPIN_LIMIT polls (with a growing
 // nanosleep back-off, well over a second in total) the waiter raises
 // DDM_ERR_DEVICE_TIMEOUT and proceeds with a neutral value, so a kernel can
-// never hang the GPU; the host then reports the error.
+// never hang the GPU; the host then reports the error.  The wait helpers take
+// the limit as an argument (SPIN_LIMIT unless given) so that the self-test of
+// ddm_debug_wait_timeout can run the same code out in milliseconds.
 constexpr uint32_t SPIN_LIMIT = 1u << 21;
 
 __device__ __forceinline__ void backoff(uint32_t iter) {
@@ -154,7 +156,8 @@ __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long
 // pipelined; the publisher's release store makes the word visible whole.
 __device__ __forceinline__ unsigned long long warp_lookback_u64(unsigned long long* status,
                                                                 long long tile, DevStatus* st,
-                                                                int where) {
+                                                                int where,
+                                                                uint32_t limit = SPIN_LIMIT) {
     const int lane = threadIdx.x & 31;
     unsigned long long sum = 0;
     long long p = tile - 1;
@@ -170,7 +173,7 @@ __device__ __forceinline__ unsigned long long warp_lookback_u64(unsigned long lo
             const long long q = p - (j * 32 + lane);
             uint32_t it = 0;
             while (v[j] == 0ull) {  // not yet published: wait (bounded)
-                if (++it > SPIN_LIMIT) {
+                if (++it > limit) {
                     raise_error(st, DDM_ERR_DEVICE_TIMEOUT, where);
                     v[j] = LB64_INC;
                     break;
@@ -242,13 +245,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 // raised and the wait continues (bounded again) so that no copy is still in
 // flight into shared memory when the block leaves; returns false on timeout.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, DevStatus* st,
-                                                  int where) {
-    for (uint32_t it = 0; it < SPIN_LIMIT; ++it) {
+                                                  int where, uint32_t limit = SPIN_LIMIT) {
+    for (uint32_t it = 0; it < limit; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
         if (it > 16) __nanosleep(64);
     }
     raise_error(st, DDM_ERR_DEVICE_TIMEOUT, where);
-    for (uint32_t it = 0; it < SPIN_LIMIT; ++it) {
+    for (uint32_t it = 0; it < limit; ++it) {
         if (mbar_try_wait(bar, parity)) break;
         __nanosleep(1024);
     }

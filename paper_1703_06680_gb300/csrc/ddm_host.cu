@@ -21,12 +21,15 @@ using namespace ddm;
 
 namespace ddm {
 thread_local bool g_pdl = false;
+int launch_wait_selftest(int which, uint32_t limit, unsigned long long* status, DevStatus* st,
+                         cudaStream_t s);
 }
 
 struct ddm_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     size_t budget = 0;
+    size_t held = 0;  // device bytes held by ensure() buffers and session coordinates
     std::string err;
     char* ws = nullptr;
     size_t ws_size = 0;
@@ -91,18 +94,24 @@ struct Carve {
     }
 };
 
+// Grows one of the context's device buffers (*buf, *size) to hold `need`
+// bytes.  c->held counts every byte the context (and its session, if any)
+// holds on the device, so the budget covers all of them together.
 int ensure(ddm_ctx* c, char** buf, size_t* size, size_t need) {
     if (need <= *size) return DDM_OK;
-    const size_t total_other = c->ws_size + c->io_size + c->out_size - *size;
-    if (c->budget && need + total_other > c->budget)
-        return fail(c, DDM_ERR_NOMEM, "scratch need " + std::to_string(need) +
-                                          " bytes exceeds the context budget");
+    const size_t other = c->held - *size;  // held includes this buffer's current size
+    if (c->budget && (other > c->budget || need > c->budget - other))
+        return fail(c, DDM_ERR_NOMEM, "device memory need of " + std::to_string(need) +
+                                          " bytes exceeds the context budget (" +
+                                          std::to_string(other) + " bytes held elsewhere)");
     if (*buf) {
         cudaFree(*buf);
+        c->held -= *size;
         *buf = nullptr;
         *size = 0;
     }
     size_t grow = need + need / 8;
+    if (c->budget && grow > c->budget - other) grow = c->budget - other;  // >= need (checked)
     cudaError_t e = cudaMalloc(buf, grow);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -115,6 +124,7 @@ int ensure(ddm_ctx* c, char** buf, size_t* size, size_t need) {
         return fail(c, DDM_ERR_NOMEM, "cudaMalloc of " + std::to_string(need) + " bytes failed");
     }
     *size = grow;
+    c->held += grow;
     return DDM_OK;
 }
 
@@ -839,12 +849,18 @@ int ddm_session_create(ddm_session** out, int device, const ddm_regions* initial
     const int d = initial->d;
     const int64_t n = initial->n, m = initial->m;
     const size_t floats = (size_t)2 * d * (n + m);
+    if (c->budget && floats * sizeof(float) > c->budget) {
+        ddm_destroy(c);
+        delete s;
+        return DDM_ERR_NOMEM;
+    }
     if (floats > 0 && cudaMalloc(&s->coords, floats * sizeof(float)) != cudaSuccess) {
         cudaGetLastError();
         ddm_destroy(c);
         delete s;
         return DDM_ERR_NOMEM;
     }
+    c->held += floats * sizeof(float);  // the resident coordinates count against the budget
     const float* const* src[4] = {initial->sub_lo, initial->sub_hi, initial->upd_lo, initial->upd_hi};
     float* p = s->coords;
     for (int a = 0; a < 4; ++a) {
@@ -1086,6 +1102,22 @@ int ddm_session_emit_delta(ddm_session* s, void* stream, int32_t* added, uint64_
     s->K_ref = s->K_new;
     s->pending = false;
     return DDM_OK;
+}
+
+int ddm_debug_wait_timeout(ddm_ctx* c, int which, uint32_t spin_limit) {
+    if (!c) return DDM_ERR_INVALID;
+    if (which < 0 || which > 1) return fail(c, DDM_ERR_INVALID, "which must be 0 or 1");
+    if (spin_limit < 1 || spin_limit > (1u << 16))
+        return fail(c, DDM_ERR_INVALID, "spin_limit must be 1 .. 65536");
+    DeviceGuard g(c->device);
+    // The status block is cleared first; its aux[0] word (zero) is the
+    // look-back word that never gets published.
+    CK(cudaMemsetAsync(c->dstat, 0, sizeof(DevStatus), c->stream));
+    PdlScope pdl_scope(c->pdl);
+    c->stats.launches += launch_wait_selftest(which, spin_limit, &c->dstat->aux[0], c->dstat,
+                                              c->stream);
+    CK(cudaGetLastError());
+    return finish(c, nullptr);
 }
 
 int ddm_debug_sweep(ddm_ctx* c, const ddm_regions* r, uint32_t* sorted_who,

@@ -1,19 +1,18 @@
 // ddm_count_noalloc: the count of ddm_count for callers that cannot allocate
 // device memory -- code running where cudaMalloc is unavailable or forbidden,
-// such as inside a host callback, under a custom allocator that owns all
-// device memory, or in a real-time simulation loop that must not allocate
-// after start-up.  Every scratch buffer of the count pipeline (sort keys and
-// values, scan status words, rank records, counts, offsets, status word) is
-// carved from one file-scope __device__ array of fixed size, so the call
-// itself allocates nothing: no cudaMalloc, no cudaFree, no pinned host buffer.
+// such as under a custom allocator that owns all device memory, or in a
+// real-time simulation loop that must not allocate after start-up.  Every
+// scratch buffer of the count pipeline (sort keys and values, scan status
+// words, rank records, counts, offsets, status word) is carved from one
+// file-scope __device__ array of fixed size, so the call itself allocates
+// nothing: no cudaMalloc, no cudaFree, no pinned host buffer.
 //
 // The array is held by every GPU that loads this library, until the process
 // exits.  All calls share it and it keeps the last call's contents, so every
 // call first clears the parts that must start at zero, and calls that overlap
 // on the GPU (on two streams, or from two threads) race and give wrong
-// results; serialise them.
-#include <mutex>
-
+// results; serialise them.  The call synchronizes its stream before it
+// returns, so it cannot run inside a host function enqueued on a stream.
 #include "emit.cuh"
 #include "sort.cuh"
 #include "sweep.cuh"
@@ -24,27 +23,21 @@ namespace {
 
 constexpr int64_t NOALLOC_MAX_REGIONS = int64_t(1) << 17;  // n + m of one instance
 constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(24) << 20;  // 24 MiB per GPU
-constexpr int NOALLOC_MAX_DEVICES = 64;
+static_assert(NOALLOC_MAX_REGIONS == DDM_NOALLOC_MAX_REGIONS, "header and library agree");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
 // In host code g_noalloc_scratch names a host-side stand-in, not device
-// memory: the device address is looked up once per device, with that device
-// current, and cached here.
-std::mutex g_noalloc_mu;
-void* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
-
-int noalloc_scratch(int device, char** out) {
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[device]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-            cudaGetLastError();
-            return DDM_ERR_CUDA;
-        }
-        g_noalloc_addr[device] = p;
+// memory.  The device address is looked up on every call, with the caller's
+// device current: the lookup allocates nothing, and no address is cached that
+// a cudaDeviceReset or another context on the same device would make stale.
+int noalloc_scratch(char** out) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return DDM_ERR_CUDA;
     }
-    *out = static_cast<char*>(g_noalloc_addr[device]);
+    *out = static_cast<char*>(p);
     return DDM_OK;
 }
 
@@ -125,13 +118,8 @@ extern "C" int ddm_count_noalloc(const ddm_regions* r, void* cuda_stream, uint64
     NoallocLayout L;
     L.carve(nullptr, r->d, r->n, r->m);
     if (L.total > NOALLOC_SCRATCH_BYTES) return DDM_ERR_INVALID;
-    int device = 0;
-    if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= NOALLOC_MAX_DEVICES) {
-        cudaGetLastError();
-        return DDM_ERR_CUDA;
-    }
     char* base = nullptr;
-    int rc = noalloc_scratch(device, &base);
+    int rc = noalloc_scratch(&base);
     if (rc) return rc;
     L.carve(base, r->d, r->n, r->m);
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);

@@ -152,17 +152,20 @@ def batch_sizes(num: int = 4096, replica: int = 0, lo: float = 100.0,
     return np.maximum(N, 2)
 
 
+def batch_instance(k: int, sizes: np.ndarray, replica: int = 0, d: int = 2,
+                   alpha: float = 1.0) -> Regions:
+    """Instance k of the batch: n_k = floor(N_k / 2) subs, m_k = N_k - n_k updates."""
+    N = int(sizes[k])
+    n = N // 2
+    return make_regions(d, n, N - n, side_for(alpha, N, d), seed_for(3, replica) + 7919 * (k + 1))
+
+
 def batch_instances(num: int = 4096, replica: int = 0, d: int = 2, alpha: float = 1.0,
                     sizes: np.ndarray | None = None) -> list[Regions]:
     """Independent instances: n_i = floor(N_i / 2) subs, m_i = N_i - n_i updates."""
     if sizes is None:
         sizes = batch_sizes(num, replica)
-    base = seed_for(3, replica)
-    out = []
-    for k, N in enumerate(sizes.tolist()):
-        n = N // 2
-        out.append(make_regions(d, n, N - n, side_for(alpha, N, d), base + 7919 * (k + 1)))
-    return out
+    return [batch_instance(k, sizes, replica, d, alpha) for k in range(len(sizes))]
 
 
 # ----------------------------------------------------------------------------

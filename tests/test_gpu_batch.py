@@ -73,12 +73,18 @@ def test_batch_capacity(ctx):
     assert e.value.K == int(offs[-1])
 
 
-def test_batch_full_size_sampled(ctx):
-    # the 4096-instance workload (d=2, alpha=1, N_i log-uniform in [1e2, 1e5])
+def test_batch_full_size_every_instance(ctx):
+    # The 4096-instance workload (d=2, alpha=1, N_i log-uniform in [1e2, 1e5]):
+    # every instance's pair list compared whole with the oracle's (oracle runs
+    # spread over the host cores in a spawn pool).
+    from tests.oracle_pool import check_batch as pool_check
     regs = synth.batch_instances(num=4096, d=2)
-    rng = np.random.default_rng(4096)
-    sample = sorted(rng.choice(4096, size=24, replace=False).tolist())
-    check_batch(ctx, regs, sample=sample)
+    insts = [to_dev(r) for r in regs]
+    del regs
+    pairs, offs = ctx.match_batch(insts)
+    assert pool_check(pairs, offs.astype(np.int64), 4096, d=2, alpha=1.0) == len(pairs)
+    _, offs2 = ctx.match_batch(insts, count_only=True)
+    assert np.array_equal(offs, offs2)
 
 
 @pytest.mark.parametrize("d", [1, 2])

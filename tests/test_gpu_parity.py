@@ -1,16 +1,16 @@
 """GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
 
 Results are integer pair lists, so the bar is bit-exact equality of the
-sorted (sub, upd) lists.  Full-size workloads are compared in full where the
-oracle finishes in seconds, and on sampled subscriptions (oracle brute force
-row by row) plus exact properties where it does not.
+sorted (sub, upd) lists.  Every workload is compared in full: where the serial
+oracle takes minutes, it runs on subscription slices in a pool of host
+processes (tests/oracle_pool.py), each slice checked against its rows.
 """
 import numpy as np
 import pytest
 
 import oracle
 import synth
-from tests.gpu_util import gpu_pairs, oracle_row, segment_of, to_dev
+from tests.gpu_util import gpu_pairs, to_dev
 from tests.helpers import special_value_instance, tiny_grid_instance
 
 pytestmark = pytest.mark.gpu
@@ -56,22 +56,20 @@ def test_d2_alpha1_full_size(ctx):
 
 
 @pytest.mark.parametrize("d,alpha", [(2, 100.0), (3, 1.0), (3, 100.0)])
-def test_nd_full_size_sampled(ctx, d, alpha):
+def test_nd_full_size_complete(ctx, d, alpha):
+    # N = 1e6 at d = 2 and 3: the complete sorted pair list (up to 1.9e8 pairs)
+    # against the oracle, run on 64 subscription slices x all updates in a spawn
+    # pool; the slices' oracle counts add up to the whole instance's K.
     import torch
+    from tests.oracle_pool import check_full
     reg = synth.large_nd(d, alpha)
     t = to_dev(reg)
     K = ctx.count(*t)
     pairs = ctx.match(*t, cap=K)
     assert pairs.shape[0] == K
-    # lexicographically sorted, no duplicates
-    key = pairs[:, 0].long() * (1 << 32) + pairs[:, 1].long()
-    assert bool((key[1:] > key[:-1]).all())
+    assert check_full(pairs, ("large_nd", (d, alpha)), reg.n) == K
     # swapping the roles of S and U gives the same count
     assert ctx.count(t[2], t[3], t[0], t[1]) == K
-    # per-subscription rows against the oracle's brute force
-    rng = np.random.default_rng(d * 1000 + int(alpha))
-    for i in rng.choice(reg.n, size=48, replace=False).tolist():
-        assert np.array_equal(segment_of(pairs, i), oracle_row(reg, i)), i
     del pairs
     torch.cuda.empty_cache()
 
@@ -364,3 +362,25 @@ def test_misaligned_pairs_rejected(ctx):
     with pytest.raises(ddm.DDMError):
         ctx.match_into(buf[1:].view(K, 2), *t)
     assert_parity(ctx, reg)
+
+
+# --- fault handling: a bounded device wait that runs out ------------------------------
+
+@pytest.mark.parametrize("which", [0, 1], ids=["lookback", "mbarrier"])
+def test_bounded_wait_times_out_and_context_survives(which):
+    # The look-back poll and the mbarrier wait, run against a hand-off that never
+    # happens with a short limit: the kernel returns, the host reads
+    # DDM_ERR_DEVICE_TIMEOUT, and the same context then gives the oracle's result.
+    import paper_1703_06680_gb300 as ddm
+    reg = synth.small_1d()
+    want = oracle.sbm(reg)
+    with ddm.Context(0) as c:
+        for _ in range(2):
+            with pytest.raises(ddm.DDMError) as e:
+                c.debug_wait_timeout(which, 4096)
+            assert e.value.code == ddm._lib.DDM_ERR_DEVICE_TIMEOUT
+            assert "timed out" in str(e.value)
+            assert np.array_equal(gpu_pairs(c, reg), want)
+        with pytest.raises(ddm.DDMError) as e:
+            c.debug_wait_timeout(2, 16)
+        assert e.value.code == ddm._lib.DDM_ERR_INVALID

@@ -187,3 +187,30 @@ def test_emit_delta_no_motion_and_capacity_retry(ddm):
     assert np.array_equal(added.cpu().numpy(), _rows_minus(want, want_prev))
     assert np.array_equal(removed.cpu().numpy(), _rows_minus(want_prev, want))
     sess.close()
+
+
+def test_session_budget_covers_change_report_lists(ddm):
+    # A session's budget caps everything it holds on the device: the resident
+    # coordinates, the pipeline workspace and the two pair lists of the change
+    # report (8 K bytes each).  With room for the first two but not the lists,
+    # emit_delta fails with DDM_ERR_NOMEM before any launch, count and emit
+    # still work, and an oversized coordinate set is refused at creation.
+    import torch
+    reg = synth.large_1d(100.0, N=200_000)          # K ~ 1e7: one list is ~80 MB
+    want = oracle.sbm(reg)
+    sess = ddm.Session(*to_dev(reg), mem_budget=64 << 20)
+    try:
+        K = sess.count()
+        assert K == len(want)
+        with pytest.raises(ddm.DDMError) as e:
+            sess.emit_delta()
+        assert e.value.code == ddm._lib.DDM_ERR_NOMEM
+        sess.count()
+        out = torch.empty((K, 2), dtype=torch.int32, device="cuda:0")
+        assert sess.emit(out) == K
+        assert np.array_equal(out.cpu().numpy(), want)
+    finally:
+        sess.close()
+    with pytest.raises(ddm.DDMError) as e:
+        ddm.Session(*to_dev(reg), mem_budget=1 << 20)  # 1.6 MB of coordinates
+    assert e.value.code == ddm._lib.DDM_ERR_NOMEM
