@@ -188,6 +188,10 @@ struct Plan {
     uint32_t num_win;
     uint32_t* lw_fill;
     uint32_t* num_flagged;
+    unsigned long long* cand_fill;
+    uint4* wmeta;
+    uint2* wcand;
+    unsigned long long cand_cap;
     unsigned long long* lw_total;
     unsigned long long* win_status;
     size_t zero_bytes;
@@ -235,20 +239,30 @@ struct Plan {
         join = d > 1 && mode != Mode::Debug && nd_path != 2;
         const bool lists = window || join;
         win_shift = join ? 11 : win_shift_;
-        lcap = join ? 0xffffffffu : 1024u;
+        // Window path: list w lives in a fixed slot of 2^win_shift entries at
+        // w << win_shift (no offsets scan); longer lists overflow to the range
+        // path.  Tiled join: lists of any length, placed by an offsets scan.
+        lcap = join ? 0xffffffffu : (1u << win_shift);
         num_win = lists ? (uint32_t)ceil_div(E, 1ull << win_shift) : 0;
         lw_fill = cv.take<uint32_t>(num_win);
         num_flagged = cv.take<uint32_t>(1);
+        cand_fill = cv.take<unsigned long long>(1);
         lw_total = cv.take<unsigned long long>(1);
         win_status = cv.take<unsigned long long>(lists ? ceil_div(num_win, OFF_TILE) + 2 : 0);
         zero_bytes = (cv.off + 255) & ~(size_t)255;
         windows = cv.take<uint4>(lists ? num_win + 1 : 0);
-        lw_off = cv.take<unsigned long long>(lists ? num_win + 1 : 0);
-        if (window) lw_cap = (unsigned long long)E + 4096;
+        lw_off = cv.take<unsigned long long>(join ? num_win + 1 : 0);
+        if (window) lw_cap = (unsigned long long)num_win << win_shift;
         else if (join) lw_cap = std::min<unsigned long long>(
             std::max<unsigned long long>(16ull * E, 16ull << 20), 64ull << 20);
         else lw_cap = 0;
         lw = cv.take<uint4>(lw_cap);
+        // Window path: the id-sorted candidates of every window (about 360 per
+        // window of 1024 positions at alpha = 100; windows that find no room
+        // go to the range path).
+        cand_cap = window ? 2 * (unsigned long long)E + 4096 : 0;
+        wcand = cv.take<uint2>(cand_cap);
+        wmeta = cv.take<uint4>(window ? num_win : 0);
         urank = cv.take<uint4>(lists ? m : 0);
         srank = cv.take<uint4>(window ? n : 0);
         soff = cv.take<unsigned long long>(window ? n : 0);
@@ -400,12 +414,16 @@ int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
         a.windows = pl.windows;
         a.win_shift = pl.win_shift;
         a.num_win = pl.num_win;
-        a.lw_off = pl.lw_off;
+        a.lw_off = pl.join ? pl.lw_off : nullptr;  // NULL: fixed slots
         a.lw_fill = pl.lw_fill;
         a.lw = pl.lw;
         a.urank = pl.urank;
         a.srank = pl.window ? pl.srank : nullptr;
         a.soff = pl.soff;
+        a.wmeta = pl.window ? pl.wmeta : nullptr;
+        a.wcand = pl.window ? pl.wcand : nullptr;
+        a.cand_fill = pl.cand_fill;
+        a.cand_cap = pl.cand_cap;
         a.lw_cap = pl.lw_cap;
     }
     a.vals = vals_sorted;
@@ -471,9 +489,8 @@ int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
   if (do_suffix) {
     mark(c, 5);
     if (pl.window) {
-        L += launch_window_offsets(pl.windows, pl.num_win, pl.lcap, pl.lw_off, pl.lw_total,
-                                   pl.win_status, c->dstat, s);
         L += launch_tile_active(a, c->dstat, s);
+        L += launch_win_setup(a, c->dstat, s);
     }
     mark(c, 6);
     if (pl.window) L += launch_emit_window(a, c->dstat, s);

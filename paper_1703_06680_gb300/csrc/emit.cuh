@@ -44,23 +44,35 @@ struct EmitArgs {
     int win_shift;
     uint32_t num_win;
     unsigned long long* lw_off;     // list offsets (exclusive scan of the capped list sizes,
-                                    // 0 for a list over lcap), numWin + 1
+                                    // 0 for a list over lcap), numWin + 1; NULL: list w
+                                    // has the fixed slot [w * lcap, (w + 1) * lcap)
     uint32_t* lw_fill;              // per-window fill cursor (zeroed)
     uint4* lw;                      // list storage {id, pos(U.hi), rank, 0}, lw_cap entries
     uint32_t lcap;                  // longest boundary list a window may use
     uint4* urank;                   // {id, pos(lo), pos(hi), 0} by lower-endpoint rank, m
     uint4* srank;                   // window path: {id, pos(lo), pos(hi), cnt} by rank, n (or NULL)
     unsigned long long* soff;       // window path: segment offset by rank, n
+    uint4* wmeta;                   // window path: {r0, ns, |W|, first wcand entry} per window
+                                    // (ns = 0: skip), numWin
+    uint2* wcand;                   // window path: id-sorted packed candidates, cand_cap entries
+    unsigned long long* cand_fill;  // window path: entries of wcand reserved so far (zeroed)
+    unsigned long long cand_cap;
     unsigned long long lw_cap;
     const uint32_t* vals;           // sorted endpoint stream (payloads)
     bool sort_all;                  // segment sort every subscription, not only flagged ones
 };
+
+// First entry of window w's boundary list.
+__device__ __forceinline__ unsigned long long list_base(const EmitArgs& a, uint32_t w) {
+    return a.lw_off ? a.lw_off[w] : (unsigned long long)w * a.lcap;
+}
 
 // d > 1: tiled join of windows of subscriptions with chunks of candidates.
 int launch_join(const EmitArgs& a, bool write, DevStatus* st, cudaStream_t s);
 
 // Window path for d = 1.
 int launch_tile_active(const EmitArgs& a, DevStatus* st, cudaStream_t s);
+int launch_win_setup(const EmitArgs& a, DevStatus* st, cudaStream_t s);
 int launch_emit_window(const EmitArgs& a, DevStatus* st, cudaStream_t s);
 
 // d > 1: permute keys of dims 1..d-1 into sub_order / upd_order layout and

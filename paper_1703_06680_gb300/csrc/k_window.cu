@@ -36,7 +36,8 @@ namespace ddm {
 
 constexpr int WIN_BLOCK = 256;        // eight warps per window
 constexpr int WIN_WARPS = WIN_BLOCK / 32;
-// The longest boundary list a window may use is a.lcap (1024 on this path).
+// The longest boundary list a window may use is a.lcap = 2^win_shift on this
+// path: list w has the fixed slot [w * lcap, (w + 1) * lcap) of the storage.
 constexpr uint32_t WCAP = 1024;       // candidates per window
 constexpr uint32_t LONG_SPAN = 512;   // positions; longer subscriptions use the range path
 constexpr int MAX_WIN_SHIFT = 10;     // windows of at most 1024 positions
@@ -51,17 +52,12 @@ constexpr uint32_t LCAP_W = 512;      // entries of a warp's candidate list (lon
 constexpr uint32_t REL_MAX = 0xffffu;
 static_assert((1u << MAX_WIN_SHIFT) + LONG_SPAN < REL_MAX, "relative positions fit 16 bits");
 
-// Dynamic shared memory of k_emit_window.  The per-warp candidate lists
-// overlay the raw candidate array of the set-up.
-constexpr size_t WSM_RAW = (size_t)WCAP * 16;
-constexpr size_t WSM_LIST = (size_t)WIN_WARPS * (LCAP_W + 32) * 8;
-constexpr size_t WSM_A = ((WSM_RAW > WSM_LIST ? WSM_RAW : WSM_LIST) + 15) & ~(size_t)15;
-constexpr size_t WSM_CAND = (size_t)WCAP * 8;
-constexpr size_t WSM_BYB = (size_t)WCAP * 4;
-constexpr size_t WSM_TOTAL = WSM_A + WSM_CAND + WSM_BYB;
+// Dynamic shared memory of k_emit_window (at most): the per-warp candidate
+// lists, then the window's candidates.
+constexpr size_t WSM_TOTAL = (size_t)WIN_WARPS * (LCAP_W + 32) * 8 + (size_t)WCAP * 8;
 
 __device__ __forceinline__ bool list_fits(const EmitArgs& a, uint32_t w, uint32_t s) {
-    return s <= a.lcap && a.lw_off[w] + s <= a.lw_cap;
+    return s <= a.lcap && list_base(a, w) + s <= a.lw_cap;
 }
 
 // One pass over the updates in lower-endpoint order (rank r, id = upd_order[r]):
@@ -136,7 +132,7 @@ __global__ void k_tile_active(EmitArgs a, DevStatus* st, unsigned gu) {
             base = __shfl_sync(0xffffffffu, base, leader);
             if (mine) {
                 const uint32_t slot = base + __popc(mask & lt);
-                if (slot < s) a.lw[a.lw_off[w] + slot] = make_uint4(j, ph, (uint32_t)r, 0u);
+                if (slot < s) a.lw[list_base(a, w) + slot] = make_uint4(j, ph, (uint32_t)r, 0u);
                 else raise_error(st, DDM_ERR_INTERNAL, 10);
             }
         }
@@ -197,33 +193,43 @@ __device__ __forceinline__ int2* shfl_ptr(int2* p, int l) {
     return reinterpret_cast<int2*>(__shfl_sync(0xffffffffu, reinterpret_cast<uintptr_t>(p), l));
 }
 
-template <bool BATCHED>
-__global__ void __launch_bounds__(WIN_BLOCK, 4) k_emit_window(EmitArgs a, DevStatus* st) {
+// Emission set-up of window w (one block per window): the candidate set W of
+// the window's subscriptions, sorted by update id, packed as 8-byte entries
+// {update id, (hi << 16) | lo} (positions relative to the window start) into
+// a reserved run of wcand, and the window's descriptor
+// wmeta[w] = {r0, ns, |W|, first entry in wcand}; ns = 0 tells the filter
+// kernel to skip the window (no subscription starts in it, or all of them go
+// to the range path).  Also writes every subscription's flag (1 = range path)
+// and counts the flagged ones.  Kept apart from the filter so that the
+// latency of these dependent loads and the id sort does not hold the filter's
+// block slots: the filter kernel starts writing pairs after one load round.
+__global__ void __launch_bounds__(WIN_BLOCK) k_win_setup(EmitArgs a, DevStatus* st) {
     pdl_begin();
-    extern __shared__ __align__(16) unsigned char wsm[];
-    uint4* const raw = reinterpret_cast<uint4*>(wsm);                 // set-up: {id, lo, hi, rank}
-    uint2* const lists = reinterpret_cast<uint2*>(wsm);               // filter: per-warp lists
-    uint2* const cand = reinterpret_cast<uint2*>(wsm + WSM_A);        // packed candidates by id
-    uint32_t* const byb = reinterpret_cast<uint32_t*>(wsm + WSM_A + WSM_CAND);  // ids by bucket
+    __shared__ uint4 raw[WCAP];                    // {id, lo, hi, arrival rank in bucket}
+    __shared__ uint32_t byb[WCAP];                 // ids by bucket
     __shared__ uint32_t bcnt[NBUCKET], bstart[NBUCKET], warp_tmp[WIN_WARPS];
-    __shared__ uint32_t s_pmax, s_nlow;
+    __shared__ uint32_t s_pmax, s_nlow, s_base;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const unsigned lt = (1u << lane) - 1u;
     const uint32_t w = blockIdx.x;
     const int S = a.win_shift;
     const uint32_t wT = w << S;  // the window's first stream position
-    // Every global read of the set-up is issued in two dependent rounds.
-    // Round 1: the window's counters, the list offset, and the counters at the
-    // farthest boundary a regular subscription of this window can reach (it
-    // starts before (w+1)T and spans at most LONG_SPAN positions).
+    // An earlier stage's error leaves the counters meaningless: no read below
+    // (the filter kernel checks the error too).
+    if (read_error(st)) return;
+    // Every global read is issued in two dependent rounds.  Round 1: the
+    // window's counters, and the counters at the farthest boundary a regular
+    // subscription of this window can reach (it starts before (w+1)T and spans
+    // at most LONG_SPAN positions).
     const uint32_t reach = (LONG_SPAN + (1u << S) - 1u) >> S;
     const uint32_t wl = min(w + 1 + reach, a.num_win);
     const uint4 t0 = a.windows[w], t1 = a.windows[w + 1];
     const uint32_t u_lim = a.windows[wl].y;
-    const unsigned long long lwo = a.lw_off[w];
-    // An earlier stage's error leaves the counters meaningless: no read below.
-    const uint32_t ns = read_error(st) ? 0u : t1.x - t0.x;  // subscriptions starting here
-    if (ns == 0) return;
+    const unsigned long long lwo = list_base(a, w);
+    const uint32_t ns = t1.x - t0.x;  // subscriptions starting here
+    if (ns == 0) {
+        if (tid == 0) a.wmeta[w] = make_uint4(0u, 0u, 0u, 0u);
+        return;
+    }
     const uint32_t r0 = t0.x, u0 = t0.y, lw_n = t0.y - t0.z;
     const bool lfit = lw_n <= a.lcap && lwo + lw_n <= a.lw_cap;
     // Candidate k of W is list entry k for k < lw_n, else rank entry
@@ -293,7 +299,16 @@ __global__ void __launch_bounds__(WIN_BLOCK, 4) k_emit_window(EmitArgs a, DevSta
     // qualify and more exist, W may exceed WCAP (treated as an overflow).
     const uint32_t room = WCAP - min(lw_n, WCAP);
     const bool clipped = nspec > room && nlow == room;
-    if (!lfit || W > WCAP || clipped) {
+    bool overflow = !lfit || W > WCAP || clipped;
+    if (!overflow) {  // a run of wcand for the packed candidates
+        if (tid == 0) {
+            const unsigned long long b = atomicAdd(a.cand_fill, (unsigned long long)W);
+            s_base = b + W <= a.cand_cap ? (uint32_t)b : 0xffffffffu;
+        }
+        __syncthreads();
+        overflow = s_base == 0xffffffffu;
+    }
+    if (overflow) {
         // The whole window goes to the range path.
         uint32_t nreg = 0;
         for (uint32_t k = tid; k < ns; k += WIN_BLOCK) {
@@ -302,8 +317,10 @@ __global__ void __launch_bounds__(WIN_BLOCK, 4) k_emit_window(EmitArgs a, DevSta
         }
         nreg = __reduce_add_sync(0xffffffffu, nreg);
         if (lane == 0 && nreg) atomicAdd(a.num_flagged, nreg);
+        if (tid == 0) a.wmeta[w] = make_uint4(r0, 0u, 0u, 0u);
         return;
     }
+    const uint32_t base = s_base;
 
     // W sorted by id: bucket sort on the high id bits (bucket starts by a
     // block scan, arrival rank in the bucket by a shared atomic), then the
@@ -334,6 +351,7 @@ __global__ void __launch_bounds__(WIN_BLOCK, 4) k_emit_window(EmitArgs a, DevSta
         byb[bstart[e.x >> bshift] + e.w] = e.x;
     }
     __syncthreads();
+    uint2* const cand = a.wcand + base;
     for (uint32_t k = tid; k < W; k += WIN_BLOCK) {
         const uint4 e = raw[k];
         const uint32_t b = e.x >> bshift, s0 = bstart[b], c = bcnt[b];
@@ -344,6 +362,34 @@ __global__ void __launch_bounds__(WIN_BLOCK, 4) k_emit_window(EmitArgs a, DevSta
         const uint32_t hi = min(e.z - wT, REL_MAX);
         cand[f] = make_uint2(e.x, (hi << 16) | lo);
     }
+    if (tid == 0) a.wmeta[w] = make_uint4(r0, ns, W, base);
+}
+
+// Pair emission of window w: warp g takes subscriptions 32g .. 32g+31 (by
+// lower endpoint) and filters the window's candidates, prepared by
+// k_win_setup, for them.
+template <bool BATCHED>
+__global__ void __launch_bounds__(WIN_BLOCK, 4) k_emit_window(EmitArgs a, DevStatus* st) {
+    pdl_begin();
+    extern __shared__ __align__(16) unsigned char wsm[];
+    uint2* const lists = reinterpret_cast<uint2*>(wsm);             // per-warp candidate lists
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t nwarps = blockDim.x >> 5;  // one warp per 128 window positions
+    uint2* const cand = reinterpret_cast<uint2*>(wsm + (size_t)nwarps * (LCAP_W + 32) * 8);
+    const unsigned lt = (1u << lane) - 1u;
+    const uint32_t w = blockIdx.x;
+    const uint32_t wT = w << a.win_shift;  // the window's first stream position
+    if (read_error(st)) return;
+    const uint4 md = a.wmeta[w];
+    const uint32_t r0 = md.x, ns = md.y, W = md.z;
+    if (ns == 0) return;
+    // One load round: the candidates into shared memory, and the entries of
+    // this thread's subscription in its warp's first group (k = tid).
+    const uint2* const gcand = a.wcand + md.w;
+    uint4 e_first = make_uint4(0u, 0u, 0u, 0u);
+    unsigned long long off_first = 0;
+    if ((uint32_t)tid < ns) { e_first = a.srank[r0 + tid]; off_first = a.soff[r0 + tid]; }
+    for (uint32_t k = tid; k < W; k += blockDim.x) cand[k] = __ldg(gcand + k);
     __syncthreads();
 
     // Filter: warp g takes subscriptions 32g .. 32g+31 (by lower endpoint).
@@ -351,11 +397,12 @@ __global__ void __launch_bounds__(WIN_BLOCK, 4) k_emit_window(EmitArgs a, DevSta
     const uint32_t Wr = (W + 31) & ~31u;
     int2* const pairs = reinterpret_cast<int2*>(a.pairs);
     bool bad = false;
-    for (uint32_t g = warp; g * 32 < ns; g += WIN_WARPS) {
+    for (uint32_t g = warp; g * 32 < ns; g += nwarps) {
         const uint32_t k = g * 32 + lane;
         uint4 e = make_uint4(0u, 0u, 0u, 0u);
         unsigned long long off = 0;
-        if (k < ns) { e = a.srank[r0 + k]; off = a.soff[r0 + k]; }
+        if (g == (uint32_t)warp) { e = e_first; off = off_first; }  // zero when k >= ns
+        else if (k < ns) { e = a.srank[r0 + k]; off = a.soff[r0 + k]; }
         const bool reg = k < ns && e.z - e.y <= LONG_SPAN;
         // Relative bounds; an idle lane tests [0xffff, 0]: lo < 0 never holds.
         const uint32_t pl = reg ? e.y - wT : REL_MAX, ph = reg ? e.z - wT : 0u;
@@ -443,6 +490,12 @@ int launch_tile_active(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
     return 1;
 }
 
+int launch_win_setup(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
+    if (a.num_win == 0 || a.n == 0) return 0;
+    launch_k(k_win_setup, a.num_win, WIN_BLOCK, 0, s, a, st);
+    return 1;
+}
+
 template <bool BATCHED>
 static void launch_emit_window_t(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
     static std::atomic<unsigned long long> attr_set{0};
@@ -453,7 +506,11 @@ static void launch_emit_window_t(const EmitArgs& a, DevStatus* st, cudaStream_t 
                              (int)WSM_TOTAL);
         if (dev >= 0 && dev < 64) attr_set.fetch_or(1ull << dev);
     }
-    launch_k(k_emit_window<BATCHED>, a.num_win, WIN_BLOCK, WSM_TOTAL, s, a, st);
+    // One warp per 128 window positions (about 32 subscriptions), 1 to 8 warps.
+    const int shift_w = a.win_shift > 7 ? a.win_shift - 7 : 0;
+    const unsigned nwarps = 1u << (shift_w < 3 ? shift_w : 3);
+    const size_t smem = (size_t)nwarps * (LCAP_W + 32) * 8 + (size_t)WCAP * 8;
+    launch_k(k_emit_window<BATCHED>, a.num_win, 32 * nwarps, smem, s, a, st);
 }
 
 int launch_emit_window(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
