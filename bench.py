@@ -213,6 +213,42 @@ def bench_batched(ctx, dev, steps: int = 3):
             "speedup_vs_plain": pw / bw}
 
 
+def bench_baselines(ctx, dev, reps: int = 5):
+    """The paper's three matchers on the same GPU: Sort-Based (this library's
+    path), Interval-Tree (Algorithm 3) and Brute-Force (Algorithm 2), all
+    writing the full sorted pair list, at N = 1e5 (brute force is O(n m))."""
+    import torch
+    out = {}
+    for d, alpha in ((1, 100.0), (2, 1.0)):
+        N = 100_000
+        reg = synth.large_1d(alpha, N=N) if d == 1 else synth.large_nd(d, alpha, N=N)
+        t = [torch.from_numpy(a).to(dev) for a in (reg.sub_lo, reg.sub_hi, reg.upd_lo, reg.upd_hi)]
+        K = ctx.count(*t)
+        buf = torch.empty((max(K, 1), 2), dtype=torch.int32, device=dev)
+        stream = torch.cuda.current_stream(dev)
+        res = {"workload": f"d={d}, N={N:.0e}, alpha={alpha:g}, sorted pair list", "K": K}
+        calls = {"sbm": lambda: ctx.match_into(buf[:K], *t),
+                 "itm": lambda: ctx.match_itm(*t, cap=K),
+                 "bruteforce": lambda: ctx.match_bruteforce(*t, cap=K)}
+        for name, fn in calls.items():
+            fn()
+            ms = []
+            for _ in range(reps):
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            res[f"{name}_ms"] = statistics.median(ms)
+            res[f"{name}_pairs_per_s"] = K / (res[f"{name}_ms"] * 1e-3)
+        res["bruteforce_over_sbm"] = res["bruteforce_ms"] / res["sbm_ms"]
+        res["itm_over_sbm"] = res["itm_ms"] / res["sbm_ms"]
+        out[f"d{d}"] = res
+    return out
+
+
 def bench_incremental(args, dev, steps: int = 10):
     """The headline workload as a session: every timestep drifts the extents by
     N(0, 0.01 side) and reports only the pairs that appeared or disappeared
@@ -525,6 +561,7 @@ def run_ours(args):
                               "candidate_tests_per_s": K0 * world / t_max_s * args.steps}
     if rank == 0 and world == 1 and not args.no_batched:
         line["batched"] = bench_batched(ctx, dev)
+        line["baselines"] = bench_baselines(ctx, dev)
     if rank == 0 and world == 1 and not args.no_served:
         line["served"] = bench_served(dev)
         line["incremental"] = bench_incremental(args, dev)

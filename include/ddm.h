@@ -123,6 +123,31 @@ int ddm_match_host(ddm_ctx *ctx, const ddm_regions *regions, int32_t *pairs, uin
                    uint64_t *K_out);
 
 /*
+ * The paper's two other matchers, as GPU comparison baselines with the result
+ * contract of ddm_match (DEVICE coordinates, K sorted int32 pairs into
+ * `pairs`, 8-byte aligned, DEVICE memory for 2 * cap int32; K > cap writes
+ * nothing and returns DDM_ERR_CAPACITY with *K_out = K).  With pairs == NULL
+ * and cap == 0 only K is computed.  Synchronous.  Errors as for ddm_match.
+ *
+ *   ddm_match_bruteforce  Brute-Force matching (Algorithm 2, Section 2): all
+ *                         n * m pairs tested in every dimension with
+ *                         Algorithm 1; O(n m d) work, for moderate sizes (a
+ *                         second, independent check of the sort-based path).
+ *   ddm_match_itm         Interval-Tree matching (Algorithm 3, Section 2): a
+ *                         static balanced interval tree (nodes ordered by lower
+ *                         bound, with each subtree's minimum lower and maximum
+ *                         upper bound) over the updates' dimension 0, queried
+ *                         by every subscription; dimensions 1..d-1 filtered
+ *                         per reported pair.  The paper's tree holds S and is
+ *                         queried by U; the roles are exchanged here, which
+ *                         the symmetry of Algorithm 1 allows.
+ */
+int ddm_match_bruteforce(ddm_ctx *ctx, const ddm_regions *regions, int32_t *pairs, uint64_t cap,
+                         uint64_t *K_out);
+int ddm_match_itm(ddm_ctx *ctx, const ddm_regions *regions, int32_t *pairs, uint64_t cap,
+                  uint64_t *K_out);
+
+/*
  * ddm_count without any allocation.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory -- code that
  * runs where cudaMalloc is unavailable or forbidden (a custom allocator that

@@ -74,6 +74,8 @@ SIGNATURES = {
     "ddm_count": (ctypes.c_int, [_P, _RP, _U64P]),
     "ddm_match": (ctypes.c_int, [_P, _RP, _P, ctypes.c_uint64, _U64P]),
     "ddm_match_host": (ctypes.c_int, [_P, _RP, _P, ctypes.c_uint64, _U64P]),
+    "ddm_match_bruteforce": (ctypes.c_int, [_P, _RP, _P, ctypes.c_uint64, _U64P]),
+    "ddm_match_itm": (ctypes.c_int, [_P, _RP, _P, ctypes.c_uint64, _U64P]),
     "ddm_debug_sweep": (ctypes.c_int, [_P, _RP, _P, _P, _P, _P, _P]),
     "ddm_set_profiling": (ctypes.c_int, [_P, ctypes.c_int]),
     "ddm_set_param": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64]),
@@ -282,6 +284,34 @@ class Context:
         out = torch.empty((max(cap, 1), 2), dtype=torch.int32, device=sub_lo.device)
         K = self.match_into(out[:cap] if cap else out[:0], sub_lo, sub_hi, upd_lo, upd_hi)
         return out[:K]
+
+    def _baseline(self, fn, tensors, cap, count_only):
+        torch = _torch()
+        p = _pack_device(*tensors)
+        K = ctypes.c_uint64(0)
+        if count_only:
+            self._check(fn(self._h, p.ref, None, 0, ctypes.byref(K)), K.value)
+            return int(K.value)
+        if cap is None:
+            cap = self._baseline(fn, tensors, None, True)
+        out = torch.empty((max(cap, 1), 2), dtype=torch.int32, device=tensors[0].device)
+        rc = fn(self._h, p.ref, ctypes.c_void_p(out.data_ptr()), cap, ctypes.byref(K))
+        self._check(rc, K.value)
+        return out[:K.value]
+
+    def match_bruteforce(self, sub_lo, sub_hi, upd_lo, upd_hi, cap: int | None = None,
+                         count_only: bool = False):
+        """ddm_match_bruteforce (Algorithm 2 on the GPU): sorted (K, 2) int32 pairs,
+        or K with count_only=True."""
+        return self._baseline(self._lib.ddm_match_bruteforce, (sub_lo, sub_hi, upd_lo, upd_hi),
+                              cap, count_only)
+
+    def match_itm(self, sub_lo, sub_hi, upd_lo, upd_hi, cap: int | None = None,
+                  count_only: bool = False):
+        """ddm_match_itm (Algorithm 3, interval tree, on the GPU): sorted (K, 2) int32
+        pairs, or K with count_only=True."""
+        return self._baseline(self._lib.ddm_match_itm, (sub_lo, sub_hi, upd_lo, upd_hi), cap,
+                              count_only)
 
     def match_host(self, sub_lo, sub_hi, upd_lo, upd_hi, cap: int | None = None,
                    out: np.ndarray | None = None):

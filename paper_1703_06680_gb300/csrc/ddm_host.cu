@@ -10,6 +10,7 @@
 #include <string>
 #include <vector>
 
+#include "baseline.cuh"
 #include "batch.cuh"
 #include "delta.cuh"
 #include "drift.cuh"
@@ -1119,6 +1120,103 @@ int ddm_session_emit_delta(ddm_session* s, void* stream, int32_t* added, uint64_
     s->K_ref = s->K_new;
     s->pending = false;
     return DDM_OK;
+}
+
+// The paper's comparison matchers (Algorithms 2 and 3) on the GPU, with the
+// result contract of ddm_match.  `pairs` NULL (and cap 0): count only.
+static int baseline_match(ddm_ctx* c, const ddm_regions* r, int32_t* pairs, uint64_t cap,
+                          uint64_t* K_out, bool itm) {
+    if (!c) return DDM_ERR_INVALID;
+    int rc = check_regions(c, r);
+    if (rc) return rc;
+    if (!pairs && cap > 0) return fail(c, DDM_ERR_INVALID, "pairs is NULL but cap > 0");
+    if (pairs && (reinterpret_cast<uintptr_t>(pairs) & 7u))
+        return fail(c, DDM_ERR_INVALID, "pairs must be 8-byte aligned");
+    DeviceGuard g(c->device);
+    const int d = r->d;
+    const int64_t n = r->n, m = r->m;
+    // Workspace: zeroed part (offsets scan status, sort status and group
+    // sums), then counts, offsets, and for the tree the sort buffers and nodes.
+    uint32_t P = 1;
+    while (P < (uint64_t)m) P <<= 1;
+    const uint64_t stiles = sort_tiles<uint32_t>((uint64_t)m);
+    const int passes = 4;
+    auto carve = [&](Carve& cv, SortScratch& sc, unsigned long long*& ost, size_t& zero,
+                     uint32_t*& cnt, unsigned long long*& off, uint32_t* kv[4], uint32_t*& tree) {
+        ost = cv.take<unsigned long long>(ceil_div((uint64_t)n, OFF_TILE) + 2);
+        sc.status = cv.take<unsigned long long>(itm ? (size_t)passes * sort_status_stride(m) : 0);
+        sc.total = cv.take<unsigned long long>(1);
+        const size_t gw = itm ? sort_group_words(stiles, passes) : 0;
+        sc.grp = gw ? cv.take<uint32_t>(gw) : nullptr;
+        zero = (cv.off + 255) & ~(size_t)255;
+        cnt = cv.take<uint32_t>(n);
+        off = cv.take<unsigned long long>(n + 1);
+        sc.tile_hist = cv.take<uint32_t>(itm ? stiles * RADIX : 0);
+        sc.offs = cv.take<unsigned long long>(itm ? stiles * RADIX + 1 : 0);
+        for (int q = 0; q < 4; ++q) kv[q] = cv.take<uint32_t>(itm ? m : 0);
+        tree = cv.take<uint32_t>(itm ? 2 * (size_t)P : 0);
+    };
+    Carve sizing;
+    SortScratch sc{};
+    unsigned long long *ost = nullptr, *off = nullptr;
+    size_t zero = 0;
+    uint32_t *cnt = nullptr, *tree = nullptr, *kv[4] = {};
+    carve(sizing, sc, ost, zero, cnt, off, kv, tree);
+    rc = ensure(c, &c->ws, &c->ws_size, sizing.off + 256);
+    if (rc) return rc;
+    Carve cv;
+    cv.base = c->ws;
+    carve(cv, sc, ost, zero, cnt, off, kv, tree);
+    cudaStream_t s = c->stream;
+    PdlScope pdl_scope(c->pdl);
+    CK(cudaMemsetAsync(c->dstat, 0, sizeof(DevStatus), s));
+    CK(cudaMemsetAsync(c->ws, 0, zero, s));
+    c->stats.calls++;
+    uint64_t& L = c->stats.launches;
+    DimPtrs dims{};
+    for (int k = 0; k < d; ++k) {
+        dims.sub_lo[k] = r->sub_lo[k]; dims.sub_hi[k] = r->sub_hi[k];
+        dims.upd_lo[k] = r->upd_lo[k]; dims.upd_hi[k] = r->upd_hi[k];
+    }
+    const uint64_t off_cap = pairs ? cap : ~0ull;
+    if (!itm) {
+        L += launch_bf_count(dims, d, n, m, cnt, c->dstat, s);
+        L += launch_offsets(cnt, n, off, off_cap, &c->dstat->K, ost, c->dstat, s);
+        if (pairs) L += launch_bf_write(dims, d, n, m, off, pairs, c->dstat, s);
+    } else {
+        L += launch_itm_keys(dims, d, m, kv[0], kv[1], c->dstat, s);
+        if (m > 0)
+            L += launch_radix_sort<uint32_t>(kv[0], kv[1], kv[2], kv[3], (uint64_t)m, passes, sc,
+                                             false, c->dstat, s);
+        ItmTree t{};
+        t.P = P; t.m = (uint32_t)m;
+        t.lo_sorted = kv[(passes & 1) * 2];
+        t.id_sorted = kv[(passes & 1) * 2 + 1];
+        t.tree = tree;
+        L += launch_itm_build(t, dims.upd_hi[0], c->dstat, s);
+        L += launch_itm_query(t, dims, d, n, m, cnt, nullptr, nullptr, c->dstat, s);
+        L += launch_offsets(cnt, n, off, off_cap, &c->dstat->K, ost, c->dstat, s);
+        if (pairs && n > 0 && m > 0) {
+            L += launch_itm_query(t, dims, d, n, m, cnt, off, pairs, c->dstat, s);
+            EmitArgs a{};  // per-segment sort by update id (every segment)
+            a.d = d; a.n = n; a.m = m;
+            a.cnt = cnt; a.off = off; a.pairs = pairs; a.cap = cap;
+            a.id_bits = id_bits(m);
+            L += launch_segment_sort(a, c->dstat, s);
+        }
+    }
+    CK(cudaGetLastError());
+    return finish(c, K_out);
+}
+
+int ddm_match_bruteforce(ddm_ctx* c, const ddm_regions* r, int32_t* pairs, uint64_t cap,
+                         uint64_t* K_out) {
+    return baseline_match(c, r, pairs, cap, K_out, false);
+}
+
+int ddm_match_itm(ddm_ctx* c, const ddm_regions* r, int32_t* pairs, uint64_t cap,
+                  uint64_t* K_out) {
+    return baseline_match(c, r, pairs, cap, K_out, true);
 }
 
 int ddm_debug_wait_timeout(ddm_ctx* c, int which, uint32_t spin_limit) {
