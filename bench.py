@@ -214,9 +214,10 @@ def bench_batched(ctx, dev, steps: int = 3):
 
 
 def bench_baselines(ctx, dev, reps: int = 5):
-    """The paper's three matchers on the same GPU: Sort-Based (this library's
-    path), Interval-Tree (Algorithm 3) and Brute-Force (Algorithm 2), all
-    writing the full sorted pair list, at N = 1e5 (brute force is O(n m))."""
+    """The paper's matchers on the same GPU: Sort-Based (this library's path),
+    Interval-Tree (Algorithm 3), Grid-Based (Section 2, the library's grid
+    size) and Brute-Force (Algorithm 2), all writing the full sorted pair
+    list, at N = 1e5 (brute force is O(n m))."""
     import torch
     out = {}
     for d, alpha in ((1, 100.0), (2, 1.0)):
@@ -229,6 +230,7 @@ def bench_baselines(ctx, dev, reps: int = 5):
         res = {"workload": f"d={d}, N={N:.0e}, alpha={alpha:g}, sorted pair list", "K": K}
         calls = {"sbm": lambda: ctx.match_into(buf[:K], *t),
                  "itm": lambda: ctx.match_itm(*t, cap=K),
+                 "grid": lambda: ctx.match_grid(*t, cap=K),
                  "bruteforce": lambda: ctx.match_bruteforce(*t, cap=K)}
         for name, fn in calls.items():
             fn()
@@ -245,6 +247,8 @@ def bench_baselines(ctx, dev, reps: int = 5):
             res[f"{name}_pairs_per_s"] = K / (res[f"{name}_ms"] * 1e-3)
         res["bruteforce_over_sbm"] = res["bruteforce_ms"] / res["sbm_ms"]
         res["itm_over_sbm"] = res["itm_ms"] / res["sbm_ms"]
+        res["grid_over_sbm"] = res["grid_ms"] / res["sbm_ms"]
+        res["grid_cells"] = ctx.last_grid
         out[f"d{d}"] = res
     return out
 

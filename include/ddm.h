@@ -148,6 +148,24 @@ int ddm_match_itm(ddm_ctx *ctx, const ddm_regions *regions, int32_t *pairs, uint
                   uint64_t *K_out);
 
 /*
+ * Grid-Based matching (Section 2), the paper's third comparison method, with
+ * the same result contract: a regular mesh of cells over the first min(d, 3)
+ * dimensions of the instance's bounding box (other dimensions are filtered per
+ * pair); every extent is registered in each cell it overlaps and brute force
+ * runs inside each cell; a pair that shares several cells is reported once,
+ * by the cell that holds max(S.lo, U.lo).  cells_per_dim > 0 fixes the cells
+ * along each gridded dimension (clamped to 2^24, 2^12 or 2^8 for 1, 2 or 3
+ * gridded dimensions; above 2^24: DDM_ERR_INVALID); 0 lets
+ * the library choose (cells about as wide as the mean extent side, at least
+ * about one extent per cell).  The paper leaves the grid size to the user or a
+ * heuristic.  grid_out (HOST, 3 values, may be NULL) receives the cells used
+ * per gridded dimension (1 for the others).  The memberships need 4 bytes per
+ * (extent, cell) pair of device memory.
+ */
+int ddm_match_grid(ddm_ctx *ctx, const ddm_regions *regions, uint32_t cells_per_dim,
+                   int32_t *pairs, uint64_t cap, uint64_t *K_out, uint32_t *grid_out);
+
+/*
  * ddm_count without any allocation.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory -- code that
  * runs where cudaMalloc is unavailable or forbidden (a custom allocator that

@@ -76,6 +76,7 @@ SIGNATURES = {
     "ddm_match_host": (ctypes.c_int, [_P, _RP, _P, ctypes.c_uint64, _U64P]),
     "ddm_match_bruteforce": (ctypes.c_int, [_P, _RP, _P, ctypes.c_uint64, _U64P]),
     "ddm_match_itm": (ctypes.c_int, [_P, _RP, _P, ctypes.c_uint64, _U64P]),
+    "ddm_match_grid": (ctypes.c_int, [_P, _RP, ctypes.c_uint32, _P, ctypes.c_uint64, _U64P, _P]),
     "ddm_debug_sweep": (ctypes.c_int, [_P, _RP, _P, _P, _P, _P, _P]),
     "ddm_set_profiling": (ctypes.c_int, [_P, ctypes.c_int]),
     "ddm_set_param": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64]),
@@ -312,6 +313,29 @@ class Context:
         pairs, or K with count_only=True."""
         return self._baseline(self._lib.ddm_match_itm, (sub_lo, sub_hi, upd_lo, upd_hi), cap,
                               count_only)
+
+    def match_grid(self, sub_lo, sub_hi, upd_lo, upd_hi, cells_per_dim: int = 0,
+                   cap: int | None = None, count_only: bool = False):
+        """ddm_match_grid (grid-based matching on the GPU): sorted (K, 2) int32 pairs, or
+        K with count_only=True.  The cells used per gridded dimension are kept in
+        self.last_grid."""
+        torch = _torch()
+        p = _pack_device(sub_lo, sub_hi, upd_lo, upd_hi)
+        K = ctypes.c_uint64(0)
+        grid = (ctypes.c_uint32 * 3)()
+        fn = self._lib.ddm_match_grid
+        if count_only or cap is None:
+            self._check(fn(self._h, p.ref, cells_per_dim, None, 0, ctypes.byref(K), grid), K.value)
+            self.last_grid = list(grid)
+            if count_only:
+                return int(K.value)
+            cap = int(K.value)
+        out = torch.empty((max(cap, 1), 2), dtype=torch.int32, device=sub_lo.device)
+        rc = fn(self._h, p.ref, cells_per_dim, ctypes.c_void_p(out.data_ptr()), cap,
+                ctypes.byref(K), grid)
+        self._check(rc, K.value)
+        self.last_grid = list(grid)
+        return out[:K.value]
 
     def match_host(self, sub_lo, sub_hi, upd_lo, upd_hi, cap: int | None = None,
                    out: np.ndarray | None = None):

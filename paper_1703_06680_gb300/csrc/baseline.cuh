@@ -57,3 +57,57 @@ int launch_itm_query(const ItmTree& t, const DimPtrs& dims, int d, int64_t n, in
                      DevStatus* st, cudaStream_t s);
 
 }  // namespace ddm
+
+namespace ddm {
+
+// Grid-Based matching (Section 2): a regular mesh over the first dg = min(d, 3)
+// dimensions of the routing space.
+constexpr int GRID_MAX_DIMS = 3;
+constexpr uint32_t GRID_MAX_CELLS = 1u << 24;
+
+struct GridPlan {
+    int dg;                         // gridded dimensions
+    uint32_t g[GRID_MAX_DIMS];      // cells along each
+    uint32_t stride[GRID_MAX_DIMS]; // cell index = sum c_k * stride[k]
+    float lo[GRID_MAX_DIMS];        // the mesh starts at the smallest lower bound
+    float inv_w[GRID_MAX_DIMS];     // cells per unit length
+    uint32_t G;                     // cells in all
+};
+
+// Device scratch of the grid matcher's first pass (zeroed before the call).
+struct GridScratch {
+    uint32_t kmax_hi[GRID_MAX_DIMS];      // max key of the upper bounds
+    uint32_t kmin_lo_inv[GRID_MAX_DIMS];  // ~(min key of the lower bounds)
+    double side_sum[GRID_MAX_DIMS];
+};
+
+// Bounding box and summed sides of the gridded dimensions (validating every
+// dimension of both sets) into *gs.
+int launch_grid_bounds(const DimPtrs& dims, int d, int64_t n, int64_t m, GridScratch* gs,
+                       DevStatus* st, cudaStream_t s);
+
+// The mesh, on the host, from the measured bounds: cells_per_dim > 0 fixes the
+// cells along each gridded dimension; else cells about as wide as the mean
+// extent side, with at least about one extent per cell (G <= GRID_MAX_CELLS).
+GridPlan grid_plan(const GridScratch& h, int d, uint64_t total, uint32_t cells_per_dim);
+
+// Per-cell membership counts of both sets (cnt_* zeroed, G entries each).
+int launch_grid_count(const DimPtrs& dims, int64_t n, int64_t m, const GridPlan& p,
+                      uint32_t* cnt_s, uint32_t* cnt_u, DevStatus* st, cudaStream_t s);
+
+// Memberships sorted by cell (cell_off_* from the scans of the counts, cursors
+// zeroed), then brute force inside each cell, reporting a pair only in the cell
+// that holds max(S.lo, U.lo) along the gridded dimensions.  Count pass
+// (pairs == NULL): cnt[i] (zeroed) accumulates; write pass: the pairs into
+// pairs[2 off[i] ..) through cursor[i] (zeroed), in any order.
+int launch_grid_fill(const DimPtrs& dims, int64_t n, int64_t m, const GridPlan& p,
+                     const unsigned long long* cell_off_s, const unsigned long long* cell_off_u,
+                     uint32_t* cur_s, uint32_t* cur_u, uint32_t* ent_s, uint32_t* ent_u,
+                     DevStatus* st, cudaStream_t s);
+int launch_grid_match(const DimPtrs& dims, int d, const GridPlan& p,
+                      const unsigned long long* cell_off_s, const unsigned long long* cell_off_u,
+                      const uint32_t* ent_s, const uint32_t* ent_u, uint32_t* cnt,
+                      const unsigned long long* off, uint32_t* cursor, int32_t* pairs,
+                      DevStatus* st, cudaStream_t s);
+
+}  // namespace ddm

@@ -1219,6 +1219,104 @@ int ddm_match_itm(ddm_ctx* c, const ddm_regions* r, int32_t* pairs, uint64_t cap
     return baseline_match(c, r, pairs, cap, K_out, true);
 }
 
+int ddm_match_grid(ddm_ctx* c, const ddm_regions* r, uint32_t cells_per_dim, int32_t* pairs,
+                   uint64_t cap, uint64_t* K_out, uint32_t* grid_out) {
+    if (!c) return DDM_ERR_INVALID;
+    int rc = check_regions(c, r);
+    if (rc) return rc;
+    if (!pairs && cap > 0) return fail(c, DDM_ERR_INVALID, "pairs is NULL but cap > 0");
+    if (pairs && (reinterpret_cast<uintptr_t>(pairs) & 7u))
+        return fail(c, DDM_ERR_INVALID, "pairs must be 8-byte aligned");
+    if (cells_per_dim > GRID_MAX_CELLS)
+        return fail(c, DDM_ERR_INVALID, "cells_per_dim out of range");
+    DeviceGuard g(c->device);
+    const int d = r->d;
+    const int64_t n = r->n, m = r->m;
+    cudaStream_t s = c->stream;
+    PdlScope pdl_scope(c->pdl);
+    uint64_t& L = c->stats.launches;
+    c->stats.calls++;
+    DimPtrs dims{};
+    for (int k = 0; k < d; ++k) {
+        dims.sub_lo[k] = r->sub_lo[k]; dims.sub_hi[k] = r->sub_hi[k];
+        dims.upd_lo[k] = r->upd_lo[k]; dims.upd_hi[k] = r->upd_hi[k];
+    }
+    if (grid_out)
+        for (int k = 0; k < GRID_MAX_DIMS; ++k) grid_out[k] = 1;
+    if (n + m == 0) {
+        if (K_out) *K_out = 0;
+        c->err.clear();
+        return DDM_OK;
+    }
+    // 1. Bounding box of the gridded dimensions (and validation); the mesh.
+    rc = ensure(c, &c->ws, &c->ws_size, 256 + sizeof(GridScratch));
+    if (rc) return rc;
+    GridScratch* gs = reinterpret_cast<GridScratch*>(c->ws);
+    CK(cudaMemsetAsync(c->dstat, 0, sizeof(DevStatus), s));
+    CK(cudaMemsetAsync(gs, 0, sizeof(GridScratch), s));
+    L += launch_grid_bounds(dims, d, n, m, gs, c->dstat, s);
+    GridScratch hg{};
+    CK(cudaMemcpyAsync(&hg, gs, sizeof hg, cudaMemcpyDeviceToHost, s));
+    rc = finish(c, nullptr);
+    if (rc) return rc;
+    const GridPlan plan = grid_plan(hg, d, (uint64_t)(n + m), cells_per_dim);
+    if (grid_out)
+        for (int k = 0; k < plan.dg; ++k) grid_out[k] = plan.g[k];
+    // 2. Memberships per cell, and their offsets.
+    const uint64_t G = plan.G;
+    Carve sizing;
+    auto layout = [&](Carve& cv, uint32_t** cz, unsigned long long** st2,
+                      unsigned long long** offs, uint32_t*& cnt, uint32_t*& cursor,
+                      unsigned long long*& ost, unsigned long long*& off, size_t& zero) {
+        for (int q = 0; q < 4; ++q) cz[q] = cv.take<uint32_t>(G);  // counts s/u, cursors s/u
+        for (int q = 0; q < 2; ++q) st2[q] = cv.take<unsigned long long>(ceil_div(G, OFF_TILE) + 2);
+        cnt = cv.take<uint32_t>(n);
+        cursor = cv.take<uint32_t>(n);
+        ost = cv.take<unsigned long long>(ceil_div((uint64_t)n, OFF_TILE) + 2);
+        zero = (cv.off + 255) & ~(size_t)255;
+        for (int q = 0; q < 2; ++q) offs[q] = cv.take<unsigned long long>(G + 1);
+        off = cv.take<unsigned long long>(n + 1);
+    };
+    uint32_t* cz[4];
+    unsigned long long *st2[2], *offs[2], *ost, *off;
+    uint32_t *cnt, *cursor;
+    size_t zero = 0;
+    layout(sizing, cz, st2, offs, cnt, cursor, ost, off, zero);
+    rc = ensure(c, &c->ws, &c->ws_size, sizing.off + 256);
+    if (rc) return rc;
+    Carve cv;
+    cv.base = c->ws;
+    layout(cv, cz, st2, offs, cnt, cursor, ost, off, zero);
+    CK(cudaMemsetAsync(c->ws, 0, zero, s));
+    L += launch_grid_count(dims, n, m, plan, cz[0], cz[1], c->dstat, s);
+    L += launch_offsets(cz[0], (int64_t)G, offs[0], ~0ull, &c->dstat->aux[0], st2[0], c->dstat, s);
+    L += launch_offsets(cz[1], (int64_t)G, offs[1], ~0ull, &c->dstat->aux[1], st2[1], c->dstat, s);
+    rc = finish(c, nullptr);
+    if (rc) return rc;
+    const uint64_t Ts = c->hstat->aux[0], Tu = c->hstat->aux[1];
+    // 3. Memberships by cell, brute force per cell (count), offsets, write, sort.
+    rc = ensure(c, &c->out, &c->out_size, 4 * (Ts + Tu) + 512);
+    if (rc) return rc;
+    uint32_t* ent_s = reinterpret_cast<uint32_t*>(c->out);
+    uint32_t* ent_u = ent_s + ((Ts + 63) & ~63ull);
+    L += launch_grid_fill(dims, n, m, plan, offs[0], offs[1], cz[2], cz[3], ent_s, ent_u,
+                          c->dstat, s);
+    L += launch_grid_match(dims, d, plan, offs[0], offs[1], ent_s, ent_u, cnt, nullptr, nullptr,
+                           nullptr, c->dstat, s);
+    L += launch_offsets(cnt, n, off, pairs ? cap : ~0ull, &c->dstat->K, ost, c->dstat, s);
+    if (pairs && n > 0 && m > 0) {
+        L += launch_grid_match(dims, d, plan, offs[0], offs[1], ent_s, ent_u, cnt, off, cursor,
+                               pairs, c->dstat, s);
+        EmitArgs a{};  // per-segment sort by update id (every segment)
+        a.d = d; a.n = n; a.m = m;
+        a.cnt = cnt; a.off = off; a.pairs = pairs; a.cap = cap;
+        a.id_bits = id_bits(m);
+        L += launch_segment_sort(a, c->dstat, s);
+    }
+    CK(cudaGetLastError());
+    return finish(c, K_out);
+}
+
 int ddm_debug_wait_timeout(ddm_ctx* c, int which, uint32_t spin_limit) {
     if (!c) return DDM_ERR_INVALID;
     if (which < 0 || which > 1) return fail(c, DDM_ERR_INVALID, "which must be 0 or 1");

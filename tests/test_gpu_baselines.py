@@ -1,6 +1,6 @@
-"""The paper's comparison matchers on the GPU: Brute-Force (Algorithm 2) and
-Interval-Tree matching (Algorithm 3), through the C ABI, against the CPU
-oracle; and brute force as a second, independent GPU-side check of the
+"""The paper's comparison matchers on the GPU: Brute-Force (Algorithm 2),
+Interval-Tree matching (Algorithm 3) and Grid-Based matching (Section 2),
+through the C ABI, against the CPU oracle; and brute force as a second, independent GPU-side check of the
 sort-based path at moderate sizes.  Results are integer pair lists: the bar is
 bit-exact equality of the sorted lists.
 """
@@ -14,7 +14,7 @@ from tests.helpers import special_value_instance, tiny_grid_instance
 
 pytestmark = pytest.mark.gpu
 
-METHODS = ["bruteforce", "itm"]
+METHODS = ["bruteforce", "itm", "grid"]
 
 
 @pytest.fixture(scope="module")
@@ -26,9 +26,13 @@ def ctx():
     c.close()
 
 
+def method_fn(ctx, method):
+    return {"bruteforce": ctx.match_bruteforce, "itm": ctx.match_itm,
+            "grid": ctx.match_grid}[method]
+
+
 def run(ctx, method, reg, count_only=False):
-    fn = ctx.match_bruteforce if method == "bruteforce" else ctx.match_itm
-    r = fn(*to_dev(reg), count_only=count_only)
+    r = method_fn(ctx, method)(*to_dev(reg), count_only=count_only)
     return r if count_only else r.cpu().numpy()
 
 
@@ -86,9 +90,8 @@ def test_invalid_input_and_capacity(ctx, method):
         assert e.value.code == ddm._lib.DDM_ERR_INVALID
     reg = synth.small_1d()
     want = oracle.sbm(reg)
-    fn = ctx.match_bruteforce if method == "bruteforce" else ctx.match_itm
     with pytest.raises(ddm.CapacityError) as e:
-        fn(*to_dev(reg), cap=len(want) - 1)
+        method_fn(ctx, method)(*to_dev(reg), cap=len(want) - 1)
     assert e.value.K == len(want)
     check(ctx, method, reg, want)   # the context stays usable
 
@@ -105,3 +108,32 @@ def test_bruteforce_checks_sort_based_path(ctx, d, alpha):
     assert len(bf) == oracle.sbm_count(reg)
     itm = ctx.match_itm(*t).cpu().numpy()
     assert np.array_equal(itm, bf)
+
+
+@pytest.mark.parametrize("d,alpha", [(1, 100.0), (2, 1.0), (3, 100.0)])
+def test_grid_size_changes_only_speed(ctx, d, alpha):
+    # Any mesh gives the same pairs: one cell (brute force), a few, the
+    # library's choice, and more cells than extents per dimension (clamped).
+    reg = synth.large_1d(alpha, N=40_000) if d == 1 else synth.large_nd(d, alpha, N=30_000)
+    want = oracle.sbm(reg)
+    t = to_dev(reg)
+    for cells in (1, 3, 0, 64, 1 << 20):
+        got = ctx.match_grid(*t, cells_per_dim=cells).cpu().numpy()
+        assert np.array_equal(got, want), cells
+        grid = ctx.last_grid
+        assert all(1 <= g for g in grid) and grid[min(d, 3):] == [1] * (3 - min(d, 3))
+        if cells == 1:
+            assert grid == [1, 1, 1]
+
+
+def test_grid_huge_extents_and_infinities(ctx):
+    # Extents spanning the whole space fall into every cell; an infinite bound
+    # makes that dimension one cell; pairs stay exact and unique.
+    reg = synth.large_nd(2, 1.0, N=20_000)
+    reg.sub_lo[:, 5] = -1.0
+    reg.sub_hi[:, 5] = 2.0e6
+    reg.upd_lo[0, 9] = -np.inf
+    reg.upd_hi[1, 9] = np.inf
+    want = oracle.sbm(reg)
+    assert np.array_equal(ctx.match_grid(*to_dev(reg)).cpu().numpy(), want)
+    assert ctx.last_grid[0] == 1
