@@ -253,51 +253,71 @@ def bench_baselines(ctx, dev, reps: int = 5):
     return out
 
 
-def bench_incremental(args, dev, steps: int = 10):
+def bench_incremental(args, dev, steps: int = 10, warmup: int = 3):
     """The headline workload as a session: every timestep drifts the extents by
     N(0, 0.01 side) and reports only the pairs that appeared or disappeared
-    (ddm_session_emit_delta), against count + full emission of the same timestep."""
+    (ddm_session_emit_delta), against count + full emission of the same
+    timestep; both also measured with their result delivered to pinned host
+    memory (what a consumer off the GPU receives)."""
     import torch
     import paper_1703_06680_gb300 as ddm
     reg = workload(args, 0)
     t_in = [torch.from_numpy(a).to(dev) for a in (reg.sub_lo, reg.sub_hi, reg.upd_lo, reg.upd_hi)]
     sess = ddm.Session(*t_in)
     sigma = 0.01 * synth.side_for(args.alpha, args.N, args.d)
-    sess.count()
-    sess.emit_delta()
+    K0 = sess.count()
+    big = torch.empty((max(K0, 1), 2), dtype=torch.int32, device=dev)
+    sess.emit_delta(big[:K0], big[:0])       # first report: every pair
+    cap = max(K0 // 8, 4096)
+    add_b = torch.empty((cap, 2), dtype=torch.int32, device=dev)
+    rem_b = torch.empty((cap, 2), dtype=torch.int32, device=dev)
+    host = torch.empty((max(K0, 1) + 4096, 2), dtype=torch.int32).pin_memory()
     stream = torch.cuda.current_stream(dev)
-    t_delta, added, removed, K = 0.0, 0, 0, 0
-    for s in range(steps):
-        sess.drift(1703, s, sigma)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
+    step = 0
+
+    def timed(fn, n):
+        nonlocal step
+        tot = 0.0
+        out = None
+        for _ in range(n):
+            sess.drift(1703, step, sigma)
+            step += 1
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot / max(n, 1), out
+
+    def report(to_host=False):
         K = sess.count()
-        a, r = sess.emit_delta()
-        e1.record(stream)
-        e1.synchronize()
-        t_delta += e0.elapsed_time(e1)
-        added += len(a)
-        removed += len(r)
-    out = torch.empty((max(K, 1), 2), dtype=torch.int32, device=dev)
-    t_full = 0.0
-    for s in range(steps):
-        sess.drift(1703, 1000 + s, sigma)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        K2 = sess.count()
-        if K2 > out.shape[0]:
-            out = torch.empty((K2, 2), dtype=torch.int32, device=dev)
-        sess.emit(out[:K2])
-        e1.record(stream)
-        e1.synchronize()
-        t_full += e0.elapsed_time(e1)
+        a, r = sess.emit_delta(add_b, rem_b)
+        if to_host:
+            host[:len(a)].copy_(a, non_blocking=True)
+            host[len(a):len(a) + len(r)].copy_(r, non_blocking=True)
+        return K, len(a), len(r)
+
+    def full(to_host=False):
+        K = sess.count()
+        sess.emit(big[:K])
+        if to_host:
+            host[:K].copy_(big[:K], non_blocking=True)
+        return K, K, 0
+
+    timed(report, warmup)
+    report_ms, (K, na, nr) = timed(report, steps)
+    report_host_ms, _ = timed(lambda: report(True), steps)
+    timed(full, warmup)
+    full_ms, _ = timed(full, steps)
+    full_host_ms, _ = timed(lambda: full(True), steps)
     sess.close()
     return {"workload": workload_name(args) + ", session with drift N(0, 0.01 side) per step",
-            "steps": steps, "K": K, "report_ms": t_delta / steps, "full_emit_ms": t_full / steps,
-            "added_per_step": added / steps, "removed_per_step": removed / steps,
-            "report_bytes_per_step": 8 * (added + removed) / steps, "full_bytes_per_step": 8 * K}
+            "steps": steps, "warmup": warmup, "K": K, "report_ms": report_ms,
+            "full_emit_ms": full_ms, "report_to_host_ms": report_host_ms,
+            "full_emit_to_host_ms": full_host_ms, "added_per_step": na, "removed_per_step": nr,
+            "report_bytes_per_step": 8 * (na + nr), "full_bytes_per_step": 8 * K}
 
 
 def bench_served(dev, requests: int = 96, slots: int = 4, load: float = 0.8):

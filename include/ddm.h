@@ -319,21 +319,28 @@ int ddm_session_emit(ddm_session *s, void *cuda_stream, int32_t *pairs, uint64_t
 
 /*
  * Incremental matching: the change report of one timestep.  After
- * ddm_session_count, computes this timestep's pairs into session-owned device
- * memory and compares them with the pairs of the previous successful
- * ddm_session_emit_delta call (an empty list before the first one):
- *   added   (DEVICE, 2 * cap_added int32)   pairs present now and not before,
- *   removed (DEVICE, 2 * cap_removed int32) pairs present before and not now,
+ * ddm_session_count, reports the pairs whose status changed since the last
+ * successful ddm_session_emit_delta call (the first call reports every pair
+ * as added):
+ *   added   (DEVICE, 2 * cap_added int32)   pairs present now and not then,
+ *   removed (DEVICE, 2 * cap_removed int32) pairs present then and not now,
  * both sorted lexicographically; *n_added / *n_removed receive their numbers.
- * Bounds: n_added <= K of this timestep, n_removed <= K of the previous one.
- * If either list does not fit, returns DDM_ERR_CAPACITY with both numbers set
- * and keeps the new timestep pending: calling ddm_session_emit_delta again,
- * without a new count, writes the same report into larger buffers.  On
- * success the current pairs become the reference of the next call.  The
- * session then holds two pair lists (16 K bytes) and their offsets; memory is
- * taken on first use.  Synchronous.  Other errors as for ddm_session_emit.
- * The paper recomputes the full match every timestep; reporting changes is
- * the dynamic DDM it names as future work (Section 6).
+ * Nothing is recomputed in full: the session keeps the coordinates of the
+ * last report, measures how far any endpoint has moved since (per
+ * dimension), and tests only the pairs of endpoints that have come within
+ * twice that distance of each other -- the only ones whose comparisons, and
+ * so whose intersection, can have changed (the dimension-0 candidates come
+ * from the sorted endpoint stream of the count phase).  The work therefore
+ * follows the motion, not K.  If either list does not fit, returns
+ * DDM_ERR_CAPACITY with both numbers set; calling again without a new count
+ * writes the same report into larger buffers.  After a delivered report the
+ * next one needs a new ddm_session_count.  Device memory (counted against the
+ * session budget): a copy of the coordinates, and 16 bytes per changed pair
+ * plus sort scratch; for d > 1 also the updates' bounds of dimensions 1..d-1
+ * sorted per dimension (16 bytes per update and dimension).  Synchronous.
+ * Other errors as for ddm_session_emit.  The paper recomputes the full match
+ * every timestep; reporting changes is the dynamic DDM it names as future work
+ * (Section 6).
  */
 int ddm_session_emit_delta(ddm_session *s, void *cuda_stream, int32_t *added, uint64_t cap_added,
                            int32_t *removed, uint64_t cap_removed, uint64_t *n_added,

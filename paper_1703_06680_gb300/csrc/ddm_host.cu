@@ -48,6 +48,7 @@ struct ddm_ctx {
     int win_shift = 10;                           // DDM_PARAM_WIN_SHIFT
     int nd_path = 0;                              // DDM_PARAM_ND_PATH
     bool pdl = true;                              // DDM_PARAM_PDL
+    bool keep_keys = false;  // sessions: the sort's last pass also writes the sorted keys
     int sweep_dim = 0;                            // DDM_PARAM_SWEEP_DIM
     cudaEvent_t ev[DDM_STAGES + 1] = {};
 };
@@ -454,7 +455,8 @@ int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
             pl.passes, pl.sort, true, c->dstat, s, rec.s_lo, rec_words);
     } else {
         L += launch_radix_sort<uint32_t>((uint32_t*)pl.keys0, pl.vals0, (uint32_t*)pl.keys1,
-                                         pl.vals1, pl.E, pl.passes, pl.sort, true, c->dstat, s,
+                                         pl.vals1, pl.E, pl.passes, pl.sort, !c->keep_keys,
+                                         c->dstat, s,
                                          rec.s_lo, rec_words);
     }
     mark(c, 2);
@@ -815,19 +817,16 @@ struct ddm_session {
     ddm_regions regions{};
     bool counted = false;     // a pipeline prefix is held in the workspace
     uint64_t K = 0;
-    // Incremental matching (ddm_session_emit_delta): two pair lists with their
-    // offsets; `ref` indexes the reference (previous) list, the other one
-    // receives the new timestep.
-    char* list[2] = {};
-    size_t list_size[2] = {};
-    char* loff[2] = {};
-    size_t loff_size[2] = {};
-    char* dwork = nullptr;    // per-sub counts and offsets of the report, scan status
+    // Incremental matching (ddm_session_emit_delta): the coordinates of the
+    // last delivered report (same layout as coords), and a work area for the
+    // report (displacements, counters, per-dimension sorted update bounds,
+    // the change keys and their sort).
+    float* ref_coords = nullptr;
+    size_t ref_size = 0;
+    bool have_ref = false;    // a report was delivered (else: everything is new)
+    char* dwork = nullptr;
     size_t dwork_size = 0;
-    int ref = 0;
-    bool have_ref = false;    // a reference list exists (else: empty)
-    bool pending = false;     // new list computed, report not yet delivered
-    uint64_t K_ref = 0, K_new = 0;
+    uint64_t delta_cap = 0;   // room for the keys of one report's changed pairs
     // The count phase as a CUDA graph: a session's shapes, coordinates and
     // workspace do not change, so after one direct run the kernels of
     // ddm_session_count are captured once and then replayed with a single
@@ -864,6 +863,7 @@ int ddm_session_create(ddm_session** out, int device, const ddm_regions* initial
     DeviceGuard g(device);
     ddm_session* s = new ddm_session();
     s->ctx = c;
+    c->keep_keys = true;  // the change report walks the sorted endpoint stream
     const int d = initial->d;
     const int64_t n = initial->n, m = initial->m;
     const size_t floats = (size_t)2 * d * (n + m);
@@ -910,10 +910,7 @@ int ddm_session_destroy(ddm_session* s) {
     if (s->ctx) {
         DeviceGuard g(s->ctx->device);
         if (s->coords) cudaFree(s->coords);  // every session call is synchronous
-        for (int k = 0; k < 2; ++k) {
-            if (s->list[k]) cudaFree(s->list[k]);
-            if (s->loff[k]) cudaFree(s->loff[k]);
-        }
+        if (s->ref_coords) cudaFree(s->ref_coords);
         if (s->dwork) cudaFree(s->dwork);
         if (s->prefix_exec) cudaGraphExecDestroy(s->prefix_exec);
         ddm_destroy(s->ctx);
@@ -996,7 +993,6 @@ int ddm_session_count(ddm_session* s, void* stream, uint64_t* K_out) {
     DeviceGuard g(c->device);
     c->stream = reinterpret_cast<cudaStream_t>(stream);
     s->counted = false;
-    s->pending = false;  // a new timestep replaces an undelivered change report
     int rc = session_prefix(s);
     if (rc) return rc;
     uint64_t K = 0;
@@ -1023,6 +1019,29 @@ int ddm_session_emit(ddm_session* s, void* stream, int32_t* pairs, uint64_t cap,
     return finish(c, K_out);
 }
 
+// Sort scratch of one radix sort of up to E KeyT keys in `passes` passes,
+// carved with its zeroed part (status words, total, group sums) first;
+// [zb, ze) is that part's byte range, to be cleared before every sort.
+}  // extern "C"
+
+namespace {
+template <typename KeyT>
+void carve_sort(Carve& cv, uint64_t E, int passes, SortScratch& sc, size_t& zb,
+                       size_t& ze) {
+    const uint64_t tiles = sort_tiles<KeyT>(E);
+    zb = (cv.off + 255) & ~(size_t)255;
+    sc.status = cv.take<unsigned long long>((size_t)passes * sort_status_stride(E));
+    sc.total = cv.take<unsigned long long>(1);
+    const size_t gw = sort_group_words(tiles, passes);
+    sc.grp = gw ? cv.take<uint32_t>(gw) : nullptr;
+    ze = cv.off;
+    sc.tile_hist = cv.take<uint32_t>(tiles * RADIX);
+    sc.offs = cv.take<unsigned long long>(tiles * RADIX + 1);
+}
+}  // namespace
+
+extern "C" {
+
 int ddm_session_emit_delta(ddm_session* s, void* stream, int32_t* added, uint64_t cap_added,
                            int32_t* removed, uint64_t cap_removed, uint64_t* n_added,
                            uint64_t* n_removed) {
@@ -1031,96 +1050,151 @@ int ddm_session_emit_delta(ddm_session* s, void* stream, int32_t* added, uint64_
     DeviceGuard g(c->device);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     c->stream = st;
+    if (!s->counted)
+        return fail(c, DDM_ERR_INVALID, "ddm_session_emit_delta needs ddm_session_count first");
+    if ((!added && cap_added) || (!removed && cap_removed))
+        return fail(c, DDM_ERR_INVALID, "output is NULL but its capacity is not 0");
+    if ((reinterpret_cast<uintptr_t>(added) | reinterpret_cast<uintptr_t>(removed)) & 7u)
+        return fail(c, DDM_ERR_INVALID, "added and removed must be 8-byte aligned");
     const Job job = session_job(s);
-    const int64_t n = job.n;
-    const int cur = s->ref ^ 1;
+    const int d = job.d;
+    const int64_t n = job.n, m = job.m;
+    const size_t coord_bytes = (size_t)2 * d * (n + m) * sizeof(float);
     int rc;
-    if (s->counted) {  // this timestep's pairs into the session's list
-        rc = ensure(c, &s->list[cur], &s->list_size[cur], std::max<size_t>(16, 8 * s->K));
+    // Room for the reference coordinates before anything is consumed.
+    {
+        char* p = reinterpret_cast<char*>(s->ref_coords);
+        rc = ensure(c, &p, &s->ref_size, std::max<size_t>(coord_bytes, 16));
+        s->ref_coords = reinterpret_cast<float*>(p);
         if (rc) return rc;
-        rc = ensure(c, &s->loff[cur], &s->loff_size[cur], 8 * (size_t)(n + 1));
+    }
+    if (!s->have_ref) {  // the first report: every pair of this timestep is new
+        if (n_added) *n_added = s->K;
+        if (n_removed) *n_removed = 0;
+        if (s->K > cap_added)
+            return fail(c, DDM_ERR_CAPACITY, "change report does not fit: " +
+                                                 std::to_string(s->K) + " added, 0 removed");
+        if (s->K && !added) return fail(c, DDM_ERR_INVALID, "output is NULL");
+        s->counted = false;  // the emission consumes the kept state
+        rc = enqueue(c, job, Mode::Match, added, cap_added, nullptr, Phase::Suffix);
         if (rc) return rc;
-        s->counted = false;
-        rc = enqueue(c, job, Mode::Match, reinterpret_cast<int32_t*>(s->list[cur]), s->K, nullptr,
-                     Phase::Suffix);
-        if (rc) return rc;
-        Plan pl;  // the layout the emission just used: its offsets off[0..n]
-        pl.layout(c->ws, job.d, job.n, job.m, Mode::Match, job.num_inst, c->win_shift, c->nd_path);
-        CK(cudaMemcpyAsync(s->loff[cur], pl.off, 8 * (size_t)(n + 1), cudaMemcpyDeviceToDevice, st));
+        if (coord_bytes)
+            CK(cudaMemcpyAsync(s->ref_coords, s->coords, coord_bytes, cudaMemcpyDeviceToDevice, st));
         rc = finish(c, nullptr);
         if (rc) return rc;
-        s->K_new = s->K;
-        s->pending = true;
-    }
-    if (!s->pending)
-        return fail(c, DDM_ERR_INVALID, "ddm_session_emit_delta needs ddm_session_count first");
-    if (!s->have_ref) {  // before the first report: an empty reference list
-        rc = ensure(c, &s->list[s->ref], &s->list_size[s->ref], 16);
-        if (rc) return rc;
-        rc = ensure(c, &s->loff[s->ref], &s->loff_size[s->ref], 8 * (size_t)(n + 1));
-        if (rc) return rc;
-        CK(cudaMemsetAsync(s->loff[s->ref], 0, 8 * (size_t)(n + 1), st));
-        s->K_ref = 0;
         s->have_ref = true;
+        return DDM_OK;
     }
-    // Work area: counts u32[n] x 2, offsets u64[n + 1] x 2, scan status x 2.
-    const size_t stat_words = (size_t)ceil_div((uint64_t)n, OFF_TILE) + 2;
-    Carve cv;  // sizes only
-    cv.take<uint32_t>(n);
-    cv.take<uint32_t>(n);
-    cv.take<unsigned long long>(n + 1);
-    cv.take<unsigned long long>(n + 1);
-    const size_t stat_off = (cv.off + 255) & ~(size_t)255;  // where take() puts the status
-    cv.take<unsigned long long>(stat_words);
-    cv.take<unsigned long long>(stat_words);
-    rc = ensure(c, &s->dwork, &s->dwork_size, cv.off);
-    if (rc) return rc;
-    Carve real;
-    real.base = s->dwork;
-    uint32_t* add_cnt = real.take<uint32_t>(n);
-    uint32_t* rem_cnt = real.take<uint32_t>(n);
-    unsigned long long* add_off = real.take<unsigned long long>(n + 1);
-    unsigned long long* rem_off = real.take<unsigned long long>(n + 1);
-    unsigned long long* st_add = real.take<unsigned long long>(stat_words);
-    unsigned long long* st_rem = real.take<unsigned long long>(stat_words);
-    if ((char*)st_add != s->dwork + stat_off) return fail(c, DDM_ERR_INTERNAL, "work layout");
-    CK(cudaMemsetAsync(s->dwork + stat_off, 0, cv.off - stat_off, st));
-    CK(cudaMemsetAsync(c->dstat, 0, sizeof(DevStatus), st));
-    PdlScope pdl_scope(c->pdl);
-    DeltaArgs da{};
-    da.n = n;
-    da.prev = reinterpret_cast<const int32_t*>(s->list[s->ref]);
-    da.prev_off = reinterpret_cast<const unsigned long long*>(s->loff[s->ref]);
-    da.cur = reinterpret_cast<const int32_t*>(s->list[cur]);
-    da.cur_off = reinterpret_cast<const unsigned long long*>(s->loff[cur]);
-    da.add_cnt = add_cnt;
-    da.rem_cnt = rem_cnt;
-    c->stats.launches += launch_delta(da, false, c->dstat, st);
-    c->stats.launches += launch_offsets(add_cnt, n, add_off, ~0ull, &c->dstat->aux[0], st_add,
-                                        c->dstat, st);
-    c->stats.launches += launch_offsets(rem_cnt, n, rem_off, ~0ull, &c->dstat->aux[1], st_rem,
-                                        c->dstat, st);
-    rc = finish(c, nullptr);
-    if (rc) return rc;
-    const uint64_t na = c->hstat->aux[0], nr = c->hstat->aux[1];
-    if (n_added) *n_added = na;
-    if (n_removed) *n_removed = nr;
-    if (na > cap_added || nr > cap_removed)
-        return fail(c, DDM_ERR_CAPACITY, "change report does not fit: " + std::to_string(na) +
-                                             " added, " + std::to_string(nr) + " removed");
-    if ((na && !added) || (nr && !removed)) return fail(c, DDM_ERR_INVALID, "output is NULL");
-    da.add_off = add_off;
-    da.rem_off = rem_off;
-    da.added = added;
-    da.removed = removed;
-    c->stats.launches += launch_delta(da, true, c->dstat, st);
-    rc = finish(c, nullptr);
-    if (rc) return rc;
-    s->ref = cur;  // the new list is the reference of the next report
-    s->K_ref = s->K_new;
-    s->pending = false;
-    return DDM_OK;
+    // Later reports: candidates from the coordinates that moved.
+    Plan pl;  // the layout of the count phase that produced the sorted stream
+    pl.layout(c->ws, d, n, m, Mode::Match, 0, c->win_shift, c->nd_path);
+    DeltaArgs a{};
+    a.d = d; a.n = (uint32_t)n; a.m = (uint32_t)m;
+    a.E = (uint32_t)pl.E;
+    a.keys = reinterpret_cast<const uint32_t*>((pl.passes & 1) ? pl.keys1 : pl.keys0);
+    a.vals = (pl.passes & 1) ? pl.vals1 : pl.vals0;
+    for (int q = 0; q < 4; ++q)
+        for (int k = 0; k < d; ++k) {
+            const float* nowp = s->ptrs[q][k];
+            const float* refp = s->ref_coords + (nowp - s->coords);  // same layout
+            switch (q) {
+                case 0: a.now.sub_lo[k] = nowp; a.ref.sub_lo[k] = refp; break;
+                case 1: a.now.sub_hi[k] = nowp; a.ref.sub_hi[k] = refp; break;
+                case 2: a.now.upd_lo[k] = nowp; a.ref.upd_lo[k] = refp; break;
+                default: a.now.upd_hi[k] = nowp; a.ref.upd_hi[k] = refp; break;
+            }
+        }
+    a.ibits = id_bits(n);
+    a.jbits = id_bits(m);
+    a.counters = &c->dstat->aux[2];  // [2] added, [3] removed, [4] write cursor
+    uint32_t* flags = reinterpret_cast<uint32_t*>(&c->dstat->aux[5]);
+    const int passes = (int)ceil_div((uint64_t)(1 + a.ibits + a.jbits), RADIX_BITS);
+    // The change keys' room: grows when a report overflows it (then rerun).
+    if (s->delta_cap == 0) s->delta_cap = std::max<uint64_t>(4096, s->K / 64);
+    for (int attempt = 0; attempt < 3; ++attempt) {
+        const uint64_t cap = s->delta_cap;
+        SortScratch sc32{}, sc64{};
+        size_t zb32 = 0, ze32 = 0, zb64 = 0, ze64 = 0;
+        uint32_t *tmp[2] = {}, *vb[2] = {};
+        uint4* pk = nullptr;
+        unsigned long long* kb[2] = {};
+        auto carve = [&](Carve& cv) {
+            a.disp = cv.take<unsigned long long>(DDM_MAX_DIMS);
+            for (int k = 1; k < d; ++k) {
+                a.lo_key[k - 1] = cv.take<uint32_t>(m);
+                a.lo_id[k - 1] = cv.take<uint32_t>(m);
+                a.hi_key[k - 1] = cv.take<uint32_t>(m);
+                a.hi_id[k - 1] = cv.take<uint32_t>(m);
+            }
+            tmp[0] = cv.take<uint32_t>(d > 1 ? m : 0);
+            tmp[1] = cv.take<uint32_t>(d > 1 ? m : 0);
+            if (d > 1) carve_sort<uint32_t>(cv, (uint64_t)m, 4, sc32, zb32, ze32);
+            pk = cv.take<uint4>(pl.E);
+            kb[0] = cv.take<unsigned long long>(cap);
+            kb[1] = cv.take<unsigned long long>(cap);
+            vb[0] = cv.take<uint32_t>(cap);
+            vb[1] = cv.take<uint32_t>(cap);
+            carve_sort<unsigned long long>(cv, cap, passes, sc64, zb64, ze64);
+        };
+        Carve sz;
+        carve(sz);
+        rc = ensure(c, &s->dwork, &s->dwork_size, sz.off + 256);
+        if (rc) return rc;
+        Carve cv;
+        cv.base = s->dwork;
+        carve(cv);
+        a.pk = pk;
+        a.keys_out = kb[0];
+        a.cap = cap;
+        PdlScope pdl_scope(c->pdl);
+        uint64_t& L = c->stats.launches;
+        CK(cudaMemsetAsync(c->dstat, 0, sizeof(DevStatus), st));
+        CK(cudaMemsetAsync(a.disp, 0, DDM_MAX_DIMS * sizeof(unsigned long long), st));
+        L += launch_delta_disp(a, c->dstat, st);
+        L += launch_delta_refk(a, pk, st);
+        if (d > 1 && m > 0) {
+            L += launch_delta_keys(a, st);
+            for (int k = 1; k < d; ++k)
+                for (int b = 0; b < 2; ++b) {
+                    CK(cudaMemsetAsync(s->dwork + zb32, 0, ze32 - zb32, st));
+                    uint32_t* key = const_cast<uint32_t*>(b ? a.hi_key[k - 1] : a.lo_key[k - 1]);
+                    uint32_t* id = const_cast<uint32_t*>(b ? a.hi_id[k - 1] : a.lo_id[k - 1]);
+                    L += launch_radix_sort<uint32_t>(key, id, tmp[0], tmp[1], (uint64_t)m, 4,
+                                                     sc32, false, c->dstat, st);
+                }
+        }
+        L += launch_delta_cand(a, c->dstat, st);
+        L += launch_delta_pad(a, st);
+        CK(cudaMemsetAsync(s->dwork + zb64, 0, ze64 - zb64, st));
+        L += launch_radix_sort<unsigned long long>(kb[0], vb[0], kb[1], vb[1], cap, passes, sc64,
+                                                   false, c->dstat, st);
+        L += launch_delta_finish(a, kb[passes & 1], added, cap_added, removed, cap_removed, flags,
+                                 s->ref_coords, s->coords, coord_bytes / sizeof(float), st);
+        rc = finish(c, nullptr);
+        if (rc) return rc;
+        const uint64_t na = c->hstat->aux[2], nr = c->hstat->aux[3];
+        const uint32_t f = static_cast<uint32_t>(c->hstat->aux[5]);
+        if (n_added) *n_added = na;
+        if (n_removed) *n_removed = nr;
+        if (f & DELTA_RERUN) {  // nothing was written or committed: again, with room
+            s->delta_cap = (na + nr) + (na + nr) / 4 + 4096;
+            continue;
+        }
+        if (f & DELTA_CAPACITY)
+            return fail(c, DDM_ERR_CAPACITY, "change report does not fit: " + std::to_string(na) +
+                                                 " added, " + std::to_string(nr) + " removed");
+        // The next report's room follows this one's size (the sort's cost is
+        // proportional to the room).
+        s->delta_cap = (na + nr) + (na + nr) / 4 + 4096;
+        s->counted = false;  // one report per timestep: the next one needs a new count
+        return DDM_OK;
+    }
+    return fail(c, DDM_ERR_INTERNAL, "change report: key room kept overflowing");
 }
+
+}  // extern "C"
+
+extern "C" {
 
 // The paper's comparison matchers (Algorithms 2 and 3) on the GPU, with the
 // result contract of ddm_match.  `pairs` NULL (and cap 0): count only.

@@ -1,33 +1,74 @@
-// Change report between two sorted pair lists of one session (incremental
-// matching): interfaces.
+// Incremental matching for served sessions (the change report): interfaces.
 #pragma once
 
 #include <cstdint>
 #include <cuda_runtime.h>
 
-#include "common.cuh"
+#include "emit.cuh"
 
 namespace ddm {
 
-// Two lists of (sub, upd) pairs, both sorted lexicographically and grouped by
-// subscription through their offsets (off[i] .. off[i+1] is sub i's segment).
+// One change report between the reference coordinates (those of the last
+// delivered report) and the current ones.  A pair's status changes only if
+// one of its elementary comparisons changes: c1(k) = [U.lo_k <= S.hi_k] or
+// c2(k) = [S.lo_k <= U.hi_k] for some dimension k (on order-preserving keys,
+// ties as in Algorithm 1).  If a comparison of two endpoints changed, the two
+// are now at most 2 disp[k] apart, disp[k] being the largest displacement of
+// any endpoint along k: candidates are the endpoint pairs that close.
 struct DeltaArgs {
-    int64_t n;                                 // subscriptions
-    const int32_t* prev;                       // previous list (2 ints per pair)
-    const unsigned long long* prev_off;        // n + 1
-    const int32_t* cur;                        // current list
-    const unsigned long long* cur_off;         // n + 1
-    uint32_t* add_cnt;                         // count pass: |cur_i \ prev_i|
-    uint32_t* rem_cnt;                         // count pass: |prev_i \ cur_i|
-    const unsigned long long* add_off;         // write pass: exclusive scans of the counts
-    const unsigned long long* rem_off;
-    int32_t* added;                            // write pass: pairs of cur not in prev
-    int32_t* removed;                          // write pass: pairs of prev not in cur
+    int d;
+    uint32_t n, m;
+    DimPtrs now, ref;               // current and reference coordinates (device)
+    // Dimension 0: the sorted endpoint stream of the current count phase.
+    uint32_t E;
+    const uint32_t* keys;           // sorted keys (E)
+    const uint32_t* vals;           // sorted payloads (kind << 30) | id (E)
+    // Dimensions 1..d-1: the updates' current bounds sorted by key, per dimension
+    // (index k - 1): lower bounds (c1 candidates) and upper bounds (c2).
+    const uint32_t* lo_key[DDM_MAX_DIMS - 1];
+    const uint32_t* lo_id[DDM_MAX_DIMS - 1];
+    const uint32_t* hi_key[DDM_MAX_DIMS - 1];
+    const uint32_t* hi_id[DDM_MAX_DIMS - 1];
+    const uint4* pk;                // dimension 0, per stream position: {current key,
+                                    // reference key, payload, 0} (E)
+    unsigned long long* disp;       // per dimension: bits of the largest |now - ref| (double)
+    unsigned long long* counters;   // [0] added, [1] removed, [2] write cursor
+    unsigned long long* keys_out;   // (removed << (ibits + jbits)) | (i << jbits) | j per
+                                    // changed pair, at most cap entries
+    unsigned long long cap;
+    int ibits, jbits;
 };
 
-// Count pass (write = false) or write pass (write = true), one warp per
-// subscription.  The write pass checks its counts against the offsets and
-// raises DDM_ERR_INTERNAL on a mismatch.
-int launch_delta(const DeltaArgs& a, bool write, DevStatus* st, cudaStream_t s);
+// Outcome flags of a report, set on the device (flags[0]).
+constexpr uint32_t DELTA_RERUN = 1u;     // more changed pairs than keys_out holds
+constexpr uint32_t DELTA_CAPACITY = 2u;  // more than the caller's buffers hold
+
+// disp[k] for every dimension (disp zeroed).
+int launch_delta_disp(const DeltaArgs& a, DevStatus* st, cudaStream_t s);
+
+// Keys and ids of the updates' bounds of dimensions 1..d-1, unsorted, into
+// a.lo_key/lo_id/hi_key/hi_id (the caller then sorts each pair by key).
+int launch_delta_keys(const DeltaArgs& a, cudaStream_t s);
+
+// pk[p] = {keys[p], reference key (dimension 0) of the endpoint at stream
+// position p, vals[p], 0}, and disp[0].
+int launch_delta_refk(const DeltaArgs& a, uint4* pk, cudaStream_t s);
+
+// The changed pairs, each exactly once: counters[0], [1] count them, and their
+// keys go to keys_out while there is room.
+int launch_delta_cand(const DeltaArgs& a, DevStatus* st, cudaStream_t s);
+
+// keys_out[q] = ~0 for q in [count, cap), so that a sort of all cap entries
+// leaves the pairs first.
+int launch_delta_pad(const DeltaArgs& a, cudaStream_t s);
+
+// From the sorted keys: the added pairs into `added`, the removed ones into
+// `removed` (flag bit stripped), unless they overflow keys_out (flags |=
+// DELTA_RERUN) or the caller's capacities (flags |= DELTA_CAPACITY); then, if
+// no flag is set, the current coordinates become the reference.
+int launch_delta_finish(const DeltaArgs& a, const unsigned long long* sorted, int32_t* added,
+                        uint64_t cap_added, int32_t* removed, uint64_t cap_removed,
+                        uint32_t* flags, float* ref_coords, const float* coords,
+                        uint64_t coord_count, cudaStream_t s);
 
 }  // namespace ddm

@@ -1,204 +1,455 @@
 // Incremental matching for served sessions: the pairs that appeared and the
-// pairs that disappeared between two timesteps.
+// pairs that disappeared since the last delivered report.
 //
 // Paper: Section 6 names dynamic DDM (regions that move between timesteps) as
-// future work; SBM itself recomputes the full match.  Here the full match of
-// the new timestep is computed as usual and compared with the previous one.
-// Both lists are sorted by (sub, upd) and grouped by subscription, so the
-// comparison splits into one comparison per subscription of two short sorted
-// runs of update ids: an id of the new run that is absent from the old run is
-// an added pair, an id of the old run absent from the new one a removed pair.
-// One warp per subscription stages both runs in shared memory and merges them
-// (merge path split over the lanes); a run longer than DELTA_STAGE is instead
-// searched in global memory, id by id, with ballots keeping the order.
+// future work; SBM itself recomputes the full match.  Here nothing is
+// recomputed in full.  By Algorithm 1 and Section 3 a pair intersects iff the
+// 2d comparisons c1(k) = [U.lo_k <= S.hi_k] and c2(k) = [S.lo_k <= U.hi_k] all
+// hold, so its status can change only if one of them changes.  If a
+// comparison between endpoints a and b changed, then, with every endpoint of
+// dimension k displaced by at most D_k, the two are now at most 2 D_k apart
+// (a <= b before and a > b now give 0 < a' - b' <= (a' - a) - (b' - b)).  So
+// the candidates of comparison (k, t) of S_i are the update bounds within
+// 2 D_k of S_i's bound: for dimension 0 a walk in the sorted endpoint stream
+// that the count phase has just produced (one thread per stream position, so
+// neighbouring threads walk neighbouring ranges), for the other dimensions a
+// binary search in the updates' bounds sorted per dimension.  A candidate is
+// kept if its predicate differs between the reference and the current
+// coordinates and (k, t) is the first of its comparisons, in the order
+// c1(0), c2(0), c1(1), ..., that changed: each changed pair is found exactly
+// once.
+#include <algorithm>
+
 #include "delta.cuh"
 
 namespace ddm {
 
 constexpr int DELTA_BLOCK = 256;
-constexpr int DELTA_WARPS = DELTA_BLOCK / 32;
-constexpr uint32_t DELTA_STAGE = 256;  // ids per run staged in shared memory
 
-// Whether id v occurs in the ascending run ids[0..len).  Staged runs
-// (len <= DELTA_STAGE, shared memory): a branch-free search of fixed length
-// whose position never passes DELTA_STAGE - 1, so the final probe covers the
-// last element.  Longer runs (global memory, ids at stride 2): a plain one.
-__device__ __forceinline__ bool staged_has(const int32_t* ids, uint32_t len, int32_t v) {
-    static_assert((DELTA_STAGE & (DELTA_STAGE - 1)) == 0, "power of two");
-    uint32_t pos = 0;
-#pragma unroll
-    for (uint32_t step = DELTA_STAGE / 2; step > 0; step >>= 1)
-        if (pos + step <= len && ids[pos + step - 1] < v) pos += step;
-    return pos < len && ids[pos] == v;
+// |now - ref| along one bound; 0 when the value did not change (which also
+// covers an infinite bound that stays infinite).
+__device__ __forceinline__ double moved(float now, float ref) {
+    return now == ref ? 0.0 : fabs((double)now - (double)ref);
 }
 
-__device__ __forceinline__ bool global_has(const int32_t* pair_ids, uint32_t len, int32_t v) {
-    uint32_t lo = 0, hi = len;
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (pair_ids[2 * mid] < v) lo = mid + 1;
-        else hi = mid;
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
     }
-    return lo < len && pair_ids[2 * lo] == v;
+    return v;
 }
 
-// Pairs of the run `src` (len_src pairs; its ids staged in src_stage when it
-// fits) whose update id is absent from the run `other`; returns how many, and
-// in the write pass stores them in order from out.
-template <bool WRITE>
-__device__ __forceinline__ uint32_t run_minus(const int32_t* src, uint32_t len_src,
-                                              const int32_t* src_stage, const int32_t* other,
-                                              uint32_t len_other, const int32_t* other_stage,
-                                              int32_t sub, int32_t* out, int lane) {
-    const unsigned lt = (1u << lane) - 1u;
-    uint32_t cnt = 0;
-    for (uint32_t k0 = 0; k0 < len_src; k0 += 32) {
-        const uint32_t k = k0 + lane;
-        bool keep = false;
-        int32_t v = 0;
-        if (k < len_src) {
-            v = src_stage ? src_stage[k] : src[2 * k + 1];
-            keep = other_stage ? !staged_has(other_stage, len_other, v)
-                               : !global_has(other + 1, len_other, v);
-        }
-        const unsigned bal = __ballot_sync(0xffffffffu, keep);
-        if (WRITE && keep) {
-            int32_t* p = out + 2 * (uint64_t)(cnt + __popc(bal & lt));
-            p[0] = sub;
-            p[1] = v;
-        }
-        cnt += __popc(bal);
-    }
-    return cnt;
-}
-
-// Both runs staged (shared memory, ascending ids): one merge of the two runs,
-// split over the warp by merge path (ties take the old run first).  Lane l
-// walks positions [l * seg, (l + 1) * seg) of the merged sequence.  A new id
-// is old iff the old element just before it (in merge order) is equal; an old
-// id survives iff the next new element is equal -- both looked up in the
-// staged runs, so an equal pair split between two lanes is still seen.  The
-// walk is done once to count and, in the write pass, again to store at the
-// lane's offsets (warp exclusive scans), which keeps both outputs in order.
-template <bool WRITE>
-__device__ __forceinline__ void merge_minus(const int32_t* A, uint32_t la, const int32_t* B,
-                                            uint32_t lb, int32_t sub, int32_t* out_add,
-                                            int32_t* out_rem, int lane, uint32_t& n_add,
-                                            uint32_t& n_rem) {
-    const uint32_t L = la + lb;
-    const uint32_t seg = (L + 31) / 32;
-    const uint32_t d0 = min((uint32_t)lane * seg, L), d1 = min(d0 + seg, L);
-    uint32_t lo = d0 > lb ? d0 - lb : 0u, hi = min(d0, la);
-    while (lo < hi) {  // merge-path split point on diagonal d0
-        const uint32_t mid = (lo + hi) >> 1;
-        if (A[mid] <= B[d0 - mid - 1]) lo = mid + 1;
-        else hi = mid;
-    }
-    const uint32_t i0 = lo, j0 = d0 - lo;
-    uint32_t add = 0, rem = 0;
-    {
-        uint32_t i = i0, j = j0;
-        for (uint32_t p = d0; p < d1; ++p) {
-            if (i < la && (j >= lb || A[i] <= B[j])) {
-                rem += (j < lb && B[j] == A[i]) ? 0u : 1u;
-                ++i;
-            } else {
-                add += (i > 0 && A[i - 1] == B[j]) ? 0u : 1u;
-                ++j;
-            }
-        }
-    }
-    uint32_t xa = add, xr = rem;  // inclusive warp scans
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t ya = __shfl_up_sync(0xffffffffu, xa, o);
-        const uint32_t yr = __shfl_up_sync(0xffffffffu, xr, o);
-        if (lane >= o) { xa += ya; xr += yr; }
-    }
-    n_add = __shfl_sync(0xffffffffu, xa, 31);
-    n_rem = __shfl_sync(0xffffffffu, xr, 31);
-    if (WRITE) {
-        uint32_t oa = xa - add, orr = xr - rem;
-        uint32_t i = i0, j = j0;
-        for (uint32_t p = d0; p < d1; ++p) {
-            if (i < la && (j >= lb || A[i] <= B[j])) {
-                if (!(j < lb && B[j] == A[i])) {
-                    out_rem[2 * (uint64_t)orr] = sub;
-                    out_rem[2 * (uint64_t)orr + 1] = A[i];
-                    ++orr;
-                }
-                ++i;
-            } else {
-                if (!(i > 0 && A[i - 1] == B[j])) {
-                    out_add[2 * (uint64_t)oa] = sub;
-                    out_add[2 * (uint64_t)oa + 1] = B[j];
-                    ++oa;
-                }
-                ++j;
-            }
-        }
-    }
-}
-
-template <bool WRITE>
-__global__ void __launch_bounds__(DELTA_BLOCK) k_delta(DeltaArgs a, DevStatus* st) {
+// Non-negative doubles order like their bit patterns, so the maximum is kept
+// as an integer maximum of the bits.
+__global__ void k_delta_disp(DeltaArgs a, DevStatus* st) {
     pdl_begin();
-    __shared__ int32_t s_a[DELTA_WARPS][DELTA_STAGE];
-    __shared__ int32_t s_b[DELTA_WARPS][DELTA_STAGE];
     if (read_error(st)) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t warps = (int64_t)gridDim.x * DELTA_WARPS;
-    for (int64_t i = (int64_t)blockIdx.x * DELTA_WARPS + warp; i < a.n; i += warps) {
-        if (WRITE && a.add_off[i + 1] == a.add_off[i] && a.rem_off[i + 1] == a.rem_off[i])
-            continue;  // the count pass found nothing to report for this subscription
-        const uint64_t pa0 = a.prev_off[i], pa1 = a.prev_off[i + 1];
-        const uint64_t cb0 = a.cur_off[i], cb1 = a.cur_off[i + 1];
-        if (pa1 < pa0 || cb1 < cb0) {
-            if (lane == 0) raise_error(st, DDM_ERR_INTERNAL, 20);
-            continue;
+    const uint64_t per_dim = 2ull * (a.n + a.m);
+    for (int k = 1; k < a.d; ++k) {  // dimension 0: k_delta_refk
+        double mx = 0.0;
+        for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < per_dim;
+             e += (uint64_t)gridDim.x * blockDim.x) {
+            const bool upd = e >= 2ull * a.n;
+            const uint64_t q = upd ? e - 2ull * a.n : e;
+            const uint32_t cnt = upd ? a.m : a.n;
+            const bool hi = q >= cnt;
+            const uint32_t id = (uint32_t)(hi ? q - cnt : q);
+            const float* pn = upd ? (hi ? a.now.upd_hi[k] : a.now.upd_lo[k])
+                                  : (hi ? a.now.sub_hi[k] : a.now.sub_lo[k]);
+            const float* pr = upd ? (hi ? a.ref.upd_hi[k] : a.ref.upd_lo[k])
+                                  : (hi ? a.ref.sub_hi[k] : a.ref.sub_lo[k]);
+            mx = fmax(mx, moved(pn[id], pr[id]));  // fmax drops a NaN (never produced)
         }
-        const uint32_t la = (uint32_t)(pa1 - pa0), lb = (uint32_t)(cb1 - cb0);
-        const int32_t* A = a.prev + 2 * pa0;
-        const int32_t* B = a.cur + 2 * cb0;
-        const int32_t* sa = nullptr;
-        const int32_t* sb = nullptr;
-        __syncwarp();
-        if (la <= DELTA_STAGE) {
-            for (uint32_t k = lane; k < la; k += 32) s_a[warp][k] = A[2 * k + 1];
-            sa = s_a[warp];
-        }
-        if (lb <= DELTA_STAGE) {
-            for (uint32_t k = lane; k < lb; k += 32) s_b[warp][k] = B[2 * k + 1];
-            sb = s_b[warp];
-        }
-        __syncwarp();
-        int32_t* out_add = WRITE ? a.added + 2 * a.add_off[i] : nullptr;
-        int32_t* out_rem = WRITE ? a.removed + 2 * a.rem_off[i] : nullptr;
-        uint32_t na, nr;
-        if (sa && sb) {
-            merge_minus<WRITE>(sa, la, sb, lb, (int32_t)i, out_add, out_rem, lane, na, nr);
-        } else {
-            na = run_minus<WRITE>(B, lb, sb, A, la, sa, (int32_t)i, out_add, lane);
-            nr = run_minus<WRITE>(A, la, sa, B, lb, sb, (int32_t)i, out_rem, lane);
-        }
-        if (lane == 0) {
-            if (!WRITE) {
-                a.add_cnt[i] = na;
-                a.rem_cnt[i] = nr;
-            } else if (a.add_off[i + 1] - a.add_off[i] != na ||
-                       a.rem_off[i + 1] - a.rem_off[i] != nr) {
-                raise_error(st, DDM_ERR_INTERNAL, 21);
-            }
-        }
+        const unsigned long long b = warp_max_u64((unsigned long long)__double_as_longlong(mx));
+        if ((threadIdx.x & 31) == 0 && b) atomicMax(&a.disp[k], b);
     }
 }
 
-int launch_delta(const DeltaArgs& a, bool write, DevStatus* st, cudaStream_t s) {
-    if (a.n <= 0) return 0;
-    int64_t g = ceil_div((uint64_t)a.n, (uint64_t)DELTA_WARPS);
-    const unsigned grid = (unsigned)(g < 1 ? 1 : (g > 152 * 8 ? 152 * 8 : g));  // 8 blocks / SM
-    if (write) launch_k(k_delta<true>, grid, DELTA_BLOCK, 0, s, a, st);
-    else launch_k(k_delta<false>, grid, DELTA_BLOCK, 0, s, a, st);
+int launch_delta_disp(const DeltaArgs& a, DevStatus* st, cudaStream_t s) {
+    if (a.d < 2) return 0;
+    uint64_t g = ceil_div(2ull * (a.n + a.m), DELTA_BLOCK);
+    g = g < 1 ? 1 : (g > 152 * 8 ? 152 * 8 : g);
+    launch_k(k_delta_disp, (unsigned)g, DELTA_BLOCK, 0, s, a, st);
+    return 1;
+}
+
+__global__ void k_delta_keys(DeltaArgs a) {
+    pdl_begin();
+    const uint64_t total = (uint64_t)(a.d - 1) * a.m;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (uint64_t)gridDim.x * blockDim.x) {
+        const int k = 1 + (int)(e / a.m);
+        const uint32_t j = (uint32_t)(e % a.m);
+        const_cast<uint32_t*>(a.lo_key[k - 1])[j] = float_key(a.now.upd_lo[k][j]);
+        const_cast<uint32_t*>(a.lo_id[k - 1])[j] = j;
+        const_cast<uint32_t*>(a.hi_key[k - 1])[j] = float_key(a.now.upd_hi[k][j]);
+        const_cast<uint32_t*>(a.hi_id[k - 1])[j] = j;
+    }
+}
+
+int launch_delta_keys(const DeltaArgs& a, cudaStream_t s) {
+    if (a.d < 2 || a.m == 0) return 0;
+    uint64_t g = ceil_div((uint64_t)(a.d - 1) * a.m, DELTA_BLOCK);
+    g = g < 1 ? 1 : (g > 152 * 8 ? 152 * 8 : g);
+    launch_k(k_delta_keys, (unsigned)g, DELTA_BLOCK, 0, s, a);
+    return 1;
+}
+
+// Per dimension-0 stream position: the current key, the reference key of the
+// same endpoint (one gather per endpoint) and the payload, packed so that the
+// walks below read one 16-byte entry per step; and the largest displacement
+// along dimension 0 (disp[0]).
+__global__ void k_delta_refk(DeltaArgs a, uint4* __restrict__ pk) {
+    pdl_begin();
+    double mx = 0.0;
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < a.E; p += gridDim.x * blockDim.x) {
+        const uint32_t v = a.vals[p], kind = v >> 30, id = v & ID_MASK, key = a.keys[p];
+        const float* src = kind == KIND_SLO ? a.ref.sub_lo[0] : kind == KIND_ULO ? a.ref.upd_lo[0]
+                         : kind == KIND_SHI ? a.ref.sub_hi[0] : a.ref.upd_hi[0];
+        const float r = src[id];
+        pk[p] = make_uint4(key, float_key(r), v, 0u);
+        mx = fmax(mx, moved(key_float(key), r));
+    }
+    const unsigned long long b = warp_max_u64((unsigned long long)__double_as_longlong(mx));
+    if ((threadIdx.x & 31) == 0 && b) atomicMax(&a.disp[0], b);
+}
+
+int launch_delta_refk(const DeltaArgs& a, uint4* pk, cudaStream_t s) {
+    if (a.E == 0) return 0;
+    uint64_t g = ceil_div((uint64_t)a.E, DELTA_BLOCK);
+    g = g > 152 * 16 ? 152 * 16 : g;
+    launch_k(k_delta_refk, (unsigned)g, DELTA_BLOCK, 0, s, a, pk);
+    return 1;
+}
+
+// Comparison q = 2k + t of the pair (i, j) in the coordinates c: t = 0 is
+// c1(k) = [U.lo_k <= S.hi_k], t = 1 is c2(k) = [S.lo_k <= U.hi_k].
+__device__ __forceinline__ bool cmp_q(const DimPtrs& c, int q, uint32_t i, uint32_t j) {
+    const int k = q >> 1;
+    return (q & 1) ? float_key(c.sub_lo[k][i]) <= float_key(c.upd_hi[k][j])
+                   : float_key(c.upd_lo[k][j]) <= float_key(c.sub_hi[k][i]);
+}
+
+// (i, j), whose comparison q changed, is kept if no earlier comparison changed
+// and its predicate (all 2d comparisons) differs between reference and now;
+// returns 0 (not kept), 1 (appeared) or 2 (disappeared).
+__device__ __forceinline__ int first_change(const DeltaArgs& a, int q, uint32_t i, uint32_t j) {
+    for (int q2 = 0; q2 < q; ++q2)
+        if (cmp_q(a.ref, q2, i, j) != cmp_q(a.now, q2, i, j)) return 0;  // found through q2
+    bool pr = true, pn = true;
+    for (int q2 = 0; q2 < 2 * a.d && (pr || pn); ++q2) {
+        pr = pr && cmp_q(a.ref, q2, i, j);
+        pn = pn && cmp_q(a.now, q2, i, j);
+    }
+    return pr == pn ? 0 : (pn ? 1 : 2);
+}
+
+// A lane's changed pairs: the first DELTA_LANE_KEYS are held in registers and
+// written after a warp-wide slot reservation; further ones take a slot each.
+constexpr int DELTA_LANE_KEYS = 4;
+
+struct LaneKeys {
+    unsigned long long k[DELTA_LANE_KEYS];
+    int nb = 0;
+    unsigned long long n_add = 0, n_rem = 0;
+
+    __device__ __forceinline__ void put(const DeltaArgs& a, int kind, uint32_t i, uint32_t j) {
+        const unsigned long long which = kind == 1 ? 0ull : 1ull;
+        (kind == 1 ? n_add : n_rem) += 1;
+        const unsigned long long key =
+            (which << (a.ibits + a.jbits)) | ((unsigned long long)i << a.jbits) | j;
+        if (nb < DELTA_LANE_KEYS) {
+#pragma unroll
+            for (int q = 0; q < DELTA_LANE_KEYS; ++q)
+                if (q == nb) k[q] = key;  // register-resident (no dynamic index)
+            ++nb;
+            return;
+        }
+        const unsigned long long slot = atomicAdd(&a.counters[2], 1ull);
+        if (slot < a.cap) a.keys_out[slot] = key;
+    }
+
+    // Called by all 32 lanes of the warp together: the warp's keys into the
+    // block's shared buffer (one shared atomic per warp); what does not fit
+    // takes global slots directly.
+    __device__ __forceinline__ void stage(const DeltaArgs& a, int lane, unsigned long long* sbuf,
+                                          uint32_t* scnt, uint32_t scap) {
+        uint32_t incl = (uint32_t)nb;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        if (total == 0) return;
+        uint32_t base = 0;
+        if (lane == 31) base = atomicAdd(scnt, total);
+        base = __shfl_sync(0xffffffffu, base, 31) + (incl - (uint32_t)nb);
+#pragma unroll
+        for (int q = 0; q < DELTA_LANE_KEYS; ++q) {
+            if (q >= nb) break;
+            if (base + q < scap) {
+                sbuf[base + q] = k[q];
+            } else {
+                const unsigned long long slot = atomicAdd(&a.counters[2], 1ull);
+                if (slot < a.cap) a.keys_out[slot] = k[q];
+            }
+        }
+        nb = 0;
+    }
+
+    // Called by all 32 lanes of the warp together.
+    __device__ __forceinline__ void flush(const DeltaArgs& a, int lane) {
+        uint32_t incl = (uint32_t)nb;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        if (total == 0) return;
+        unsigned long long base = 0;
+        if (lane == 31) base = atomicAdd(&a.counters[2], (unsigned long long)total);
+        base = __shfl_sync(0xffffffffu, base, 31) + (incl - (uint32_t)nb);
+#pragma unroll
+        for (int q = 0; q < DELTA_LANE_KEYS; ++q)
+            if (q < nb && base + q < a.cap) a.keys_out[base + q] = k[q];
+        nb = 0;
+    }
+};
+
+// Keys of the values within r of x (a superset: bounds rounded outwards;
+// everything when r is not finite).
+__device__ __forceinline__ void key_window(float x, double r, uint32_t& klo, uint32_t& khi) {
+    if (!(r < 1e300)) {
+        klo = 0u;
+        khi = 0xffffffffu;
+        return;
+    }
+    const double lo = (double)x - r, hi = (double)x + r;
+    klo = float_key(__double2float_rd(lo));
+    khi = float_key(__double2float_ru(hi));
+    if (lo != lo) klo = 0u;            // x infinite: inf - inf
+    if (hi != hi) khi = 0xffffffffu;
+}
+
+__device__ __forceinline__ double radius(const DeltaArgs& a, int k) {
+    const double D = __longlong_as_double((long long)a.disp[k]);
+    return D == 0.0 ? 0.0 : 2.0 * D * (1.0 + 0x1p-30);
+}
+
+// Dimension 0: the stream positions, 64 per warp step; the subscription
+// bounds among them are handed out to the lanes (ballots), and each walks its
+// neighbourhood, testing each update bound of the other kind with the keys
+// alone (current and reference keys, packed per position).  Dimensions
+// k >= 1: items (k, t, i), 32 per warp step, by binary search.  The lanes of a
+// warp reserve their output slots together.
+__global__ void __launch_bounds__(DELTA_BLOCK) k_delta_cand(DeltaArgs a, DevStatus* st) {
+    pdl_begin();
+    if (read_error(st)) return;
+    constexpr uint32_t SBUF = 2048;  // keys staged per block iteration
+    __shared__ unsigned long long sbuf[SBUF];
+    __shared__ uint32_t scnt;
+    __shared__ unsigned long long sbase;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t warp_id = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    LaneKeys out;
+    const double D0 = __longlong_as_double((long long)a.disp[0]);
+    if (threadIdx.x == 0) scnt = 0;
+    __syncthreads();
+    // A block takes 8 x 64 stream positions per iteration (the same number of
+    // iterations for all its warps), stages their keys in shared memory and
+    // reserves global slots for all of them with one atomic.
+    constexpr uint32_t CHUNK = (DELTA_BLOCK / 32) * 64;
+    for (uint64_t cbase = (uint64_t)blockIdx.x * CHUNK; cbase < a.E;
+         cbase += (uint64_t)gridDim.x * CHUNK) {
+      const uint64_t base = cbase + (uint64_t)warp * 64;
+      if (base < a.E) {
+        const uint64_t p0 = base + lane, p1 = base + 32 + lane;
+        const uint32_t k0 = p0 < a.E ? a.pk[p0].z >> 30 : KIND_ULO;
+        const uint32_t k1 = p1 < a.E ? a.pk[p1].z >> 30 : KIND_ULO;
+        const unsigned m0 = __ballot_sync(0xffffffffu, k0 == KIND_SHI || k0 == KIND_SLO);
+        const unsigned m1 = __ballot_sync(0xffffffffu, k1 == KIND_SHI || k1 == KIND_SLO);
+        const int c0 = __popc(m0), tot = c0 + __popc(m1);
+        for (int r0 = 0; r0 < tot; r0 += 32) {  // up to 64 items: one or two rounds
+          const int it = r0 + lane;
+          if (it < tot) {
+            // Lane l takes item r0 + l: the (r0 + l)-th subscription bound of the
+            // 64 positions.
+            unsigned mm = it < c0 ? m0 : m1;
+            for (int t = it < c0 ? it : it - c0; t > 0; --t) mm &= mm - 1u;
+            const uint64_t pos = base + (it < c0 ? 0 : 32) + (uint32_t)(__ffs(mm) - 1);
+            const uint32_t p = (uint32_t)pos;
+            const uint4 ep = a.pk[p < a.E ? p : 0];  // mm != 0 and p < E by construction
+            const uint32_t kind = ep.z >> 30;
+            const bool t0 = kind == KIND_SHI;                 // c1: U lowers near S.hi
+            const uint32_t want = t0 ? KIND_ULO : KIND_UHI;   // c2: U uppers near S.lo
+            const uint32_t i = ep.z & ID_MASK, kp = ep.x, rp = ep.y;
+            // The walk covers every update bound within |d_p| + D of this bound:
+            // a changed comparison needs |now_q - now_p| <= |d_q - d_p| <= D + |d_p|.
+            const float xp = key_float(kp);
+            const double dp = moved(xp, key_float(rp));
+            const double rad = D0 == 0.0 ? 0.0 : (D0 + dp) * (1.0 + 0x1p-30);
+            uint32_t klo, khi;
+            key_window(xp, rad, klo, khi);
+            // This subscription's other bound along dimension 0 (loaded once, on
+            // the first changed comparison).
+            bool have_o = false;
+            uint32_t ko_now = 0, ko_ref = 0;
+            auto test = [&](const uint4 eq) {
+                if ((eq.z >> 30) != want) return;
+                const bool now = t0 ? eq.x <= kp : kp <= eq.x;
+                const bool ref = t0 ? eq.y <= rp : rp <= eq.y;
+                if (now == ref) return;
+                const uint32_t j = eq.z & ID_MASK;
+                if (!have_o) {
+                    ko_now = float_key(t0 ? a.now.sub_lo[0][i] : a.now.sub_hi[0][i]);
+                    ko_ref = float_key(t0 ? a.ref.sub_lo[0][i] : a.ref.sub_hi[0][i]);
+                    have_o = true;
+                }
+                // The update's other bound, now and then.
+                const uint32_t uo_now = float_key(t0 ? a.now.upd_hi[0][j] : a.now.upd_lo[0][j]);
+                const uint32_t uo_ref = float_key(t0 ? a.ref.upd_hi[0][j] : a.ref.upd_lo[0][j]);
+                // c1 = [U.lo <= S.hi], c2 = [S.lo <= U.hi] along dimension 0.
+                const bool c1n = t0 ? now : uo_now <= ko_now;
+                const bool c1r = t0 ? ref : uo_ref <= ko_ref;
+                const bool c2n = t0 ? ko_now <= uo_now : now;
+                const bool c2r = t0 ? ko_ref <= uo_ref : ref;
+                if (!t0 && c1n != c1r) return;  // found through c1(0)
+                bool pn = c1n && c2n, pr = c1r && c2r;
+                for (int q2 = 2; q2 < 2 * a.d && (pr || pn); ++q2) {
+                    pr = pr && cmp_q(a.ref, q2, i, j);
+                    pn = pn && cmp_q(a.now, q2, i, j);
+                }
+                if (pr != pn) out.put(a, pn ? 1 : 2, i, j);
+            };
+            for (uint32_t q = p; q-- > 0;) {
+                const uint4 eq = a.pk[q];
+                if (eq.x < klo) break;
+                test(eq);
+            }
+            for (uint32_t q = p + 1; q < a.E; ++q) {
+                const uint4 eq = a.pk[q];
+                if (eq.x > khi) break;
+                test(eq);
+            }
+          }
+          out.stage(a, lane, sbuf, &scnt, SBUF);
+        }
+      }
+      __syncthreads();
+      const uint32_t ns = scnt < SBUF ? scnt : SBUF;
+      if (threadIdx.x == 0) sbase = ns ? atomicAdd(&a.counters[2], (unsigned long long)ns) : 0ull;
+      __syncthreads();
+      for (uint32_t q = threadIdx.x; q < ns; q += DELTA_BLOCK)
+          if (sbase + q < a.cap) a.keys_out[sbase + q] = sbuf[q];
+      __syncthreads();
+      if (threadIdx.x == 0) scnt = 0;
+      __syncthreads();
+    }
+    (void)warp_id;
+    (void)warps;
+    const uint64_t other = 2ull * (a.d - 1) * a.n;
+    for (uint64_t base = warp_id * 32; base < other; base += warps * 32) {
+        const uint64_t r = base + lane;
+        if (r < other) {
+            const int k = 1 + (int)(r / (2ull * a.n));
+            const int t = (int)((r / a.n) & 1);
+            const uint32_t i = (uint32_t)(r % a.n);
+            const uint32_t* key = t == 0 ? a.lo_key[k - 1] : a.hi_key[k - 1];
+            const uint32_t* id = t == 0 ? a.lo_id[k - 1] : a.hi_id[k - 1];
+            uint32_t klo, khi;
+            key_window(t == 0 ? a.now.sub_hi[k][i] : a.now.sub_lo[k][i], radius(a, k), klo, khi);
+            uint32_t lo = 0, hi = a.m;  // first key >= klo
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (key[mid] < klo) lo = mid + 1;
+                else hi = mid;
+            }
+            for (uint32_t q = lo; q < a.m && key[q] <= khi; ++q) {
+                const uint32_t j = id[q];
+                if (cmp_q(a.ref, 2 * k + t, i, j) == cmp_q(a.now, 2 * k + t, i, j)) continue;
+                const int c = first_change(a, 2 * k + t, i, j);
+                if (c) out.put(a, c, i, j);
+            }
+        }
+        out.flush(a, lane);
+    }
+    // The counts, one atomic per warp and kind.
+    unsigned long long na = out.n_add, nr = out.n_rem;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        na += __shfl_xor_sync(0xffffffffu, na, o);
+        nr += __shfl_xor_sync(0xffffffffu, nr, o);
+    }
+    if (lane == 0) {
+        if (na) atomicAdd(&a.counters[0], na);
+        if (nr) atomicAdd(&a.counters[1], nr);
+    }
+}
+
+int launch_delta_cand(const DeltaArgs& a, DevStatus* st, cudaStream_t s) {
+    const uint64_t warps_needed =
+        std::max<uint64_t>(ceil_div(a.E, 64), ceil_div(2ull * (a.d - 1) * a.n, 32));
+    if (warps_needed == 0) return 0;
+    uint64_t g = ceil_div(warps_needed, DELTA_BLOCK / 32);
+    g = g > 152 * 16 ? 152 * 16 : g;
+    launch_k(k_delta_cand, (unsigned)g, DELTA_BLOCK, 0, s, a, st);
+    return 1;
+}
+
+__global__ void k_delta_pad(DeltaArgs a) {
+    pdl_begin();
+    const unsigned long long used = a.counters[2];
+    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < a.cap;
+         q += (uint64_t)gridDim.x * blockDim.x)
+        if (q >= used) a.keys_out[q] = ~0ull;
+}
+
+int launch_delta_pad(const DeltaArgs& a, cudaStream_t s) {
+    if (a.cap == 0) return 0;
+    uint64_t g = ceil_div(a.cap, DELTA_BLOCK);
+    g = g > 152 * 8 ? 152 * 8 : g;
+    launch_k(k_delta_pad, (unsigned)g, DELTA_BLOCK, 0, s, a);
+    return 1;
+}
+
+__global__ void k_delta_finish(DeltaArgs a, const unsigned long long* __restrict__ sorted,
+                               int2* __restrict__ added, uint64_t cap_added,
+                               int2* __restrict__ removed, uint64_t cap_removed,
+                               uint32_t* flags, float* __restrict__ ref_coords,
+                               const float* __restrict__ coords, uint64_t coord_count) {
+    pdl_begin();
+    const unsigned long long na = a.counters[0], nr = a.counters[1];
+    uint32_t f = 0;
+    if (na + nr > a.cap) f |= DELTA_RERUN;
+    else if (na > cap_added || nr > cap_removed) f |= DELTA_CAPACITY;
+    if (blockIdx.x == 0 && threadIdx.x == 0) flags[0] = f;
+    if (f) return;
+    const unsigned long long imask = (1ull << a.ibits) - 1ull, jmask = (1ull << a.jbits) - 1ull;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < na + nr; q += stride) {
+        const unsigned long long k = sorted[q];
+        const int2 pr = make_int2((int32_t)((k >> a.jbits) & imask), (int32_t)(k & jmask));
+        if (q < na) added[q] = pr;
+        else removed[q - na] = pr;
+    }
+    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < coord_count; q += stride)
+        ref_coords[q] = coords[q];  // the delivered report's coordinates: the next reference
+}
+
+int launch_delta_finish(const DeltaArgs& a, const unsigned long long* sorted, int32_t* added,
+                        uint64_t cap_added, int32_t* removed, uint64_t cap_removed,
+                        uint32_t* flags, float* ref_coords, const float* coords,
+                        uint64_t coord_count, cudaStream_t s) {
+    const uint64_t work = std::max<uint64_t>(a.cap, coord_count);
+    uint64_t g = ceil_div(work > 0 ? work : 1, DELTA_BLOCK);
+    g = g > 152 * 8 ? 152 * 8 : g;
+    launch_k(k_delta_finish, (unsigned)g, DELTA_BLOCK, 0, s, a, sorted,
+             reinterpret_cast<int2*>(added), cap_added, reinterpret_cast<int2*>(removed),
+             cap_removed, flags, ref_coords, coords, coord_count);
     return 1;
 }
 

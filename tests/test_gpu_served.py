@@ -189,28 +189,84 @@ def test_emit_delta_no_motion_and_capacity_retry(ddm):
     sess.close()
 
 
-def test_session_budget_covers_change_report_lists(ddm):
+def test_session_budget_covers_change_report_buffers(ddm):
     # A session's budget caps everything it holds on the device: the resident
-    # coordinates, the pipeline workspace and the two pair lists of the change
-    # report (8 K bytes each).  With room for the first two but not the lists,
-    # emit_delta fails with DDM_ERR_NOMEM before any launch, count and emit
-    # still work, and an oversized coordinate set is refused at creation.
+    # coordinates, the pipeline workspace, the reference coordinates and the
+    # buffers of a change report (16 bytes per changed pair).  A report with
+    # more changes than the budget allows fails with DDM_ERR_NOMEM before it
+    # writes anything; count and emit still work; an oversized coordinate set
+    # is refused at creation.
     import torch
-    reg = synth.large_1d(100.0, N=200_000)          # K ~ 1e7: one list is ~80 MB
-    want = oracle.sbm(reg)
+    reg = synth.large_1d(100.0, N=200_000)          # K ~ 1e7
+    side = synth.side_for(100.0, 200_000, 1)
     sess = ddm.Session(*to_dev(reg), mem_budget=64 << 20)
     try:
         K = sess.count()
-        assert K == len(want)
+        assert K == oracle.sbm_count(reg)
+        added, removed = sess.emit_delta()          # first report: into the caller's buffers
+        assert len(added) == K and len(removed) == 0
+        sess.drift(77, 0, 0.5 * side)               # millions of pairs change
+        host = synth.drift(reg, 77, 0, 0.5 * side)
+        want = oracle.sbm(host)
+        assert sess.count() == len(want)
         with pytest.raises(ddm.DDMError) as e:
             sess.emit_delta()
         assert e.value.code == ddm._lib.DDM_ERR_NOMEM
         sess.count()
-        out = torch.empty((K, 2), dtype=torch.int32, device="cuda:0")
-        assert sess.emit(out) == K
+        out = torch.empty((len(want), 2), dtype=torch.int32, device="cuda:0")
+        assert sess.emit(out) == len(want)
         assert np.array_equal(out.cpu().numpy(), want)
     finally:
         sess.close()
     with pytest.raises(ddm.DDMError) as e:
         ddm.Session(*to_dev(reg), mem_budget=1 << 20)  # 1.6 MB of coordinates
     assert e.value.code == ddm._lib.DDM_ERR_NOMEM
+
+
+@pytest.mark.parametrize("d,alpha", [(1, 100.0), (1, 0.01), (2, 100.0), (3, 1.0)])
+def test_emit_delta_against_last_delivered_report(ddm, d, alpha):
+    # Reports at steps 0, 1, 3 and 6 of a drifting workload (served drift,
+    # 0.1 side per step, and a slower one): each report is the difference from
+    # the last DELIVERED report, whatever happened in between.
+    N = 60_000 if d == 1 else 30_000
+    side = synth.side_for(alpha, N, d)
+    reg = synth.make_regions(d, N // 2, N - N // 2, side, 4400 + d)
+    for sigma in (0.1 * side, 0.01 * side):
+        sess = ddm.Session(*to_dev(reg))
+        host, prev = reg, None
+        for step in range(7):
+            sess.drift(91, step, sigma)
+            host = synth.drift(host, 91, step, sigma)
+            K = sess.count()
+            if step not in (0, 1, 3, 6):
+                continue
+            want = oracle.sbm(host)
+            assert K == len(want)
+            added, removed = sess.emit_delta()
+            base = np.zeros((0, 2), np.int32) if prev is None else prev
+            assert np.array_equal(added.cpu().numpy(), _rows_minus(want, base)), (sigma, step)
+            assert np.array_equal(removed.cpu().numpy(), _rows_minus(base, want)), (sigma, step)
+            prev = want
+        sess.close()
+
+
+def test_emit_delta_infinite_and_degenerate_bounds(ddm):
+    # Extents with infinite bounds (they stay infinite under drift), points,
+    # and touching extents: the report stays the exact set difference.
+    rng = np.random.default_rng(5)
+    from tests.helpers import tiny_grid_instance
+    reg = tiny_grid_instance(rng, 2, 300, 280, grid=16)
+    reg.sub_lo[0, :5] = -np.inf
+    reg.upd_hi[1, :7] = np.inf
+    sess = ddm.Session(*to_dev(reg))
+    host, prev = reg, np.zeros((0, 2), np.int32)
+    for step in range(4):
+        sess.drift(3, step, 0.7)
+        host = synth.drift(host, 3, step, 0.7)
+        want = oracle.sbm(host)
+        assert sess.count() == len(want)
+        added, removed = sess.emit_delta()
+        assert np.array_equal(added.cpu().numpy(), _rows_minus(want, prev)), step
+        assert np.array_equal(removed.cpu().numpy(), _rows_minus(prev, want)), step
+        prev = want
+    sess.close()
