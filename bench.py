@@ -348,25 +348,26 @@ def bench_served(dev, requests: int = 96, slots: int = 4, load: float = 0.8):
     for s_ in sims:
         s_.close()
 
-    # 1b) served capacity: the same requests all queued at once
-    sims = make_sims()
-    server = Server(sims, slots=slots)
-    t0 = time.perf_counter()
-    sat = [server.submit(int(k), arrival=t0) for k in order]
-    for r in sat:
-        r.done.wait(600)
-    sat_wall = max(r.finish for r in sat) - t0
-    server.close()
-    served_sat_pairs = sum(r.K for r in sat) / sat_wall
-    for s_ in sims:
-        s_.close()
-    def at_load(lf: float):
-        rate_ = lf * capacity
-        offsets = np.cumsum(np.random.default_rng(int(lf * 1000)).exponential(1.0 / rate_,
-                                                                              size=requests))
-        # served: continuous batching at the offered load
+    # 1b) served capacity: the same requests all queued at once, with `slots`
+    # slots (overlap) and with one slot (count reuse and resident state, no overlap)
+    def saturated(nslots):
         sims = make_sims()
-        server = Server(sims, slots=slots)
+        server = Server(sims, slots=nslots)
+        t0 = time.perf_counter()
+        sat = [server.submit(int(k), arrival=t0) for k in order]
+        for r in sat:
+            r.done.wait(600)
+        wall_ = max(r.finish for r in sat) - t0
+        server.close()
+        for s_ in sims:
+            s_.close()
+        return sum(r.K for r in sat) / wall_, wall_
+
+    served_sat_pairs, sat_wall = saturated(slots)
+    served1_sat_pairs, sat1_wall = saturated(1)
+    def served_at(offsets, nslots):
+        sims = make_sims()
+        server = Server(sims, slots=nslots)
         t0 = time.perf_counter()
         sreqs = []
         for k, off in zip(order, offsets):
@@ -378,9 +379,17 @@ def bench_served(dev, requests: int = 96, slots: int = 4, load: float = 0.8):
             r.done.wait(600)
         served_wall = max(r.finish for r in sreqs) - t0
         server.close()
-        srv = latency_summary(sreqs, served_wall)
         for s_ in sims:
             s_.close()
+        return latency_summary(sreqs, served_wall)
+
+    def at_load(lf: float):
+        rate_ = lf * capacity
+        offsets = np.cumsum(np.random.default_rng(int(lf * 1000)).exponential(1.0 / rate_,
+                                                                              size=requests))
+        # served: continuous batching at the offered load, and the one-slot server
+        srv = served_at(offsets, slots)
+        srv1 = served_at(offsets, 1)
         # plain at the same offered load (queueing included)
         sims = make_sims()
         t0 = time.perf_counter()
@@ -390,14 +399,16 @@ def bench_served(dev, requests: int = 96, slots: int = 4, load: float = 0.8):
         pln = latency_summary(preqs, plain_wall)
         for s_ in sims:
             s_.close()
-        return rate_, srv, pln
+        return rate_, srv, srv1, pln
 
     sweep = {}
     for lf in (0.5, 0.8, 1.0):
-        r_, srv, pln = at_load(lf)
+        r_, srv, srv1, pln = at_load(lf)
         sweep[str(lf)] = {"offered_rps": r_, "served_p50_ms": srv["p50_ms"],
-                          "served_p99_ms": srv["p99_ms"], "plain_p50_ms": pln["p50_ms"],
-                          "plain_p99_ms": pln["p99_ms"],
+                          "served_p99_ms": srv["p99_ms"],
+                          "served_1slot_p50_ms": srv1["p50_ms"],
+                          "served_1slot_p99_ms": srv1["p99_ms"],
+                          "plain_p50_ms": pln["p50_ms"], "plain_p99_ms": pln["p99_ms"],
                           "p99_speedup": pln["p99_ms"] / srv["p99_ms"] if srv["p99_ms"] else None}
         if lf == load:
             rate, served, plain = r_, srv, pln
@@ -407,9 +418,14 @@ def bench_served(dev, requests: int = 96, slots: int = 4, load: float = 0.8):
             "requests": requests, "slots": slots, "offered_load_vs_plain_capacity": load,
             "plain_capacity_rps": capacity, "offered_rps": rate, "served": served,
             "plain": plain,
+            "plain_note": "one ddm_match per request on the session's resident coordinates, "
+                          "buffer sized by the previous K (retry when it does not fit)",
             "saturated": {"plain_pairs_per_s": plain_sat_pairs, "served_pairs_per_s": served_sat_pairs,
+                          "served_1slot_pairs_per_s": served1_sat_pairs,
                           "plain_rps": capacity, "served_rps": requests / sat_wall,
-                          "throughput_speedup": served_sat_pairs / plain_sat_pairs},
+                          "served_1slot_rps": requests / sat1_wall,
+                          "throughput_speedup": served_sat_pairs / plain_sat_pairs,
+                          "overlap_speedup_vs_1slot": served_sat_pairs / served1_sat_pairs},
             "p99_speedup": plain["p99_ms"] / served["p99_ms"] if served["p99_ms"] else None,
             "load_sweep": sweep,
             "throughput_speedup": served["pairs_per_s"] / plain["pairs_per_s"]

@@ -216,11 +216,18 @@ int ddm_count_noalloc(const ddm_regions *regions, void *cuda_stream, uint64_t *K
  *                         correct).  Results are identical; the order used is
  *                         reported in ddm_stats.dim_order.  Sessions and batched
  *                         calls always use the given order.
+ *   DDM_PARAM_SORT_ITEMS  keys per thread of the 32-bit endpoint sort: 12, 16 or 18
+ *                         (default 18), i.e. tiles of 3072, 4096 or 4608 keys.
+ *   DDM_PARAM_JOIN_SHIFT  log2 of the window length, in sorted-stream positions, of
+ *                         the tiled join for d > 1: 9 .. 11 (default 11).
+ * Results never depend on any tunable; only speed does.
  */
 #define DDM_PARAM_WIN_SHIFT 1
 #define DDM_PARAM_ND_PATH 2
 #define DDM_PARAM_PDL 3
 #define DDM_PARAM_SWEEP_DIM 4
+#define DDM_PARAM_SORT_ITEMS 5
+#define DDM_PARAM_JOIN_SHIFT 6
 int ddm_set_param(ddm_ctx *ctx, int param, int64_t value);
 
 /*

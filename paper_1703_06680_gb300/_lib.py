@@ -29,6 +29,8 @@ PARAM_WIN_SHIFT = 1
 PARAM_ND_PATH = 2
 PARAM_PDL = 3
 PARAM_SWEEP_DIM = 4
+PARAM_SORT_ITEMS = 5
+PARAM_JOIN_SHIFT = 6
 
 
 class DDMError(RuntimeError):
@@ -503,6 +505,17 @@ class Session:
         self._check(rc, max(na.value, nr.value))
         self._K_ref = self._K_last
         return added[:na.value], removed[:nr.value]
+
+    def packed(self):
+        """The resident coordinates as a packed descriptor for Context.match_packed
+        (device pointers into the session's memory, no copy; valid while the
+        session lives)."""
+        r = self._lib.ddm_session_regions(self._h).contents
+        ptrs = [[arr[k] for k in range(self.d)] for arr in (r.sub_lo, r.sub_hi, r.upd_lo,
+                                                             r.upd_hi)]
+        p = _Packed(self.d, self.n, self.m, ptrs)
+        p.owner = self
+        return p
 
     def coords(self):
         """Copies of the resident coordinates as (d, count) float32 CUDA tensors."""

@@ -49,6 +49,8 @@ struct ddm_ctx {
     int nd_path = 0;                              // DDM_PARAM_ND_PATH
     bool pdl = true;                              // DDM_PARAM_PDL
     bool keep_keys = false;  // sessions: the sort's last pass also writes the sorted keys
+    int sort_items = 18;                          // DDM_PARAM_SORT_ITEMS
+    int join_shift = 11;                          // DDM_PARAM_JOIN_SHIFT
     int sweep_dim = 0;                            // DDM_PARAM_SWEEP_DIM
     cudaEvent_t ev[DDM_STAGES + 1] = {};
 };
@@ -219,12 +221,16 @@ struct Plan {
     unsigned long long* inst_off;
     size_t total;
 
+    int sort_items;
+
     void layout(char* base, int d_, int64_t n_, int64_t m_, Mode mode, int num_inst_,
-                int win_shift_ = 10, int nd_path = 0) {
+                int win_shift_ = 10, int nd_path = 0, int sort_items_ = 18, int join_shift = 11) {
+        sort_items = sort_items_;
         d = d_; n = n_; m = m_; E = 2 * (n + m); num_inst = num_inst_;
         const bool batch = num_inst > 0;
         passes = batch ? (int)ceil_div(32 + ceil_log2(num_inst), RADIX_BITS) : 4;
-        const uint64_t stiles = batch ? sort_tiles<unsigned long long>(E) : sort_tiles<uint32_t>(E);
+        const uint64_t stiles = batch ? sort_tiles<unsigned long long>(E)
+                                      : sort_tiles<uint32_t>(E, sort_items);
         Carve cv;
         cv.base = base;
         sort.status = cv.take<unsigned long long>((size_t)passes * sort_status_stride(E));
@@ -240,7 +246,7 @@ struct Plan {
         window = mode == Mode::Match && d == 1;
         join = d > 1 && mode != Mode::Debug && nd_path != 2;
         const bool lists = window || join;
-        win_shift = join ? 11 : win_shift_;
+        win_shift = join ? join_shift : win_shift_;
         // Window path: list w lives in a fixed slot of 2^win_shift entries at
         // w << win_shift (no offsets scan); longer lists overflow to the range
         // path.  Tiled join: lists of any length, placed by an offsets scan.
@@ -317,12 +323,14 @@ enum class Phase { All, Prefix, Suffix };
 int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
             const DebugOut* dbg, Phase phase = Phase::All) {
     Plan pl;
-    pl.layout(nullptr, job.d, job.n, job.m, mode, job.num_inst, c->win_shift, c->nd_path);
+    pl.layout(nullptr, job.d, job.n, job.m, mode, job.num_inst, c->win_shift, c->nd_path,
+              c->sort_items, c->join_shift);
     if (phase == Phase::Suffix && pl.total > c->ws_size)
         return fail(c, DDM_ERR_INTERNAL, "emission phase without its prefix");
     int rc = ensure(c, &c->ws, &c->ws_size, pl.total);
     if (rc) return rc;
-    pl.layout(c->ws, job.d, job.n, job.m, mode, job.num_inst, c->win_shift, c->nd_path);
+    pl.layout(c->ws, job.d, job.n, job.m, mode, job.num_inst, c->win_shift, c->nd_path,
+              c->sort_items, c->join_shift);
     // Pairs are stored as 8-byte (i, j) units.
     if (pairs && (reinterpret_cast<uintptr_t>(pairs) & 7u))
         return fail(c, DDM_ERR_INVALID, "pairs must be 8-byte aligned");
@@ -456,8 +464,7 @@ int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
     } else {
         L += launch_radix_sort<uint32_t>((uint32_t*)pl.keys0, pl.vals0, (uint32_t*)pl.keys1,
                                          pl.vals1, pl.E, pl.passes, pl.sort, !c->keep_keys,
-                                         c->dstat, s,
-                                         rec.s_lo, rec_words);
+                                         c->dstat, s, rec.s_lo, rec_words, pl.sort_items);
     }
     mark(c, 2);
     L += launch_sweep_scan(vals_sorted, pl.E, pl.n, pl.m, rec, pl.scan_status, c->dstat, s);
@@ -626,6 +633,17 @@ int ddm_set_param(ddm_ctx* c, int param, int64_t value) {
     if (param == DDM_PARAM_SWEEP_DIM) {
         if (value < 0 || value > 1) return fail(c, DDM_ERR_INVALID, "sweep dim must be 0 or 1");
         c->sweep_dim = (int)value;
+        return DDM_OK;
+    }
+    if (param == DDM_PARAM_SORT_ITEMS) {
+        if (value != 12 && value != 16 && value != 18)
+            return fail(c, DDM_ERR_INVALID, "sort items must be 12, 16 or 18");
+        c->sort_items = (int)value;
+        return DDM_OK;
+    }
+    if (param == DDM_PARAM_JOIN_SHIFT) {
+        if (value < 9 || value > 11) return fail(c, DDM_ERR_INVALID, "join shift must be 9..11");
+        c->join_shift = (int)value;
         return DDM_OK;
     }
     if (param == DDM_PARAM_PDL) {
@@ -1087,7 +1105,8 @@ int ddm_session_emit_delta(ddm_session* s, void* stream, int32_t* added, uint64_
     }
     // Later reports: candidates from the coordinates that moved.
     Plan pl;  // the layout of the count phase that produced the sorted stream
-    pl.layout(c->ws, d, n, m, Mode::Match, 0, c->win_shift, c->nd_path);
+    pl.layout(c->ws, d, n, m, Mode::Match, 0, c->win_shift, c->nd_path, c->sort_items,
+              c->join_shift);
     DeltaArgs a{};
     a.d = d; a.n = (uint32_t)n; a.m = (uint32_t)m;
     a.E = (uint32_t)pl.E;

@@ -39,7 +39,7 @@ namespace ddm {
 constexpr int JOIN_BLOCK = 512;
 constexpr int JOIN_WARPS = JOIN_BLOCK / 32;
 constexpr uint32_t JOIN_CHUNK = 512;
-constexpr int JOIN_SHIFT = 11;  // windows of 2048 stream positions
+constexpr int JOIN_SHIFT = 11;  // windows of at most 2048 stream positions (DDM_PARAM_JOIN_SHIFT)
 constexpr uint32_t JOIN_MAXSUB = 1u << JOIN_SHIFT;
 constexpr uint32_t JOIN_LONG_RANGE = 16;  // candidate ranges walked by the whole warp
 
@@ -355,7 +355,7 @@ static void launch_join_w(const EmitArgs& a, size_t smem, DevStatus* st, cudaStr
 
 int launch_join(const EmitArgs& a, bool write, DevStatus* st, cudaStream_t s) {
     if (a.num_win == 0 || a.n == 0) return 0;
-    if (a.win_shift != JOIN_SHIFT) return -1;
+    if (a.win_shift > JOIN_SHIFT) return -1;  // shared memory holds at most 2^JOIN_SHIFT subs
     const size_t smem = join_smem_bytes(a.d);
     if (write) launch_join_w<true>(a, smem, st, s);
     else launch_join_w<false>(a, smem, st, s);

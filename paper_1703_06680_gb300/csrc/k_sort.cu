@@ -331,13 +331,12 @@ k_downsweep(const KeyT* __restrict__ keys_in, const uint32_t* __restrict__ vals_
     }
 }
 
-template <typename KeyT>
-int launch_radix_sort(KeyT* keys0, uint32_t* vals0, KeyT* keys1, uint32_t* vals1, uint64_t E,
-                      int passes, const SortScratch& sc, bool skip_last_keys, DevStatus* st,
-                      cudaStream_t s, void* clear_ptr, uint64_t clear_words) {
-    if (E == 0) return 0;
-    constexpr int ITEMS = sort_items<KeyT>();
-    const uint64_t tiles = sort_tiles<KeyT>(E);
+template <typename KeyT, int ITEMS>
+static int radix_sort_items(KeyT* keys0, uint32_t* vals0, KeyT* keys1, uint32_t* vals1,
+                            uint64_t E, int passes, const SortScratch& sc, bool skip_last_keys,
+                            DevStatus* st, cudaStream_t s, void* clear_ptr,
+                            uint64_t clear_words) {
+    const uint64_t tiles = ceil_div(E, (uint64_t)SORT_BLOCK * ITEMS);
     KeyT* kb[2] = {keys0, keys1};
     uint32_t* vb[2] = {vals0, vals1};
     const uint64_t cells = tiles * RADIX;
@@ -373,12 +372,32 @@ int launch_radix_sort(KeyT* keys0, uint32_t* vals0, KeyT* keys1, uint32_t* vals1
     return launches;
 }
 
+template <typename KeyT>
+int launch_radix_sort(KeyT* keys0, uint32_t* vals0, KeyT* keys1, uint32_t* vals1, uint64_t E,
+                      int passes, const SortScratch& sc, bool skip_last_keys, DevStatus* st,
+                      cudaStream_t s, void* clear_ptr, uint64_t clear_words, int items) {
+    if (E == 0) return 0;
+    if (sizeof(KeyT) == 8 || items == 0) items = sort_items<KeyT>();
+    switch (items) {  // the tile sizes a context may choose (DDM_PARAM_SORT_ITEMS)
+        case 12:
+            return radix_sort_items<KeyT, 12>(keys0, vals0, keys1, vals1, E, passes, sc,
+                                              skip_last_keys, st, s, clear_ptr, clear_words);
+        case 16:
+            return radix_sort_items<KeyT, 16>(keys0, vals0, keys1, vals1, E, passes, sc,
+                                              skip_last_keys, st, s, clear_ptr, clear_words);
+        default:
+            return radix_sort_items<KeyT, SORT_ITEMS_32>(keys0, vals0, keys1, vals1, E, passes,
+                                                         sc, skip_last_keys, st, s, clear_ptr,
+                                                         clear_words);
+    }
+}
+
 template int launch_radix_sort<uint32_t>(uint32_t*, uint32_t*, uint32_t*, uint32_t*, uint64_t,
                                          int, const SortScratch&, bool, DevStatus*, cudaStream_t,
-                                         void*, uint64_t);
+                                         void*, uint64_t, int);
 template int launch_radix_sort<unsigned long long>(unsigned long long*, uint32_t*,
                                                    unsigned long long*, uint32_t*, uint64_t, int,
                                                    const SortScratch&, bool, DevStatus*,
-                                                   cudaStream_t, void*, uint64_t);
+                                                   cudaStream_t, void*, uint64_t, int);
 
 }  // namespace ddm

@@ -18,9 +18,12 @@ constexpr int SORT_ITEMS_64 = 12;      // keys per thread, 64-bit keys
 template <typename KeyT>
 constexpr int sort_items() { return sizeof(KeyT) == 4 ? SORT_ITEMS_32 : SORT_ITEMS_64; }
 
+// Tiles of a sort of E keys; items = keys per thread (0: the default of KeyT;
+// 32-bit keys may also use 12 or 16, see launch_radix_sort).
 template <typename KeyT>
-inline uint64_t sort_tiles(uint64_t E) {
-    return ceil_div(E, (uint64_t)SORT_BLOCK * sort_items<KeyT>());
+inline uint64_t sort_tiles(uint64_t E, int items = 0) {
+    if (sizeof(KeyT) == 8 || items == 0) items = sort_items<KeyT>();
+    return ceil_div(E, (uint64_t)SORT_BLOCK * items);
 }
 
 // Fused offsets: with at most SORT_FUSED_MAX_TILES tiles, the downsweep
@@ -74,9 +77,13 @@ int launch_keybuild_d0(const float* sub_lo, const float* sub_hi, const float* up
 // clear_ptr/clear_words (16-byte words, may be NULL/0): a buffer that the last
 // pass's blocks zero while their tiles load (the rank-record tables of the
 // sweep scan that follows).
+// items: keys per thread of a 32-bit sort, 12, 16 or 18 (0: the default, 18);
+// 64-bit keys always use 12.  The scratch must be sized for the same choice
+// (sort_tiles<KeyT>(E, items)).
 template <typename KeyT>
 int launch_radix_sort(KeyT* keys0, uint32_t* vals0, KeyT* keys1, uint32_t* vals1, uint64_t E,
                       int passes, const SortScratch& sc, bool skip_last_keys, DevStatus* st,
-                      cudaStream_t s, void* clear_ptr = nullptr, uint64_t clear_words = 0);
+                      cudaStream_t s, void* clear_ptr = nullptr, uint64_t clear_words = 0,
+                      int items = 0);
 
 }  // namespace ddm

@@ -5,7 +5,8 @@ import json
 import numpy as np
 
 from paper_1703_06680_gb300 import autotune
-from paper_1703_06680_gb300._lib import PARAM_ND_PATH, PARAM_WIN_SHIFT
+from paper_1703_06680_gb300._lib import (PARAM_JOIN_SHIFT, PARAM_ND_PATH, PARAM_SORT_ITEMS,
+                                         PARAM_WIN_SHIFT)
 
 
 class FakeCtx:
@@ -39,20 +40,24 @@ def test_tune_picks_fastest_and_caches(tmp_path):
     cache = tmp_path / "tune.json"
     ctx = FakeCtx(K=1000)
     fake_ms = {8: 3.0, 9: 1.0, 10: 2.0}
+    items_ms = {12: 0.5, 16: 0.2, 18: 0.4}
 
-    def timer(c, t, K, reps):
-        return fake_ms[c.params[PARAM_WIN_SHIFT]]
+    def timer(c, t, K, reps):   # defaults for tunables not set yet (18 items, window 10)
+        return fake_ms[c.params.get(PARAM_WIN_SHIFT, 10)] + items_ms[c.params.get(PARAM_SORT_ITEMS, 18)]
 
     chosen = autotune.tune(ctx, tensors(1, 100, 100), cache_path=str(cache), gpu="G", timer=timer)
     assert chosen["win_shift"] == 9 and ctx.params[PARAM_WIN_SHIFT] == 9
+    assert chosen["sort_items"] == 16 and ctx.params[PARAM_SORT_ITEMS] == 16
     assert PARAM_ND_PATH not in ctx.params            # d = 1: no d > 1 strategy
+    assert PARAM_JOIN_SHIFT not in ctx.params
     stored = json.loads(cache.read_text())
     assert stored[chosen["key"]]["win_shift"] == 9
-    assert stored[chosen["key"]]["win_shift_ms"] == {"8": 3.0, "9": 1.0, "10": 2.0}
+    assert stored[chosen["key"]]["win_shift_ms"] == {"8": 3.2, "9": 1.2, "10": 2.2}
+    assert stored[chosen["key"]]["sort_items"] == 16
 
     fresh = FakeCtx(K=1000)
     assert autotune.apply_cached(fresh, tensors(1, 100, 100), cache_path=str(cache), gpu="G")
-    assert fresh.params == {PARAM_WIN_SHIFT: 9}
+    assert fresh.params == {PARAM_WIN_SHIFT: 9, PARAM_SORT_ITEMS: 16}
     # another workload class or GPU: nothing cached
     assert not autotune.apply_cached(FakeCtx(K=10**6), tensors(1, 100, 100),
                                      cache_path=str(cache), gpu="G")
@@ -66,10 +71,12 @@ def test_tune_d2_uses_strategy_only_and_merges_cache(tmp_path):
     ctx = FakeCtx(K=500)
 
     def timer(c, t, K, reps):
-        return {1: 5.0, 2: 4.0}[c.params[PARAM_ND_PATH]]
+        return ({1: 5.0, 2: 4.0}[c.params[PARAM_ND_PATH]]
+                + {9: 1.0, 10: 0.5, 11: 2.0}[c.params.get(PARAM_JOIN_SHIFT, 11)])
 
     chosen = autotune.tune(ctx, tensors(2, 50, 60), cache_path=str(cache), gpu="G", timer=timer)
     assert chosen["nd_path"] == 2 and "win_shift" not in chosen
+    assert chosen["join_shift"] == 10 and ctx.params[PARAM_JOIN_SHIFT] == 10
     assert chosen["sweep_dim"] == 0                   # equal times: the first candidate
     stored = json.loads(cache.read_text())
     assert stored["other"] == {"win_shift": 7}       # earlier entries kept

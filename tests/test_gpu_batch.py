@@ -103,6 +103,12 @@ def test_autotune_on_gpu_keeps_results(tmp_path, d):
         name = "win_shift" if d == 1 else "nd_path"
         assert chosen[name] in autotune.CANDIDATES[
             autotune.PARAM_WIN_SHIFT if d == 1 else autotune.PARAM_ND_PATH]
+        # the tile parameters are tuned too, and cached with the rest
+        assert chosen["sort_items"] in autotune.CANDIDATES[autotune.PARAM_SORT_ITEMS]
+        if d > 1:
+            assert chosen["join_shift"] in autotune.CANDIDATES[autotune.PARAM_JOIN_SHIFT]
+        entry = autotune._load(cache)[chosen["key"]]
+        assert entry["sort_items"] == chosen["sort_items"]
         assert np.array_equal(ctx.match(*t).cpu().numpy(), want)
     with ddm.Context(0) as ctx2:
         assert autotune.apply_cached(ctx2, t, cache_path=cache)

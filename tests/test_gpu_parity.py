@@ -384,3 +384,27 @@ def test_bounded_wait_times_out_and_context_survives(which):
         with pytest.raises(ddm.DDMError) as e:
             c.debug_wait_timeout(2, 16)
         assert e.value.code == ddm._lib.DDM_ERR_INVALID
+
+
+def test_tile_parameters_change_only_speed():
+    # Every sort tile size (keys per thread) and every join window gives the
+    # oracle's pairs, including the flat-scan sort above 1024 tiles.
+    import paper_1703_06680_gb300 as ddm
+    reg1 = synth.large_1d(100.0, N=200_001)
+    want1 = oracle.sbm(reg1)
+    big = synth.large_1d(1.0, N=2_500_000)      # > 1024 tiles at every tile size
+    want_big = oracle.sbm(big)
+    reg2 = synth.large_nd(3, 100.0, N=40_001)
+    want2 = oracle.sbm(reg2)
+    with ddm.Context(0) as c:
+        for items in (12, 16, 18):
+            c.set_param(ddm._lib.PARAM_SORT_ITEMS, items)
+            assert np.array_equal(gpu_pairs(c, reg1), want1), items
+            assert np.array_equal(gpu_pairs(c, big), want_big), items
+            assert np.array_equal(gpu_pairs(c, reg2), want2), items
+        for shift in (9, 10, 11):
+            c.set_param(ddm._lib.PARAM_JOIN_SHIFT, shift)
+            assert np.array_equal(gpu_pairs(c, reg2), want2), shift
+        for bad in ((ddm._lib.PARAM_SORT_ITEMS, 20), (ddm._lib.PARAM_JOIN_SHIFT, 12)):
+            with pytest.raises(ddm.DDMError):
+                c.set_param(*bad)
