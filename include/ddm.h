@@ -220,6 +220,14 @@ int ddm_count_noalloc(const ddm_regions *regions, void *cuda_stream, uint64_t *K
  *                         (default 18), i.e. tiles of 3072, 4096 or 4608 keys.
  *   DDM_PARAM_JOIN_SHIFT  log2 of the window length, in sorted-stream positions, of
  *                         the tiled join for d > 1: 9 .. 11 (default 11).
+ *   DDM_PARAM_ND_WRITE    how ddm_match writes the pairs for d > 1 with the tiled join:
+ *                         1 = a second filter pass into each subscription's segment,
+ *                         then a per-segment sort; 2 = the count pass also records
+ *                         every surviving pair as a 64-bit key and one radix sort of
+ *                         those keys gives the list (no second filter pass; needs 16
+ *                         bytes per pair and per slot of room, room sized by the last
+ *                         call's K; falls back to 1 when a window's share overflows);
+ *                         0 (default) = 2 for d >= 3, 1 for d = 2 (measured).
  * Results never depend on any tunable; only speed does.
  */
 #define DDM_PARAM_WIN_SHIFT 1
@@ -228,6 +236,7 @@ int ddm_count_noalloc(const ddm_regions *regions, void *cuda_stream, uint64_t *K
 #define DDM_PARAM_SWEEP_DIM 4
 #define DDM_PARAM_SORT_ITEMS 5
 #define DDM_PARAM_JOIN_SHIFT 6
+#define DDM_PARAM_ND_WRITE 7
 int ddm_set_param(ddm_ctx *ctx, int param, int64_t value);
 
 /*
@@ -256,6 +265,11 @@ typedef struct {
      * dimension, dim_order[1] the pruning one (identity unless
      * DDM_PARAM_SWEEP_DIM = 1 reordered a d > 1 call). */
     uint32_t dim_order[DDM_MAX_DIMS];
+    /* d > 1 ddm_match calls whose pairs came from the survivors recorded by the
+     * count pass (one sort, no second filter pass); the others ran the general
+     * write pass (the first call of a context has no size hint; windows that
+     * overflowed; no memory for the keys). */
+    uint64_t survivor_calls;
 } ddm_stats;
 
 int ddm_set_profiling(ddm_ctx *ctx, int enable);

@@ -31,6 +31,7 @@ PARAM_PDL = 3
 PARAM_SWEEP_DIM = 4
 PARAM_SORT_ITEMS = 5
 PARAM_JOIN_SHIFT = 6
+PARAM_ND_WRITE = 7
 
 
 class DDMError(RuntimeError):
@@ -47,7 +48,8 @@ class CapacityError(DDMError):
 
 class Stats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_uint64), ("calls", ctypes.c_uint64),
-                ("stage_ms", ctypes.c_float * 8), ("dim_order", ctypes.c_uint32 * 8)]
+                ("stage_ms", ctypes.c_float * 8), ("dim_order", ctypes.c_uint32 * 8),
+                ("survivor_calls", ctypes.c_uint64)]
 
 
 STAGE_NAMES = ["keybuild", "radix_sort", "sweep_scan", "counts", "offsets", "emit_setup", "emit",
@@ -243,7 +245,8 @@ class Context:
         self._check(self._lib.ddm_get_stats(self._h, ctypes.byref(s)))
         return {"launches": int(s.launches), "calls": int(s.calls),
                 "stage_ms": dict(zip(STAGE_NAMES, [float(x) for x in s.stage_ms])),
-                "dim_order": [int(x) for x in s.dim_order]}
+                "dim_order": [int(x) for x in s.dim_order],
+                "survivor_calls": int(s.survivor_calls)}
 
     # -- entry points ----------------------------------------------------------
     def count(self, sub_lo, sub_hi, upd_lo, upd_hi) -> int:

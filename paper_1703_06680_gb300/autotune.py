@@ -13,21 +13,23 @@ import math
 import os
 import statistics
 
-from ._lib import (PARAM_JOIN_SHIFT, PARAM_ND_PATH, PARAM_SORT_ITEMS, PARAM_SWEEP_DIM,
-                   PARAM_WIN_SHIFT)
+from ._lib import (PARAM_JOIN_SHIFT, PARAM_ND_PATH, PARAM_ND_WRITE, PARAM_SORT_ITEMS,
+                   PARAM_SWEEP_DIM, PARAM_WIN_SHIFT)
 
 # Candidate values per tunable, in the order they are tuned (one at a time, each
 # with the best values found so far for the earlier ones), and which
 # dimensionalities a tunable affects.  Algorithm choices first, then tile sizes:
 # the sort's keys per thread (tiles of 3072 / 4096 / 4608 keys), the window of
 # the d = 1 emission and the window of the d > 1 join.
-CANDIDATES = {PARAM_ND_PATH: (1, 2), PARAM_SWEEP_DIM: (0, 1), PARAM_SORT_ITEMS: (12, 16, 18),
-              PARAM_WIN_SHIFT: (8, 9, 10), PARAM_JOIN_SHIFT: (9, 10, 11)}
+CANDIDATES = {PARAM_ND_PATH: (1, 2), PARAM_SWEEP_DIM: (0, 1), PARAM_ND_WRITE: (1, 2),
+              PARAM_SORT_ITEMS: (12, 16, 18), PARAM_WIN_SHIFT: (8, 9, 10),
+              PARAM_JOIN_SHIFT: (9, 10, 11)}
 NAMES = {PARAM_WIN_SHIFT: "win_shift", PARAM_ND_PATH: "nd_path", PARAM_SWEEP_DIM: "sweep_dim",
-         PARAM_SORT_ITEMS: "sort_items", PARAM_JOIN_SHIFT: "join_shift"}
+         PARAM_SORT_ITEMS: "sort_items", PARAM_JOIN_SHIFT: "join_shift",
+         PARAM_ND_WRITE: "nd_write"}
 APPLIES = {PARAM_WIN_SHIFT: lambda d: d == 1, PARAM_ND_PATH: lambda d: d > 1,
            PARAM_SWEEP_DIM: lambda d: d > 1, PARAM_SORT_ITEMS: lambda d: True,
-           PARAM_JOIN_SHIFT: lambda d: d > 1}
+           PARAM_JOIN_SHIFT: lambda d: d > 1, PARAM_ND_WRITE: lambda d: d > 1}
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
 

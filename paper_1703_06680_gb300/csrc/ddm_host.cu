@@ -50,7 +50,17 @@ struct ddm_ctx {
     bool pdl = true;                              // DDM_PARAM_PDL
     bool keep_keys = false;  // sessions: the sort's last pass also writes the sorted keys
     int sort_items = 18;                          // DDM_PARAM_SORT_ITEMS
+    // d > 1 matching: the join's count pass records its survivors here, so
+    // that the pairs come from one sort of those keys instead of a second
+    // filter pass and a per-segment sort (when all of them fit).
+    char* sv = nullptr;
+    size_t sv_size = 0;
+    uint64_t surv_hint = 0;                       // K of the last d > 1 match
+    uint64_t surv_fail_K = ~0ull;                 // K whose survivors did not fit
+    unsigned long long* surv_keys = nullptr;      // non-NULL: record in this call
+    uint64_t surv_cap = 0;
     int join_shift = 11;                          // DDM_PARAM_JOIN_SHIFT
+    int nd_write = 0;                             // DDM_PARAM_ND_WRITE
     int sweep_dim = 0;                            // DDM_PARAM_SWEEP_DIM
     cudaEvent_t ev[DDM_STAGES + 1] = {};
 };
@@ -132,6 +142,23 @@ int ensure(ddm_ctx* c, char** buf, size_t* size, size_t need) {
     return DDM_OK;
 }
 
+// Sort scratch of one radix sort of up to E KeyT keys in `passes` passes,
+// carved with its zeroed part (status words, total, group sums) first;
+// [zb, ze) is that part's byte range, to be cleared before every sort.
+template <typename KeyT>
+void carve_sort(Carve& cv, uint64_t E, int passes, SortScratch& sc, size_t& zb,
+                       size_t& ze) {
+    const uint64_t tiles = sort_tiles<KeyT>(E);
+    zb = (cv.off + 255) & ~(size_t)255;
+    sc.status = cv.take<unsigned long long>((size_t)passes * sort_status_stride(E));
+    sc.total = cv.take<unsigned long long>(1);
+    const size_t gw = sort_group_words(tiles, passes);
+    sc.grp = gw ? cv.take<uint32_t>(gw) : nullptr;
+    ze = cv.off;
+    sc.tile_hist = cv.take<uint32_t>(tiles * RADIX);
+    sc.offs = cv.take<unsigned long long>(tiles * RADIX + 1);
+}
+
 int check_regions(ddm_ctx* c, const ddm_regions* r) {
     if (!r) return fail(c, DDM_ERR_INVALID, "regions is NULL");
     if (r->d < 1 || r->d > DDM_MAX_DIMS) return fail(c, DDM_ERR_INVALID, "d out of range");
@@ -193,6 +220,7 @@ struct Plan {
     uint32_t* lw_fill;
     uint32_t* num_flagged;
     unsigned long long* cand_fill;
+    unsigned long long* surv_fill;
     uint4* wmeta;
     uint2* wcand;
     unsigned long long cand_cap;
@@ -255,6 +283,7 @@ struct Plan {
         lw_fill = cv.take<uint32_t>(num_win);
         num_flagged = cv.take<uint32_t>(1);
         cand_fill = cv.take<unsigned long long>(1);
+        surv_fill = cv.take<unsigned long long>(join ? num_win : 0);
         lw_total = cv.take<unsigned long long>(1);
         win_status = cv.take<unsigned long long>(lists ? ceil_div(num_win, OFF_TILE) + 2 : 0);
         zero_bytes = (cv.off + 255) & ~(size_t)255;
@@ -437,6 +466,12 @@ int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
         a.lw_cap = pl.lw_cap;
     }
     a.vals = vals_sorted;
+    a.surv = nullptr;
+    if (pl.join && mode == Mode::Match && !batch && c->surv_keys) {
+        a.surv = c->surv_keys;
+        a.surv_cap = c->surv_cap;
+        a.surv_fill = pl.surv_fill;
+    }
   if (do_prefix) {
     mark(c, 0);
     if (batch) {
@@ -481,7 +516,9 @@ int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
             L += launch_window_offsets(pl.windows, pl.num_win, pl.lcap, pl.lw_off, pl.lw_total,
                                        pl.win_status, c->dstat, s);
             L += launch_tile_active(a, c->dstat, s);
-            L += launch_join(a, false, c->dstat, s);
+            const int lj = launch_join(a, false, c->dstat, s);
+            if (lj < 0) return fail(c, DDM_ERR_INTERNAL, "join launch configuration");
+            L += lj;
         }
         L += launch_filter_count(a, c->dstat, s);  // with the join: flagged subscriptions only
     }
@@ -504,7 +541,11 @@ int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
     }
     mark(c, 6);
     if (pl.window) L += launch_emit_window(a, c->dstat, s);
-    else if (pl.join && mode == Mode::Match) L += launch_join(a, true, c->dstat, s);
+    else if (pl.join && mode == Mode::Match) {
+        const int lj = launch_join(a, true, c->dstat, s);
+        if (lj < 0) return fail(c, DDM_ERR_INTERNAL, "join launch configuration");
+        L += lj;
+    }
     else if (mode == Mode::Match) L += launch_emit_ranges(a, c->dstat, s);
     mark(c, 7);
     if ((pl.window || pl.join) && mode == Mode::Match)
@@ -598,6 +639,7 @@ int ddm_destroy(ddm_ctx* c) {
     if (c->ws) cudaFree(c->ws);
     if (c->io) cudaFree(c->io);
     if (c->out) cudaFree(c->out);
+    if (c->sv) cudaFree(c->sv);
     if (c->dstat) cudaFree(c->dstat);
     if (c->hstat) cudaFreeHost(c->hstat);
     delete c;
@@ -644,6 +686,11 @@ int ddm_set_param(ddm_ctx* c, int param, int64_t value) {
     if (param == DDM_PARAM_JOIN_SHIFT) {
         if (value < 9 || value > 11) return fail(c, DDM_ERR_INVALID, "join shift must be 9..11");
         c->join_shift = (int)value;
+        return DDM_OK;
+    }
+    if (param == DDM_PARAM_ND_WRITE) {
+        if (value < 0 || value > 2) return fail(c, DDM_ERR_INVALID, "nd write must be 0..2");
+        c->nd_write = (int)value;
         return DDM_OK;
     }
     if (param == DDM_PARAM_PDL) {
@@ -719,6 +766,121 @@ int ddm_count(ddm_ctx* c, const ddm_regions* r, uint64_t* K_out) {
     return finish(c, K_out);
 }
 
+}  // extern "C"
+
+namespace {
+
+constexpr int MATCH_RETRY = 1;  // not an error code: take the general path
+
+// d > 1 with the tiled join: the count pass records every survivor as the key
+// (i << id_bits(m)) | j, and the sorted pair list is one radix sort of those
+// keys, unpacked into `pairs` -- no second filter pass and no per-segment
+// sort.  The keys' room follows the previous d > 1 call's K.  Returns
+// MATCH_RETRY (nothing written, the error text cleared) when the room cannot be
+// had, when not every survivor fitted, or when subscriptions of overflowing
+// windows went to the range path; the caller then runs the general pipeline.
+int match_from_survivors(ddm_ctx* c, const ddm_regions* r, int32_t* pairs, uint64_t cap,
+                         uint64_t* K_out) {
+    const int64_t n = r->n, m = r->m;
+    // Room for the keys: one slice per join window, sized by the window's
+    // subscriptions.
+    Plan pl0;
+    pl0.layout(nullptr, r->d, n, m, Mode::Match, 0, c->win_shift, c->nd_path, c->sort_items,
+               c->join_shift);
+    const uint32_t slices = pl0.num_win;
+    const uint64_t hint = c->surv_hint;  // 0: this attempt is not sized from a known K
+    if (slices == 0 || (hint && hint == c->surv_fail_K)) return MATCH_RETRY;
+    // Per subscription of a window: twice the last K's share, plus 8.
+    const uint64_t per_sub = ceil_div(2 * hint, (uint64_t)n) + 8;
+    const uint64_t room = per_sub * (uint64_t)n;
+    const int passes = (int)ceil_div((uint64_t)(id_bits(n) + id_bits(m)), RADIX_BITS);
+    SortScratch sc{};
+    size_t zb = 0, ze = 0;
+    unsigned long long* kb[2] = {};
+    unsigned long long* dpos = nullptr;
+    auto carve = [&](Carve& cv) {
+        kb[0] = cv.take<unsigned long long>(room);  // the windows' slices, then sort buffer
+        kb[1] = cv.take<unsigned long long>(room);  // the compacted keys
+        dpos = cv.take<unsigned long long>(slices + 1);
+        carve_sort<unsigned long long>(cv, room, passes, sc, zb, ze);
+    };
+    Carve sz;
+    carve(sz);
+    if (ensure(c, &c->sv, &c->sv_size, sz.off + 256) != DDM_OK) {
+        c->err.clear();
+        return MATCH_RETRY;  // no room for the keys: the general path needs none
+    }
+    Carve cv;
+    cv.base = c->sv;
+    carve(cv);
+    Job job;
+    job.d = r->d; job.n = n; job.m = m; job.r = r;
+    c->surv_keys = kb[0];
+    c->surv_cap = per_sub;
+    int rc = enqueue(c, job, Mode::Match, nullptr, 0, nullptr, Phase::Prefix);
+    c->surv_keys = nullptr;
+    if (rc) return rc;
+    uint64_t K = 0;
+    rc = finish(c, &K);
+    if (rc) return rc;
+    c->surv_hint = K;
+    Plan pl;
+    pl.layout(c->ws, job.d, n, m, Mode::Match, 0, c->win_shift, c->nd_path, c->sort_items,
+              c->join_shift);
+    std::vector<unsigned long long> fill(slices);
+    uint32_t flagged = 0;
+    CK(cudaMemcpy(fill.data(), pl.surv_fill, slices * sizeof(unsigned long long),
+                  cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&flagged, pl.num_flagged, sizeof flagged, cudaMemcpyDeviceToHost));
+    if (K_out) *K_out = K;
+    if (K > cap)
+        return fail(c, DDM_ERR_CAPACITY, "output capacity too small for " + std::to_string(K) +
+                                             " pairs");
+    // Window w holds ns_w subscriptions: its slice has ns_w * per_sub entries.
+    // Its fill counts reserved slots, unused ones (set to ~0) included.
+    std::vector<uint4> win(slices + 1);
+    CK(cudaMemcpy(win.data(), pl.windows, (slices + 1) * sizeof(uint4), cudaMemcpyDeviceToHost));
+    std::vector<unsigned long long> pos(slices + 1, 0);
+    bool fits = flagged == 0;
+    for (uint32_t w = 0; w < slices; ++w) {
+        pos[w + 1] = pos[w] + fill[w];
+        fits = fits && fill[w] <= (uint64_t)(win[w + 1].x - win[w].x) * per_sub;
+    }
+    const uint64_t T = pos[slices];
+    if (!fits || T < K) {
+        // Skewed windows (or overflowing ones): the general path for this
+        // output size from now on, so the count pass is not paid twice again.
+        if (hint == K) c->surv_fail_K = K;
+        return MATCH_RETRY;
+    }
+    // Stages 5 (no set-up here), 6 (the sort and unpack of the survivors) and
+    // 7 (no per-segment sort).
+    mark(c, 5);
+    mark(c, 6);
+    if (K > 0) {
+        cudaStream_t s = c->stream;
+        PdlScope pdl_scope(c->pdl);
+        CK(cudaMemcpyAsync(dpos, pos.data(), (slices + 1) * sizeof(unsigned long long),
+                           cudaMemcpyHostToDevice, s));
+        CK(cudaMemsetAsync(c->sv + zb, 0, ze - zb, s));
+        c->stats.launches += launch_surv_compact(kb[0], pl.surv_fill, pl.windows, slices,
+                                                 per_sub, dpos, kb[1], s);
+        // Keys only; the T - K unused slots (~0) sort last.
+        c->stats.launches += launch_radix_sort<unsigned long long>(
+            kb[1], nullptr, kb[0], nullptr, T, passes, sc, false, c->dstat, s);
+        c->stats.launches += launch_delta_unpack(kb[(passes & 1) ? 0 : 1], K, id_bits(m), pairs,
+                                                 s);
+    }
+    mark(c, 7);
+    mark(c, 8);
+    c->stats.survivor_calls++;
+    return finish(c, K_out);
+}
+
+}  // namespace
+
+extern "C" {
+
 int ddm_match(ddm_ctx* c, const ddm_regions* r, int32_t* pairs, uint64_t cap, uint64_t* K_out) {
     if (!c) return DDM_ERR_INVALID;
     int rc = check_regions(c, r);
@@ -729,6 +891,15 @@ int ddm_match(ddm_ctx* c, const ddm_regions* r, int32_t* pairs, uint64_t cap, ui
     std::vector<const float*> hold;
     rc = order_dims(c, r, &ro, hold);
     if (rc) return rc;
+    // d > 1 pairs from the count pass's survivors (one sort) or from a second
+    // filter pass and per-segment sorts: measured on GB300, the survivors win
+    // at d >= 3 (the filter dominates), the write pass at d = 2 (the sort of
+    // K keys dominates); DDM_PARAM_ND_WRITE overrides.
+    const bool survivors = c->nd_write == 2 || (c->nd_write == 0 && ro.d >= 3);
+    if (survivors && ro.d > 1 && c->nd_path != 2 && ro.n > 0 && ro.m > 0 && pairs) {
+        rc = match_from_survivors(c, &ro, pairs, cap, K_out);
+        if (rc != MATCH_RETRY) return rc;
+    }
     rc = enqueue_plain(c, &ro, Mode::Match, pairs, cap, nullptr);
     if (rc) return rc;
     return finish(c, K_out);
@@ -1036,29 +1207,6 @@ int ddm_session_emit(ddm_session* s, void* stream, int32_t* pairs, uint64_t cap,
     if (rc) return rc;
     return finish(c, K_out);
 }
-
-// Sort scratch of one radix sort of up to E KeyT keys in `passes` passes,
-// carved with its zeroed part (status words, total, group sums) first;
-// [zb, ze) is that part's byte range, to be cleared before every sort.
-}  // extern "C"
-
-namespace {
-template <typename KeyT>
-void carve_sort(Carve& cv, uint64_t E, int passes, SortScratch& sc, size_t& zb,
-                       size_t& ze) {
-    const uint64_t tiles = sort_tiles<KeyT>(E);
-    zb = (cv.off + 255) & ~(size_t)255;
-    sc.status = cv.take<unsigned long long>((size_t)passes * sort_status_stride(E));
-    sc.total = cv.take<unsigned long long>(1);
-    const size_t gw = sort_group_words(tiles, passes);
-    sc.grp = gw ? cv.take<uint32_t>(gw) : nullptr;
-    ze = cv.off;
-    sc.tile_hist = cv.take<uint32_t>(tiles * RADIX);
-    sc.offs = cv.take<unsigned long long>(tiles * RADIX + 1);
-}
-}  // namespace
-
-extern "C" {
 
 int ddm_session_emit_delta(ddm_session* s, void* stream, int32_t* added, uint64_t cap_added,
                            int32_t* removed, uint64_t cap_removed, uint64_t* n_added,

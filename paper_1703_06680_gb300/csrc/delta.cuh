@@ -71,4 +71,9 @@ int launch_delta_finish(const DeltaArgs& a, const unsigned long long* sorted, in
                         uint32_t* flags, float* ref_coords, const float* coords,
                         uint64_t coord_count, cudaStream_t s);
 
+// Sorted pair keys (i << jbits) | j into interleaved int32 pairs
+// (pairs[2q] = key >> jbits, pairs[2q + 1] = key & ((1 << jbits) - 1)).
+int launch_delta_unpack(const unsigned long long* keys, uint64_t count, int jbits, int32_t* pairs,
+                        cudaStream_t s);
+
 }  // namespace ddm

@@ -58,6 +58,13 @@ struct EmitArgs {
     unsigned long long* cand_fill;  // window path: entries of wcand reserved so far (zeroed)
     unsigned long long cand_cap;
     unsigned long long lw_cap;
+    // d > 1, tiled join: the count pass also records every survivor as the key
+    // (i << id_bits) | j into surv; window w, whose subscriptions have the
+    // lower-endpoint ranks r0 .. r0 + ns, uses entries [r0 surv_cap,
+    // (r0 + ns) surv_cap) (fill counter surv_fill[w]); NULL: not recorded.
+    unsigned long long* surv;
+    unsigned long long surv_cap;
+    unsigned long long* surv_fill;
     const uint32_t* vals;           // sorted endpoint stream (payloads)
     bool sort_all;                  // segment sort every subscription, not only flagged ones
 };
@@ -69,6 +76,11 @@ __device__ __forceinline__ unsigned long long list_base(const EmitArgs& a, uint3
 
 // d > 1: tiled join of windows of subscriptions with chunks of candidates.
 int launch_join(const EmitArgs& a, bool write, DevStatus* st, cudaStream_t s);
+// Window w's used survivor entries (fill[w], padded holes included) into
+// dst[pos[w] .. pos[w] + fill[w]).
+int launch_surv_compact(const unsigned long long* surv, const unsigned long long* fill,
+                        const uint4* windows, uint32_t num_win, unsigned long long per_sub,
+                        const unsigned long long* pos, unsigned long long* dst, cudaStream_t s);
 
 // Window path for d = 1.
 int launch_tile_active(const EmitArgs& a, DevStatus* st, cudaStream_t s);

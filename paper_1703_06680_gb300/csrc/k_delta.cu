@@ -400,6 +400,28 @@ int launch_delta_cand(const DeltaArgs& a, DevStatus* st, cudaStream_t s) {
     return 1;
 }
 
+// Sorted pair keys (i << jbits) | j into interleaved int32 pairs.
+__global__ void k_keys_unpack(const unsigned long long* __restrict__ keys, uint64_t count,
+                              int jbits, int2* __restrict__ pairs) {
+    pdl_begin();
+    const unsigned long long mask = (1ull << jbits) - 1ull;
+    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < count;
+         q += (uint64_t)gridDim.x * blockDim.x) {
+        const unsigned long long k = keys[q];
+        pairs[q] = make_int2((int32_t)(k >> jbits), (int32_t)(k & mask));
+    }
+}
+
+int launch_delta_unpack(const unsigned long long* keys, uint64_t count, int jbits, int32_t* pairs,
+                        cudaStream_t s) {
+    if (count == 0) return 0;
+    uint64_t g = ceil_div(count, DELTA_BLOCK);
+    g = g > 152 * 16 ? 152 * 16 : g;
+    launch_k(k_keys_unpack, (unsigned)g, DELTA_BLOCK, 0, s, keys, count, jbits,
+             reinterpret_cast<int2*>(pairs));
+    return 1;
+}
+
 __global__ void k_delta_pad(DeltaArgs a) {
     pdl_begin();
     const unsigned long long used = a.counters[2];

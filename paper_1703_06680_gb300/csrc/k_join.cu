@@ -32,6 +32,8 @@
 // list does not fit flag their subscriptions for the range path.
 #include <atomic>
 
+#include <algorithm>
+
 #include "emit.cuh"
 
 namespace ddm {
@@ -42,6 +44,7 @@ constexpr uint32_t JOIN_CHUNK = 512;
 constexpr int JOIN_SHIFT = 11;  // windows of at most 2048 stream positions (DDM_PARAM_JOIN_SHIFT)
 constexpr uint32_t JOIN_MAXSUB = 1u << JOIN_SHIFT;
 constexpr uint32_t JOIN_LONG_RANGE = 16;  // candidate ranges walked by the whole warp
+static_assert(JOIN_LONG_RANGE <= 32, "a short range's survivors fit a 32-bit mask");
 
 // Dynamic shared memory of one join block for d dimensions.
 __host__ __device__ inline size_t join_smem_bytes(int d) {
@@ -72,6 +75,42 @@ __device__ __forceinline__ uint32_t chunk_count_at_most(const uint32_t* sk, uint
 
 // DD > 0: compiled for DD = d - 1 extra dimensions; DD = 0: any d (arrays of
 // DDM_MAX_DIMS - 1, runtime bound).
+// Survivor slots of one warp: reserved from the window's fill counter in
+// granules (one atomic per granule, not per warp step) of about 1/128 of the
+// window's slice, between 32 and 512; slots a warp reserved but did not use
+// are set to ~0 (sorted last).  All members are warp-uniform.
+struct SurvSlots {
+    unsigned long long next = 0, left = 0;
+    uint32_t gran = 32;
+
+    // Slots for cnt keys (cnt warp-uniform); returns the first.  Called by all
+    // 32 lanes together.
+    __device__ __forceinline__ unsigned long long take(uint32_t cnt, unsigned long long* sv,
+                                                       unsigned long long* fill,
+                                                       unsigned long long cap, int lane) {
+        if (cnt > left) {
+            pad(sv, cap, lane);
+            const unsigned long long want = cnt > gran ? cnt : gran;
+            unsigned long long b = 0;
+            if (lane == 0) b = atomicAdd(fill, want);
+            next = __shfl_sync(0xffffffffu, b, 0);
+            left = want;
+        }
+        const unsigned long long r = next;
+        next += cnt;
+        left -= cnt;
+        return r;
+    }
+
+    // The unused reserved slots become ~0.
+    __device__ __forceinline__ void pad(unsigned long long* sv, unsigned long long cap, int lane) {
+        for (unsigned long long q = lane; q < left; q += 32)
+            if (next + q < cap) sv[next + q] = ~0ull;
+        next += left;
+        left = 0;
+    }
+};
+
 template <bool WRITE, int DD>
 __global__ void __launch_bounds__(JOIN_BLOCK) k_join(EmitArgs a, DevStatus* st) {
     constexpr int NK = DD > 0 ? DD : DDM_MAX_DIMS - 1;
@@ -91,6 +130,7 @@ __global__ void __launch_bounds__(JOIN_BLOCK) k_join(EmitArgs a, DevStatus* st) 
     __shared__ uint32_t c_sk[JOIN_CHUNK];             // sorted dim-1 lo keys
     __shared__ uint32_t s_wmax[JOIN_WARPS];
     __shared__ uint32_t s_pmax, s_first;
+    const bool rec_surv = !WRITE && a.surv != nullptr;
 
     if (read_error(st)) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -104,6 +144,13 @@ __global__ void __launch_bounds__(JOIN_BLOCK) k_join(EmitArgs a, DevStatus* st) 
         if (tid == 0) raise_error(st, DDM_ERR_INTERNAL, 16);
         return;
     }
+    // Count pass with survivor recording: this window's slice of the list,
+    // surv_cap entries per subscription starting here (ranks r0 .. r0 + ns).
+    unsigned long long* const sv_fill = rec_surv ? a.surv_fill + w : nullptr;
+    unsigned long long* const sv = rec_surv ? a.surv + (uint64_t)r0 * a.surv_cap : nullptr;
+    const unsigned long long sv_cap = (unsigned long long)ns * a.surv_cap;
+    SurvSlots slots;
+    slots.gran = (uint32_t)min(max(sv_cap / 128, 32ull), 512ull);
     const uint32_t lw_n = t0.y - t0.z;
     const bool overflow = !(lw_n <= a.lcap && a.lw_off[w] + lw_n <= a.lw_cap);
     if (tid == 0) s_pmax = 0;
@@ -252,6 +299,8 @@ __global__ void __launch_bounds__(JOIN_BLOCK) k_join(EmitArgs a, DevStatus* st) 
                 }
             }
             const bool longr = b1 - b0 >= JOIN_LONG_RANGE;
+            const uint32_t cur0 = cur;
+            uint32_t passmask = 0;  // short range: bit x - b0 = candidate x survives
             if (b0 < b1 && !longr) {
                 int2* seg = reinterpret_cast<int2*>(a.pairs) + obase;
                 for (uint32_t x = b0; x < b1; ++x) {
@@ -266,7 +315,28 @@ __global__ void __launch_bounds__(JOIN_BLOCK) k_join(EmitArgs a, DevStatus* st) 
                     }
                     if (pass) {
                         if (WRITE && cur < c) seg[cur] = make_int2(i_out, (int32_t)(c_id[x] - j_base));
+                        passmask |= 1u << (x - b0);
                         ++cur;
+                    }
+                }
+            }
+            if (rec_surv) {  // the short ranges' survivors: one shared reservation per warp
+                const uint32_t mine = (b0 < b1 && !longr) ? cur - cur0 : 0u;
+                uint32_t incl = mine;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const uint32_t wtot = __shfl_sync(0xffffffffu, incl, 31);
+                unsigned long long pos = 0;
+                if (wtot) pos = slots.take(wtot, sv, sv_fill, sv_cap, lane) + incl - mine;
+                if (mine) {  // the survivors of the short range, from its mask
+                    const unsigned long long ihi = (unsigned long long)s_id[k] << a.id_bits;
+                    for (uint32_t mm = passmask; mm; mm &= mm - 1u) {
+                        const uint32_t x = b0 + (uint32_t)(__ffs(mm) - 1);
+                        if (pos < sv_cap) sv[pos] = ihi | c_id[x];
+                        ++pos;
                     }
                 }
             }
@@ -278,6 +348,7 @@ __global__ void __launch_bounds__(JOIN_BLOCK) k_join(EmitArgs a, DevStatus* st) 
                 const uint32_t sph = __shfl_sync(0xffffffffu, ph, src);
                 const uint32_t sb0 = __shfl_sync(0xffffffffu, b0, src);
                 const uint32_t sb1 = __shfl_sync(0xffffffffu, b1, src);
+                const uint32_t sid_src = __shfl_sync(0xffffffffu, k < ns ? s_id[k] : 0u, src);
                 uint32_t scur = __shfl_sync(0xffffffffu, cur, src);
                 uint2 sown[NK];
 #pragma unroll
@@ -310,6 +381,13 @@ __global__ void __launch_bounds__(JOIN_BLOCK) k_join(EmitArgs a, DevStatus* st) 
                         }
                     }
                     const unsigned bal = __ballot_sync(0xffffffffu, pass);
+                    if (rec_surv && bal) {
+                        const unsigned long long b =
+                            slots.take((uint32_t)__popc(bal), sv, sv_fill, sv_cap, lane) +
+                            __popc(bal & ((1u << lane) - 1u));
+                        if (pass && b < sv_cap)
+                            sv[b] = ((unsigned long long)sid_src << a.id_bits) | c_id[xx];
+                    }
                     if (WRITE) {
                         const uint32_t r = scur + __popc(bal & ((1u << lane) - 1u));
                         if (pass && r < sc) sseg[r] = make_int2(si, (int32_t)(c_id[xx] - sj));
@@ -322,6 +400,7 @@ __global__ void __launch_bounds__(JOIN_BLOCK) k_join(EmitArgs a, DevStatus* st) 
         }
         __syncthreads();
     }
+    if (rec_surv) slots.pad(sv, sv_cap, lane);
     for (uint32_t k = tid; k < ns; k += JOIN_BLOCK) {
         const uint32_t i = s_id[k];
         if (!WRITE) a.cnt[i] = s_cnt[k];
@@ -351,6 +430,28 @@ static void launch_join_w(const EmitArgs& a, size_t smem, DevStatus* st, cudaStr
         case 3: launch_join_t<WRITE, 3>(a, smem, st, s); break;
         default: launch_join_t<WRITE, 0>(a, smem, st, s); break;
     }
+}
+
+// Window w's used entries (its fill, holes included) moved to dst[pos[w] ..).
+__global__ void k_surv_compact(const unsigned long long* __restrict__ surv,
+                               const unsigned long long* __restrict__ fill,
+                               const uint4* __restrict__ windows, unsigned long long per_sub,
+                               const unsigned long long* __restrict__ pos,
+                               unsigned long long* __restrict__ dst) {
+    pdl_begin();
+    const uint32_t w = blockIdx.x;
+    const unsigned long long* src = surv + (uint64_t)windows[w].x * per_sub;
+    unsigned long long* out = dst + pos[w];
+    const unsigned long long f = fill[w];
+    for (uint64_t q = threadIdx.x; q < f; q += blockDim.x) out[q] = src[q];
+}
+
+int launch_surv_compact(const unsigned long long* surv, const unsigned long long* fill,
+                        const uint4* windows, uint32_t num_win, unsigned long long per_sub,
+                        const unsigned long long* pos, unsigned long long* dst, cudaStream_t s) {
+    if (num_win == 0) return 0;
+    launch_k(k_surv_compact, num_win, 256, 0, s, surv, fill, windows, per_sub, pos, dst);
+    return 1;
 }
 
 int launch_join(const EmitArgs& a, bool write, DevStatus* st, cudaStream_t s) {

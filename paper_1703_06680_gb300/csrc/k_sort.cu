@@ -223,9 +223,9 @@ k_downsweep(const KeyT* __restrict__ keys_in, const uint32_t* __restrict__ vals_
     const bool full = tbase + TILE <= E;
     if (tid == 0 && full) {  // the tile is in flight while the digit offsets are formed
         mbar_init(&sm.bar, 1);
-        mbar_expect_tx(&sm.bar, TILE * (sizeof(KeyT) + sizeof(uint32_t)));
+        mbar_expect_tx(&sm.bar, TILE * (sizeof(KeyT) + (vals_in ? sizeof(uint32_t) : 0)));
         tma_load_1d(sm.keys, keys_in + tbase, TILE * sizeof(KeyT), &sm.bar);
-        tma_load_1d(sm.vals_raw, vals_in + tbase, TILE * sizeof(uint32_t), &sm.bar);
+        if (vals_in) tma_load_1d(sm.vals_raw, vals_in + tbase, TILE * sizeof(uint32_t), &sm.bar);
     }
     for (int t = tid; t < WARPS * RADIX; t += SORT_BLOCK) (&sm.whist[0][0])[t] = 0;
     if (grp) {  // fused offsets (thread = digit)
@@ -258,7 +258,7 @@ k_downsweep(const KeyT* __restrict__ keys_in, const uint32_t* __restrict__ vals_
         for (int i = tid; i < TILE; i += SORT_BLOCK) {
             const uint64_t e = tbase + i;
             sm.keys[i] = e < E ? keys_in[e] : ~(KeyT)0;  // tail: all-ones key, digit 255, last
-            sm.vals_raw[i] = e < E ? vals_in[e] : 0u;
+            sm.vals_raw[i] = e < E && vals_in ? vals_in[e] : 0u;
         }
         __syncthreads();
     }
@@ -314,7 +314,7 @@ k_downsweep(const KeyT* __restrict__ keys_in, const uint32_t* __restrict__ vals_
     for (int i = 0; i < ITEMS; ++i) {
         const uint32_t slot = sm.tile_start[dig[i]] + sm.whist[warp][dig[i]] + rank[i];
         sm.keys[slot] = key[i];
-        sm.u.vals[slot] = sm.vals_raw[wofs + i * 32 + lane];
+        if (vals_in) sm.u.vals[slot] = sm.vals_raw[wofs + i * 32 + lane];
     }
     __syncthreads();
     // Runs of equal digits go to consecutive global positions (coalesced).
@@ -326,7 +326,7 @@ k_downsweep(const KeyT* __restrict__ keys_in, const uint32_t* __restrict__ vals_
         const uint32_t pos = sm.gbase[d] + (uint32_t)(s - sm.tile_start[d]);
         if (pos < E) {
             if (write_keys) keys_out[pos] = k;
-            vals_out[pos] = sm.u.vals[s];
+            if (vals_out) vals_out[pos] = sm.u.vals[s];
         }
     }
 }

@@ -77,6 +77,7 @@ int launch_keybuild_d0(const float* sub_lo, const float* sub_hi, const float* up
 // clear_ptr/clear_words (16-byte words, may be NULL/0): a buffer that the last
 // pass's blocks zero while their tiles load (the rank-record tables of the
 // sweep scan that follows).
+// vals0 and vals1 may both be NULL: the keys alone are sorted.
 // items: keys per thread of a 32-bit sort, 12, 16 or 18 (0: the default, 18);
 // 64-bit keys always use 12.  The scratch must be sized for the same choice
 // (sort_tiles<KeyT>(E, items)).

@@ -408,3 +408,46 @@ def test_tile_parameters_change_only_speed():
         for bad in ((ddm._lib.PARAM_SORT_ITEMS, 20), (ddm._lib.PARAM_JOIN_SHIFT, 12)):
             with pytest.raises(ddm.DDMError):
                 c.set_param(*bad)
+
+
+@pytest.mark.parametrize("d,alpha", [(2, 100.0), (3, 1.0), (3, 100.0)])
+def test_survivor_path_and_general_path_agree(d, alpha):
+    # d > 1: the count pass records its survivors and the pairs come from one
+    # sort of them once the context knows the output size (a first call without
+    # that hint may run the general write pass instead).  Both give the
+    # oracle's list; so does a later call on another instance.
+    import paper_1703_06680_gb300 as ddm
+    reg = synth.large_nd(d, alpha, N=300_000 if alpha == 100.0 else 600_000)
+    from tests.oracle_pool import check_full
+    with ddm.Context(0) as c:
+        c.set_param(ddm._lib.PARAM_ND_WRITE, 2)
+        t = to_dev(reg)
+        K = c.count(*t)
+        first = c.match(*t, cap=K)   # sized without a hint: may take either path
+        second = c.match(*t, cap=K)
+        assert c.stats()["survivor_calls"] >= 1
+        assert torch_equal(first, second)
+        assert check_full(second, ("large_nd", (d, alpha, 0, reg.n + reg.m)), reg.n) == K
+        small = synth.large_nd(d, alpha, N=20_001)
+        assert np.array_equal(gpu_pairs(c, small), oracle.sbm(small))
+
+
+def torch_equal(a, b):
+    import torch
+    return a.shape == b.shape and bool(torch.equal(a, b))
+
+
+@pytest.mark.parametrize("d,alpha", [(2, 1.0), (3, 100.0)])
+def test_nd_write_modes_agree(d, alpha):
+    # Both ways of writing the d > 1 pairs, and the automatic choice, give the
+    # oracle's list on the same context (two calls each, the second sized).
+    import paper_1703_06680_gb300 as ddm
+    reg = synth.large_nd(d, alpha, N=80_001)
+    want = oracle.sbm(reg)
+    with ddm.Context(0) as c:
+        for mode in (1, 2, 0):
+            c.set_param(ddm._lib.PARAM_ND_WRITE, mode)
+            for _ in range(2):
+                assert np.array_equal(gpu_pairs(c, reg), want), mode
+        with pytest.raises(ddm.DDMError):
+            c.set_param(ddm._lib.PARAM_ND_WRITE, 3)
