@@ -492,6 +492,13 @@ int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
     // aligned too, so rounding up to 16-byte words stays inside them.
     const size_t rec_words =
         ((size_t)((char*)(rec.upd_order + pl.m) - (char*)rec.s_lo) + 15) / 16;
+    // The sweep's tile aggregates (S lowers, U lowers, S uppers per SCAN_TILE
+    // positions) are counted by the sort's last pass, which knows every output
+    // position, into the scan status words (zeroed above, 24 bytes per tile
+    // against the 16 used); the sweep's tiles then need no look-back.
+    uint32_t* kinds = !batch && ceil_div(pl.E, (uint64_t)SCAN_TILE) <= SCAN_KINDS_MAX_TILES
+                          ? reinterpret_cast<uint32_t*>(pl.scan_status)
+                          : nullptr;
     if (batch) {
         L += launch_radix_sort<unsigned long long>(
             (unsigned long long*)pl.keys0, pl.vals0, (unsigned long long*)pl.keys1, pl.vals1, pl.E,
@@ -499,10 +506,10 @@ int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
     } else {
         L += launch_radix_sort<uint32_t>((uint32_t*)pl.keys0, pl.vals0, (uint32_t*)pl.keys1,
                                          pl.vals1, pl.E, pl.passes, pl.sort, !c->keep_keys,
-                                         c->dstat, s, rec.s_lo, rec_words, pl.sort_items);
+                                         c->dstat, s, rec.s_lo, rec_words, pl.sort_items, kinds);
     }
     mark(c, 2);
-    L += launch_sweep_scan(vals_sorted, pl.E, pl.n, pl.m, rec, pl.scan_status, c->dstat, s);
+    L += launch_sweep_scan(vals_sorted, pl.E, pl.n, pl.m, rec, pl.scan_status, c->dstat, s, kinds);
     mark(c, 3);
     // d = 1: the counts are formed inside the offsets scan (one kernel for a4
     // and a5), except for diagnostics, which also want the update counts.

@@ -199,6 +199,19 @@ struct DownSmem {
     uint64_t bar;
 };
 
+// Adds one endpoint of the sorted output to the kind counters of its scan tile
+// (see launch_radix_sort): lanes with the same (tile, kind) are counted by one
+// atomic of their lowest lane.  Called by all lanes of the warp.
+__device__ __forceinline__ void count_kind(uint32_t* kinds, uint32_t pos, uint32_t E, uint32_t v,
+                                           int lane) {
+    static_assert((SCAN_TILE & (SCAN_TILE - 1)) == 0, "scan tiles are a power of two");
+    const uint32_t kind = v >> 30;
+    const bool use = pos < E && kind != KIND_UHI;
+    const uint32_t key = use ? ((pos / SCAN_TILE) << 2 | kind) : 0xffffffffu;
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    if (use && lane == __ffs(peers) - 1) atomicAdd(&kinds[key], (uint32_t)__popc(peers));
+}
+
 // Downsweep: the tile arrives by TMA bulk copies (keys and values); stable
 // rank of every key inside the tile (per-warp peer masks, warp-ordered
 // prefix); exchange through shared memory into digit-major order; runs of
@@ -210,7 +223,8 @@ k_downsweep(const KeyT* __restrict__ keys_in, const uint32_t* __restrict__ vals_
             KeyT* __restrict__ keys_out, uint32_t* __restrict__ vals_out, uint32_t E, int shift,
             const unsigned long long* __restrict__ base, const uint32_t* __restrict__ tile_hist,
             const uint32_t* __restrict__ grp, uint32_t tiles, int write_keys,
-            uint4* __restrict__ clr, uint64_t clr_words, DevStatus* st) {
+            uint4* __restrict__ clr, uint64_t clr_words, uint32_t* __restrict__ kinds,
+            DevStatus* st) {
     pdl_begin();
     using Smem = DownSmem<KeyT, ITEMS>;
     constexpr int TILE = Smem::TILE;
@@ -231,16 +245,25 @@ k_downsweep(const KeyT* __restrict__ keys_in, const uint32_t* __restrict__ vals_
     if (grp) {  // fused offsets (thread = digit)
         const uint32_t g = tile >> SORT_GROUP_SHIFT;
         const uint32_t ngroups = (tiles + (1u << SORT_GROUP_SHIFT) - 1) >> SORT_GROUP_SHIFT;
+        // Every load is issued before the first sum (predicated, fixed counts),
+        // so the bases cost about two L2 round trips rather than one per batch.
+        constexpr int MAXG = (int)(SORT_FUSED_MAX_TILES >> SORT_GROUP_SHIFT);
+        constexpr int GT = 1 << SORT_GROUP_SHIFT;
+        uint32_t gv[MAXG], tv[GT - 1];
+#pragma unroll
+        for (int q = 0; q < MAXG; ++q) gv[q] = (uint32_t)q < ngroups ? grp[q * RADIX + tid] : 0u;
+        const uint32_t t0 = g << SORT_GROUP_SHIFT;
+#pragma unroll
+        for (int k = 0; k < GT - 1; ++k)
+            tv[k] = t0 + k < tile ? tile_hist[(uint64_t)(t0 + k) * RADIX + tid] : 0u;
         uint32_t total = 0, before = 0;
-#pragma unroll 8
-        for (uint32_t q = 0; q < ngroups; ++q) {
-            const uint32_t v = grp[q * RADIX + tid];
-            total += v;
-            before += q < g ? v : 0u;
+#pragma unroll
+        for (int q = 0; q < MAXG; ++q) {
+            total += gv[q];
+            before += (uint32_t)q < g ? gv[q] : 0u;
         }
-#pragma unroll 8
-        for (uint32_t t = g << SORT_GROUP_SHIFT; t < tile; ++t)
-            before += tile_hist[(uint64_t)t * RADIX + tid];
+#pragma unroll
+        for (int k = 0; k < GT - 1; ++k) before += tv[k];
         sm.gbase[tid] = block_excl_scan_256(total, sm.warp_tmp) + before;
     } else {
         sm.gbase[tid] = (uint32_t)base[(uint64_t)tid * tiles + tile];
@@ -328,6 +351,7 @@ k_downsweep(const KeyT* __restrict__ keys_in, const uint32_t* __restrict__ vals_
             if (write_keys) keys_out[pos] = k;
             if (vals_out) vals_out[pos] = sm.u.vals[s];
         }
+        if (kinds) count_kind(kinds, pos, E, sm.u.vals[s], lane);
     }
 }
 
@@ -335,7 +359,7 @@ template <typename KeyT, int ITEMS>
 static int radix_sort_items(KeyT* keys0, uint32_t* vals0, KeyT* keys1, uint32_t* vals1,
                             uint64_t E, int passes, const SortScratch& sc, bool skip_last_keys,
                             DevStatus* st, cudaStream_t s, void* clear_ptr,
-                            uint64_t clear_words) {
+                            uint64_t clear_words, uint32_t* kinds) {
     const uint64_t tiles = ceil_div(E, (uint64_t)SORT_BLOCK * ITEMS);
     KeyT* kb[2] = {keys0, keys1};
     uint32_t* vb[2] = {vals0, vals1};
@@ -366,7 +390,7 @@ static int radix_sort_items(KeyT* keys0, uint32_t* vals0, KeyT* keys1, uint32_t*
                  vb[p & 1], kb[(p + 1) & 1], vb[(p + 1) & 1], (uint32_t)E, 8 * p, sc.offs,
                  sc.tile_hist, grp, (uint32_t)tiles, write_keys,
                  last ? static_cast<uint4*>(clear_ptr) : static_cast<uint4*>(nullptr),
-                 last ? clear_words : 0ull, st);
+                 last ? clear_words : 0ull, last && vals0 ? kinds : nullptr, st);
         ++launches;
     }
     return launches;
@@ -375,29 +399,30 @@ static int radix_sort_items(KeyT* keys0, uint32_t* vals0, KeyT* keys1, uint32_t*
 template <typename KeyT>
 int launch_radix_sort(KeyT* keys0, uint32_t* vals0, KeyT* keys1, uint32_t* vals1, uint64_t E,
                       int passes, const SortScratch& sc, bool skip_last_keys, DevStatus* st,
-                      cudaStream_t s, void* clear_ptr, uint64_t clear_words, int items) {
+                      cudaStream_t s, void* clear_ptr, uint64_t clear_words, int items,
+                      uint32_t* kinds) {
     if (E == 0) return 0;
     if (sizeof(KeyT) == 8 || items == 0) items = sort_items<KeyT>();
     switch (items) {  // the tile sizes a context may choose (DDM_PARAM_SORT_ITEMS)
         case 12:
             return radix_sort_items<KeyT, 12>(keys0, vals0, keys1, vals1, E, passes, sc,
-                                              skip_last_keys, st, s, clear_ptr, clear_words);
+                                              skip_last_keys, st, s, clear_ptr, clear_words, kinds);
         case 16:
             return radix_sort_items<KeyT, 16>(keys0, vals0, keys1, vals1, E, passes, sc,
-                                              skip_last_keys, st, s, clear_ptr, clear_words);
+                                              skip_last_keys, st, s, clear_ptr, clear_words, kinds);
         default:
             return radix_sort_items<KeyT, SORT_ITEMS_32>(keys0, vals0, keys1, vals1, E, passes,
                                                          sc, skip_last_keys, st, s, clear_ptr,
-                                                         clear_words);
+                                                         clear_words, kinds);
     }
 }
 
 template int launch_radix_sort<uint32_t>(uint32_t*, uint32_t*, uint32_t*, uint32_t*, uint64_t,
                                          int, const SortScratch&, bool, DevStatus*, cudaStream_t,
-                                         void*, uint64_t, int);
+                                         void*, uint64_t, int, uint32_t*);
 template int launch_radix_sort<unsigned long long>(unsigned long long*, uint32_t*,
                                                    unsigned long long*, uint32_t*, uint64_t, int,
                                                    const SortScratch&, bool, DevStatus*,
-                                                   cudaStream_t, void*, uint64_t, int);
+                                                   cudaStream_t, void*, uint64_t, int, uint32_t*);
 
 }  // namespace ddm

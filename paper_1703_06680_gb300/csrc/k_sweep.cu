@@ -29,16 +29,22 @@ __device__ __forceinline__ unsigned long long kind_inc(uint32_t kind) {
                                    : kind == KIND_SHI ? (1ull << 42) : 0ull;
 }
 
+// Two ways to the counts before a tile.  With `kinds` (the tile aggregates that
+// the sort's last pass formed), the block sums the aggregates of all earlier
+// tiles itself; no tile waits for another.  Without, each tile publishes its
+// aggregate and looks back (decoupled look-back, tiles numbered in start order).
 __global__ void __launch_bounds__(SCAN_BLOCK)
 k_sweep_scan(const uint32_t* __restrict__ vals, uint32_t E, uint32_t n, uint32_t m,
              Records rec, unsigned long long* __restrict__ status,
-             uint32_t* __restrict__ tile_counter, DevStatus* st) {
+             uint32_t* __restrict__ tile_counter, const uint4* __restrict__ kinds,
+             DevStatus* st) {
     pdl_begin();
     __shared__ unsigned long long warp_sum[SCAN_BLOCK / 32];
+    __shared__ uint32_t kind_sum[SCAN_BLOCK / 32][3];
     __shared__ unsigned long long tile_prefix[3];
     __shared__ uint32_t tile_id_s;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) tile_id_s = atomicAdd(tile_counter, 1u);
+    if (tid == 0) tile_id_s = kinds ? blockIdx.x : atomicAdd(tile_counter, 1u);
     __syncthreads();
     const uint32_t tile = tile_id_s;
     const uint64_t base = (uint64_t)tile * SCAN_TILE + (uint64_t)tid * SCAN_ITEMS;
@@ -55,6 +61,14 @@ k_sweep_scan(const uint32_t* __restrict__ vals, uint32_t E, uint32_t n, uint32_t
 #pragma unroll
         for (int k = 0; k < SCAN_ITEMS; ++k) v[k] = base + k < E ? vals[base + k] : 0xFFFFFFFFu;
     }
+    uint32_t ka = 0, kb = 0, kc = 0;  // S lowers, U lowers, S uppers in earlier tiles
+    if (kinds) {
+#pragma unroll 4
+        for (uint32_t t = tid; t < tile; t += SCAN_BLOCK) {
+            const uint4 q = kinds[t];
+            ka += q.x; kb += q.y; kc += q.z;
+        }
+    }
     unsigned long long mine = 0;
 #pragma unroll
     for (int k = 0; k < SCAN_ITEMS; ++k)
@@ -68,6 +82,14 @@ k_sweep_scan(const uint32_t* __restrict__ vals, uint32_t E, uint32_t n, uint32_t
         if (lane >= o) x += y;
     }
     if (lane == 31) warp_sum[warp] = x;
+    if (kinds) {
+        ka = __reduce_add_sync(0xffffffffu, ka);
+        kb = __reduce_add_sync(0xffffffffu, kb);
+        kc = __reduce_add_sync(0xffffffffu, kc);
+        if (lane == 0) {
+            kind_sum[warp][0] = ka; kind_sum[warp][1] = kb; kind_sum[warp][2] = kc;
+        }
+    }
     __syncthreads();
     unsigned long long wexcl = 0, total = 0;
 #pragma unroll
@@ -78,8 +100,15 @@ k_sweep_scan(const uint32_t* __restrict__ vals, uint32_t E, uint32_t n, uint32_t
     }
     unsigned long long excl = wexcl + x - mine;
 
-    // Publish the tile aggregate, one look-back word per counter, then look back.
-    if (warp < 3) {
+    if (kinds) {
+        if (tid < 3) {
+            unsigned long long pre = 0;
+#pragma unroll
+            for (int w = 0; w < SCAN_BLOCK / 32; ++w) pre += kind_sum[w][tid];
+            tile_prefix[tid] = pre;
+        }
+    } else if (warp < 3) {
+        // Publish the tile aggregate, one look-back word per counter, then look back.
         const unsigned long long agg = (total >> (21 * warp)) & ((1ull << 21) - 1);
         const uint64_t stride = gridDim.x + 1ull;
         unsigned long long* word = status + (uint64_t)warp * stride + tile;
@@ -140,14 +169,16 @@ k_sweep_scan(const uint32_t* __restrict__ vals, uint32_t E, uint32_t n, uint32_t
 }
 
 int launch_sweep_scan(const uint32_t* vals, uint64_t E, int64_t n, int64_t m, const Records& rec,
-                       unsigned long long* status, DevStatus* st, cudaStream_t s) {
+                       unsigned long long* status, DevStatus* st, cudaStream_t s,
+                       const uint32_t* kinds) {
     if (E == 0) return 0;
     const uint64_t tiles = ceil_div(E, SCAN_TILE);
     // layout: 3 counters x (tiles + 1) words; the last word of counter 0's row
     // region doubles as the tile counter.
     uint32_t* counter = reinterpret_cast<uint32_t*>(status + 3 * (tiles + 1));
+    if (tiles > SCAN_KINDS_MAX_TILES) kinds = nullptr;
     launch_k(k_sweep_scan, (unsigned)tiles, SCAN_BLOCK, 0, s, vals, (uint32_t)E, (uint32_t)n,
-                                                        (uint32_t)m, rec, status, counter, st);
+             (uint32_t)m, rec, status, counter, reinterpret_cast<const uint4*>(kinds), st);
     return 1;
 }
 
@@ -204,13 +235,8 @@ struct OffsetSource {
     uint32_t lcap;
 };
 
-__device__ __forceinline__ uint32_t offset_value(const OffsetSource& src, uint64_t i, bool& bad) {
-    if (src.kind == 1) {
-        const uint32_t b = src.hi[i].y, c = src.lo[i].z;
-        bad |= b < c;
-        src.cnt_out[i] = b - c;
-        return b - c;
-    }
+// Kinds 0 and 2 (kind 1 is read inside k_offsets).
+__device__ __forceinline__ uint32_t offset_value(const OffsetSource& src, uint64_t i) {
     if (src.kind == 2) {
         const uint4 t = src.windows[i];
         const uint32_t sz = t.y - t.z;
@@ -236,12 +262,31 @@ k_offsets(OffsetSource src, uint32_t n, unsigned long long* __restrict__ off,
     const uint32_t tile = tile_id_s;
     const uint64_t tbase = (uint64_t)tile * OFF_TILE;
     // Coalesced load (striped), then each thread takes OFF_ITEMS consecutive values.
+    // Counts from rank records: every load is issued before the first store of
+    // a count, which the compiler could not otherwise move loads across.
     {
         bool bad = false;
+        if (src.kind == 1) {
+            uint32_t b[OFF_ITEMS], c[OFF_ITEMS];
 #pragma unroll
-        for (int k = 0; k < OFF_ITEMS; ++k) {
-            const int i = k * OFF_BLOCK + tid;
-            s_in[pad32(i)] = tbase + i < n ? offset_value(src, tbase + i, bad) : 0u;
+            for (int k = 0; k < OFF_ITEMS; ++k) {
+                const uint64_t i = tbase + k * OFF_BLOCK + tid;
+                b[k] = i < n ? src.hi[i].y : 0u;
+                c[k] = i < n ? src.lo[i].z : 0u;
+            }
+#pragma unroll
+            for (int k = 0; k < OFF_ITEMS; ++k) {
+                const int i = k * OFF_BLOCK + tid;
+                bad |= b[k] < c[k];
+                s_in[pad32(i)] = b[k] - c[k];
+                if (tbase + i < n) src.cnt_out[tbase + i] = b[k] - c[k];
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < OFF_ITEMS; ++k) {
+                const int i = k * OFF_BLOCK + tid;
+                s_in[pad32(i)] = tbase + i < n ? offset_value(src, tbase + i) : 0u;
+            }
         }
         if (bad) raise_error(st, DDM_ERR_INTERNAL, 4);
     }

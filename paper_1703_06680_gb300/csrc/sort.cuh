@@ -81,10 +81,15 @@ int launch_keybuild_d0(const float* sub_lo, const float* sub_hi, const float* up
 // items: keys per thread of a 32-bit sort, 12, 16 or 18 (0: the default, 18);
 // 64-bit keys always use 12.  The scratch must be sized for the same choice
 // (sort_tiles<KeyT>(E, items)).
+// kinds (may be NULL; needs values in endpoint-payload form): per SCAN_TILE
+// positions of the sorted output, four u32 counters, zeroed by the caller, to
+// which the last pass adds how many S lowers, U lowers and S uppers it writes
+// into that range (the fourth stays 0).  These are the tile aggregates of the
+// sweep scan (launch_sweep_scan), formed where the output positions are known.
 template <typename KeyT>
 int launch_radix_sort(KeyT* keys0, uint32_t* vals0, KeyT* keys1, uint32_t* vals1, uint64_t E,
                       int passes, const SortScratch& sc, bool skip_last_keys, DevStatus* st,
                       cudaStream_t s, void* clear_ptr = nullptr, uint64_t clear_words = 0,
-                      int items = 0);
+                      int items = 0, uint32_t* kinds = nullptr);
 
 }  // namespace ddm

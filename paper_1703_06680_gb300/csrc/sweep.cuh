@@ -38,9 +38,14 @@ struct Records {
     uint32_t *dbg_who, *dbg_subset, *dbg_updset;  // optional diagnostics (may be NULL)
 };
 
-// Status words: 3 * (ceil(E / SCAN_TILE) + 1) u64, zeroed.
+// Status words: 3 * (ceil(E / SCAN_TILE) + 1) u64, zeroed.  kinds (may be NULL):
+// the tile aggregates that launch_radix_sort's last pass formed (4 u32 per
+// SCAN_TILE positions); with them, and at most SCAN_KINDS_MAX_TILES tiles, the
+// tiles take their prefixes from the aggregates and the status words go unused.
+constexpr uint64_t SCAN_KINDS_MAX_TILES = 4096;
 int launch_sweep_scan(const uint32_t* vals, uint64_t E, int64_t n, int64_t m, const Records& rec,
-                       unsigned long long* status, DevStatus* st, cudaStream_t s);
+                       unsigned long long* status, DevStatus* st, cudaStream_t s,
+                       const uint32_t* kinds = nullptr);
 
 // cnt[i] = B_i - C_i; optional upd_cnt[j] = B_j - C_j.
 int launch_rank_count(const Records& rec, int64_t n, int64_t m, uint32_t* cnt,
