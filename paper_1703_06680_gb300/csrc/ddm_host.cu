@@ -508,12 +508,16 @@ int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
                                          pl.vals1, pl.E, pl.passes, pl.sort, !c->keep_keys,
                                          c->dstat, s, rec.s_lo, rec_words, pl.sort_items, kinds);
     }
-    mark(c, 2);
-    L += launch_sweep_scan(vals_sorted, pl.E, pl.n, pl.m, rec, pl.scan_status, c->dstat, s, kinds);
-    mark(c, 3);
     // d = 1: the counts are formed inside the offsets scan (one kernel for a4
-    // and a5), except for diagnostics, which also want the update counts.
+    // and a5), except for diagnostics, which also want the update counts.  The
+    // sweep adds up the counts per id tile into the offsets scan's status words
+    // (zeroed above; one word per tile), so that scan needs no look-back.
     const bool fused_counts = job.d == 1 && !dbg;
+    unsigned long long* cnt_agg = fused_counts ? pl.off_status : nullptr;
+    mark(c, 2);
+    L += launch_sweep_scan(vals_sorted, pl.E, pl.n, pl.m, rec, pl.scan_status, c->dstat, s, kinds,
+                           cnt_agg);
+    mark(c, 3);
     if (job.d == 1) {
         if (!fused_counts)
             L += launch_rank_count(rec, pl.n, pl.m, pl.cnt, dbg ? dbg->upd_cnt : nullptr, c->dstat, s);
@@ -533,19 +537,21 @@ int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
     if (dbg && dbg->sub_cnt && pl.n > 0)
         CK(cudaMemcpyAsync(dbg->sub_cnt, pl.cnt, pl.n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
     const uint64_t off_cap = mode == Mode::Match && phase == Phase::All ? cap : ~0ull;
-    if (fused_counts)
+    if (pl.window && !fused_counts)
+        return fail(c, DDM_ERR_INTERNAL, "window path without fused counts");
+    // Window path: the rank tables of the emission are scattered from id order
+    // here (subscriptions by the offsets scan, updates by launch_upd_ranks).
+    if (fused_counts) {
         L += launch_rank_offsets(rec, pl.n, pl.cnt, pl.off, off_cap, &c->dstat->K, pl.off_status,
-                                 c->dstat, s);
-    else
+                                 c->dstat, s, cnt_agg, pl.window ? pl.srank : nullptr, pl.soff);
+        if (pl.window) L += launch_upd_ranks(a, c->dstat, s);
+    } else
         L += launch_offsets(pl.cnt, pl.n, pl.off, off_cap, &c->dstat->K, pl.off_status, c->dstat, s);
     if (batch) L += launch_inst_offsets(ba, pl.off, pl.inst_off, s);
   }
   if (do_suffix) {
     mark(c, 5);
-    if (pl.window) {
-        L += launch_tile_active(a, c->dstat, s);
-        L += launch_win_setup(a, c->dstat, s);
-    }
+    if (pl.window) L += launch_win_setup(a, c->dstat, s);
     mark(c, 6);
     if (pl.window) L += launch_emit_window(a, c->dstat, s);
     else if (pl.join && mode == Mode::Match) {

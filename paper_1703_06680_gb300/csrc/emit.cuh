@@ -84,6 +84,9 @@ int launch_surv_compact(const unsigned long long* surv, const unsigned long long
 
 // Window path for d = 1.
 int launch_tile_active(const EmitArgs& a, DevStatus* st, cudaStream_t s);
+// Window path (fixed-slot lists): urank and the boundary lists from the
+// updates' records in id order; srank / soff come from launch_rank_offsets.
+int launch_upd_ranks(const EmitArgs& a, DevStatus* st, cudaStream_t s);
 int launch_win_setup(const EmitArgs& a, DevStatus* st, cudaStream_t s);
 int launch_emit_window(const EmitArgs& a, DevStatus* st, cudaStream_t s);
 

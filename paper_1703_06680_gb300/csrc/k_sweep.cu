@@ -33,18 +33,22 @@ __device__ __forceinline__ unsigned long long kind_inc(uint32_t kind) {
 // the sort's last pass formed), the block sums the aggregates of all earlier
 // tiles itself; no tile waits for another.  Without, each tile publishes its
 // aggregate and looks back (decoupled look-back, tiles numbered in start order).
-__global__ void __launch_bounds__(SCAN_BLOCK)
+// At most 64 registers: four blocks per SM keep every tile of 2e6 endpoints resident.
+__global__ void __launch_bounds__(SCAN_BLOCK, 4)
 k_sweep_scan(const uint32_t* __restrict__ vals, uint32_t E, uint32_t n, uint32_t m,
              Records rec, unsigned long long* __restrict__ status,
              uint32_t* __restrict__ tile_counter, const uint4* __restrict__ kinds,
-             DevStatus* st) {
+             unsigned long long* __restrict__ cnt_agg, uint32_t cnt_tiles, DevStatus* st) {
     pdl_begin();
     __shared__ unsigned long long warp_sum[SCAN_BLOCK / 32];
     __shared__ uint32_t kind_sum[SCAN_BLOCK / 32][3];
     __shared__ unsigned long long tile_prefix[3];
     __shared__ uint32_t tile_id_s;
+    extern __shared__ unsigned long long s_agg[];  // cnt_tiles words when cnt_agg is set
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) tile_id_s = kinds ? blockIdx.x : atomicAdd(tile_counter, 1u);
+    if (cnt_agg)
+        for (uint32_t t = tid; t < cnt_tiles; t += SCAN_BLOCK) s_agg[t] = 0ull;
     __syncthreads();
     const uint32_t tile = tile_id_s;
     const uint64_t base = (uint64_t)tile * SCAN_TILE + (uint64_t)tid * SCAN_ITEMS;
@@ -149,6 +153,10 @@ k_sweep_scan(const uint32_t* __restrict__ vals, uint32_t E, uint32_t n, uint32_t
         const uint32_t z = is_upper ? 0u : (is_upd ? cShi : cUhi);
         const uint32_t w = is_upper ? 0u : (is_upd ? cUlo : cSlo);
         tab[id] = make_uint4(p, y, z, w);
+        // B_i at S_i's upper endpoint, -C_i at its lower one (mod 2^64).
+        if (cnt_agg && !is_upd)
+            atomicAdd(&s_agg[id / OFF_TILE],
+                      is_upper ? (unsigned long long)y : 0ull - (unsigned long long)z);
         if (!is_upper) {
             const uint32_t r = is_upd ? cUlo : cSlo;
             if (r < (is_upd ? m : n)) (is_upd ? rec.upd_order : rec.sub_order)[r] = id;
@@ -166,19 +174,28 @@ k_sweep_scan(const uint32_t* __restrict__ vals, uint32_t E, uint32_t n, uint32_t
             rec.dbg_updset[p] = cUlo - cUhi_after;
         }
     }
+    if (cnt_agg) {
+        __syncthreads();
+        for (uint32_t t = tid; t < cnt_tiles; t += SCAN_BLOCK)
+            if (s_agg[t]) atomicAdd(&cnt_agg[t], s_agg[t]);
+    }
 }
 
 int launch_sweep_scan(const uint32_t* vals, uint64_t E, int64_t n, int64_t m, const Records& rec,
                        unsigned long long* status, DevStatus* st, cudaStream_t s,
-                       const uint32_t* kinds) {
+                       const uint32_t* kinds, unsigned long long* cnt_agg) {
     if (E == 0) return 0;
     const uint64_t tiles = ceil_div(E, SCAN_TILE);
     // layout: 3 counters x (tiles + 1) words; the last word of counter 0's row
     // region doubles as the tile counter.
     uint32_t* counter = reinterpret_cast<uint32_t*>(status + 3 * (tiles + 1));
     if (tiles > SCAN_KINDS_MAX_TILES) kinds = nullptr;
-    launch_k(k_sweep_scan, (unsigned)tiles, SCAN_BLOCK, 0, s, vals, (uint32_t)E, (uint32_t)n,
-             (uint32_t)m, rec, status, counter, reinterpret_cast<const uint4*>(kinds), st);
+    const uint64_t ctiles = ceil_div((uint64_t)n, (uint64_t)OFF_TILE);
+    if (ctiles > CNT_AGG_MAX_TILES) cnt_agg = nullptr;
+    const uint32_t ct = cnt_agg ? (uint32_t)ctiles : 0u;
+    launch_k(k_sweep_scan, (unsigned)tiles, SCAN_BLOCK, ct * sizeof(unsigned long long), s, vals,
+             (uint32_t)E, (uint32_t)n, (uint32_t)m, rec, status, counter,
+             reinterpret_cast<const uint4*>(kinds), cnt_agg, ct, st);
     return 1;
 }
 
@@ -233,6 +250,12 @@ struct OffsetSource {
     uint32_t* cnt_out;
     const uint4* windows;
     uint32_t lcap;
+    const unsigned long long* agg;  // kind 1: per-tile sums of the counts, or NULL
+    // kind 1, window emission (or NULL): the subscriptions' rank tables
+    // srank[r] = {i, pos(lo), pos(hi), cnt} and soff[r] = off[i], r = the rank of
+    // S_i's lower endpoint (its record's w field), scattered from id order.
+    uint4* srank;
+    unsigned long long* soff;
 };
 
 // Kinds 0 and 2 (kind 1 is read inside k_offsets).
@@ -254,16 +277,19 @@ k_offsets(OffsetSource src, uint32_t n, unsigned long long* __restrict__ off,
     __shared__ uint32_t s_in[OFF_TILE + OFF_TILE / 32];
     __shared__ unsigned long long s_out[OFF_TILE + OFF_TILE / 32];
     __shared__ unsigned long long warp_sum[OFF_BLOCK / 32];
+    __shared__ unsigned long long agg_sum[OFF_BLOCK / 32];
     __shared__ unsigned long long tile_prefix;
     __shared__ uint32_t tile_id_s;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) tile_id_s = atomicAdd(tile_counter, 1u);
+    if (tid == 0) tile_id_s = src.agg ? blockIdx.x : atomicAdd(tile_counter, 1u);
     __syncthreads();
     const uint32_t tile = tile_id_s;
     const uint64_t tbase = (uint64_t)tile * OFF_TILE;
     // Coalesced load (striped), then each thread takes OFF_ITEMS consecutive values.
     // Counts from rank records: every load is issued before the first store of
     // a count, which the compiler could not otherwise move loads across.
+    unsigned long long pre_part = 0;
+    uint32_t pl[OFF_ITEMS], ph[OFF_ITEMS], rk[OFF_ITEMS];  // kind 1: positions and rank
     {
         bool bad = false;
         if (src.kind == 1) {
@@ -271,9 +297,16 @@ k_offsets(OffsetSource src, uint32_t n, unsigned long long* __restrict__ off,
 #pragma unroll
             for (int k = 0; k < OFF_ITEMS; ++k) {
                 const uint64_t i = tbase + k * OFF_BLOCK + tid;
-                b[k] = i < n ? src.hi[i].y : 0u;
-                c[k] = i < n ? src.lo[i].z : 0u;
+                const uint4 lo = i < n ? src.lo[i] : make_uint4(0u, 0u, 0u, 0u);
+                const uint4 hi = i < n ? src.hi[i] : make_uint4(0u, 0u, 0u, 0u);
+                b[k] = hi.y;
+                c[k] = lo.z;
+                pl[k] = lo.x;
+                rk[k] = lo.w;
+                ph[k] = hi.x;
             }
+            if (src.agg)  // this thread's share of the earlier tiles' sums
+                for (uint32_t t = tid; t < tile; t += OFF_BLOCK) pre_part += src.agg[t];
 #pragma unroll
             for (int k = 0; k < OFF_ITEMS; ++k) {
                 const int i = k * OFF_BLOCK + tid;
@@ -305,6 +338,9 @@ k_offsets(OffsetSource src, uint32_t n, unsigned long long* __restrict__ off,
         if (lane >= o) x += y;
     }
     if (lane == 31) warp_sum[warp] = x;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) pre_part += __shfl_xor_sync(0xffffffffu, pre_part, o);
+    if (lane == 0) agg_sum[warp] = pre_part;
     __syncthreads();
     unsigned long long wexcl = 0, total = 0;
 #pragma unroll
@@ -313,7 +349,15 @@ k_offsets(OffsetSource src, uint32_t n, unsigned long long* __restrict__ off,
         if (w < warp) wexcl += t;
         total += t;
     }
-    if (warp == 0) {
+    if (src.agg) {
+        if (tid == 0) {
+            unsigned long long pre = 0;
+#pragma unroll
+            for (int w = 0; w < OFF_BLOCK / 32; ++w) pre += agg_sum[w];
+            tile_prefix = pre;
+            if (src.agg[tile] != total) raise_error(st, DDM_ERR_INTERNAL, 4);
+        }
+    } else if (warp == 0) {
         unsigned long long* word = status + tile;
         if (lane == 0) st_release_u64(word, (tile == 0 ? LB64_INC : LB64_AGG) | total);
         unsigned long long pre = tile == 0 ? 0ull : warp_lookback_u64(status, tile, st, 5);
@@ -333,7 +377,19 @@ k_offsets(OffsetSource src, uint32_t n, unsigned long long* __restrict__ off,
 #pragma unroll
     for (int k = 0; k < OFF_ITEMS; ++k) {
         const int i = k * OFF_BLOCK + tid;
-        if (tbase + i < n) off[tbase + i] = s_out[pad32(i)];
+        if (tbase + i < n) {
+            const unsigned long long o = s_out[pad32(i)];
+            off[tbase + i] = o;
+            if (src.srank) {
+                if (rk[k] < n) {
+                    src.srank[rk[k]] = make_uint4((uint32_t)(tbase + i), pl[k], ph[k],
+                                                  s_in[pad32(i)]);
+                    src.soff[rk[k]] = o;
+                } else {
+                    raise_error(st, DDM_ERR_INTERNAL, 4);
+                }
+            }
+        }
     }
     // The thread holding the last element also writes off[n] and the total.
     const uint64_t mybase = tbase + (uint64_t)tid * OFF_ITEMS;
@@ -360,7 +416,8 @@ int launch_offsets(const uint32_t* cnt, int64_t n, unsigned long long* off, uint
 
 int launch_rank_offsets(const Records& rec, int64_t n, uint32_t* cnt, unsigned long long* off,
                         uint64_t cap, unsigned long long* total, unsigned long long* status,
-                        DevStatus* st, cudaStream_t s) {
+                        DevStatus* st, cudaStream_t s, const unsigned long long* cnt_agg,
+                        uint4* srank, unsigned long long* soff) {
     if (n == 0) return 0;
     const uint64_t tiles = ceil_div((uint64_t)n, OFF_TILE);
     uint32_t* counter = reinterpret_cast<uint32_t*>(status + tiles);
@@ -369,6 +426,9 @@ int launch_rank_offsets(const Records& rec, int64_t n, uint32_t* cnt, unsigned l
     src.lo = rec.s_lo;
     src.hi = rec.s_hi;
     src.cnt_out = cnt;
+    src.agg = tiles <= CNT_AGG_MAX_TILES ? cnt_agg : nullptr;
+    src.srank = srank;
+    src.soff = srank ? soff : nullptr;
     launch_k(k_offsets, (unsigned)tiles, OFF_BLOCK, 0, s, src, (uint32_t)n, off, cap, total, status,
              counter, st);
     return 1;

@@ -139,6 +139,39 @@ __global__ void k_tile_active(EmitArgs a, DevStatus* st, unsigned gu) {
     }
 }
 
+// Window path, the same for the updates in id order (no gather by rank): U_j's
+// records give its positions and the rank r of its lower endpoint (w field),
+// so urank[r] = {j, pos(lo), pos(hi), 0} is scattered, and U_j is added to the
+// boundary list of every window boundary it spans, one atomic per list entry
+// (about a fifth of the updates span one at the usual densities).  The
+// subscriptions' rank tables come from the offsets scan (launch_rank_offsets).
+__global__ void __launch_bounds__(256) k_upd_ranks(EmitArgs a, DevStatus* st) {
+    pdl_begin();
+    if (read_error(st)) return;
+    const int S = a.win_shift;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < a.m; j += stride) {
+        const uint4 lo = a.rec.u_lo[j];
+        const uint32_t ph = a.rec.u_hi[j].x, pl = lo.x, r = lo.w;
+        if (r >= a.m) {
+            raise_error(st, DDM_ERR_INTERNAL, 10);
+            continue;
+        }
+        a.urank[r] = make_uint4((uint32_t)j, pl, ph, 0u);
+        const uint32_t whi = min(ph >> S, a.num_win - 1);
+        for (uint32_t w = (pl >> S) + 1; w <= whi; ++w) {
+            const uint4 t = a.windows[w];
+            const uint32_t sz = t.y - t.z;
+            if (!list_fits(a, w, sz)) continue;
+            const uint32_t slot = atomicAdd(&a.lw_fill[w], 1u);
+            if (slot < sz)
+                a.lw[list_base(a, w) + slot] = make_uint4((uint32_t)j, ph, r, 0u);
+            else
+                raise_error(st, DDM_ERR_INTERNAL, 10);
+        }
+    }
+}
+
 // One subscription of the filter: its relative bounds, output id, id base
 // and next free slot of its segment.
 struct FilterSub {
@@ -487,6 +520,12 @@ int launch_tile_active(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
     const unsigned gs = a.srank && a.n ? grid_for((uint64_t)a.n, 512, 152 * 8) : 0u;
     if (gu + gs == 0) return 0;
     launch_k(k_tile_active, gu + gs, 256, 0, s, a, st, gu);
+    return 1;
+}
+
+int launch_upd_ranks(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
+    if (a.num_win == 0 || a.m == 0) return 0;
+    launch_k(k_upd_ranks, grid_for((uint64_t)a.m, 256, 152 * 8), 256, 0, s, a, st);
     return 1;
 }
 

@@ -42,10 +42,16 @@ struct Records {
 // the tile aggregates that launch_radix_sort's last pass formed (4 u32 per
 // SCAN_TILE positions); with them, and at most SCAN_KINDS_MAX_TILES tiles, the
 // tiles take their prefixes from the aggregates and the status words go unused.
+// cnt_agg (may be NULL; ceil(n / OFF_TILE) u64, zeroed): the scan also adds up,
+// per OFF_TILE subscription ids, the counts B_i - C_i of launch_rank_offsets
+// (each block in shared memory, then one atomic per id tile), so that the
+// offsets scan needs no look-back.  Used only with at most CNT_AGG_MAX_TILES
+// id tiles; the caller passes the same pointer to launch_rank_offsets.
 constexpr uint64_t SCAN_KINDS_MAX_TILES = 4096;
+constexpr uint64_t CNT_AGG_MAX_TILES = 2048;
 int launch_sweep_scan(const uint32_t* vals, uint64_t E, int64_t n, int64_t m, const Records& rec,
                        unsigned long long* status, DevStatus* st, cudaStream_t s,
-                       const uint32_t* kinds = nullptr);
+                       const uint32_t* kinds = nullptr, unsigned long long* cnt_agg = nullptr);
 
 // cnt[i] = B_i - C_i; optional upd_cnt[j] = B_j - C_j.
 int launch_rank_count(const Records& rec, int64_t n, int64_t m, uint32_t* cnt,
@@ -60,9 +66,16 @@ int launch_offsets(const uint32_t* cnt, int64_t n, unsigned long long* off, uint
 
 // a4 + a5 in one kernel: cnt[i] = B_i - C_i of the subscriptions' records and
 // off[] / *total as launch_offsets gives for those counts.  Same status words.
+// cnt_agg: the per-id-tile sums from launch_sweep_scan (or NULL): each tile
+// then takes its prefix from them instead of looking back.  srank / soff (or
+// NULL): the window emission's subscription rank tables, n entries each,
+// srank[r] = {i, pos(S_i.lo), pos(S_i.hi), cnt[i]} and soff[r] = off[i] with r
+// the rank of S_i's lower endpoint among the subscriptions' lower endpoints.
 int launch_rank_offsets(const Records& rec, int64_t n, uint32_t* cnt, unsigned long long* off,
                         uint64_t cap, unsigned long long* total, unsigned long long* status,
-                        DevStatus* st, cudaStream_t s);
+                        DevStatus* st, cudaStream_t s,
+                        const unsigned long long* cnt_agg = nullptr, uint4* srank = nullptr,
+                        unsigned long long* soff = nullptr);
 
 // Offsets of the boundary lists: value of window w = windows[w].y - windows[w].z
 // (updates active at the window boundary), or 0 when that exceeds lcap.
