@@ -24,6 +24,10 @@ namespace ddm {
 thread_local bool g_pdl = false;
 int launch_wait_selftest(int which, uint32_t limit, unsigned long long* status, DevStatus* st,
                          cudaStream_t s);
+// k_status.cu: a call's zero fill (status and zeroed workspace) and the status
+// copy into the mapped host mirror.
+int launch_prologue(DevStatus* st, void* zero, uint64_t zero_bytes, cudaStream_t s);
+int launch_publish(const DevStatus* st, DevStatus* host_mapped, cudaStream_t s);
 }
 
 struct ddm_ctx {
@@ -36,6 +40,7 @@ struct ddm_ctx {
     size_t ws_size = 0;
     DevStatus* dstat = nullptr;  // device
     DevStatus* hstat = nullptr;  // pinned host mirror
+    DevStatus* hstat_dev = nullptr;  // its device address when mapped (else NULL: copy)
     // host-buffer entry point staging (inputs, outputs)
     char* io = nullptr;
     size_t io_size = 0;
@@ -367,12 +372,11 @@ int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
     PdlScope pdl_scope(c->pdl);
     const bool batch = job.num_inst > 0;
     const bool do_prefix = phase != Phase::Suffix, do_suffix = phase != Phase::Prefix;
+    uint64_t& L = c->stats.launches;
     if (do_prefix) {
-        CK(cudaMemsetAsync(c->dstat, 0, sizeof(DevStatus), s));
-        CK(cudaMemsetAsync(c->ws, 0, pl.zero_bytes, s));
+        L += launch_prologue(c->dstat, c->ws, pl.zero_bytes, s);
         c->stats.calls++;
     }
-    uint64_t& L = c->stats.launches;
 
     // Coordinates of every dimension as device arrays over the job's ids.
     DimPtrs dims{};
@@ -580,7 +584,14 @@ int enqueue_plain(ddm_ctx* c, const ddm_regions* r, Mode mode, int32_t* pairs, u
 
 // Reads the device status and maps it to a return code.
 int finish(ddm_ctx* c, uint64_t* K_out) {
-    CK(cudaMemcpyAsync(c->hstat, c->dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost, c->stream));
+    if (c->hstat_dev) {
+        PdlScope pdl_scope(c->pdl);
+        c->stats.launches += launch_publish(c->dstat, c->hstat_dev, c->stream);
+        CK(cudaGetLastError());
+    } else {
+        CK(cudaMemcpyAsync(c->hstat, c->dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost,
+                           c->stream));
+    }
     CK(cudaStreamSynchronize(c->stream));
     if (c->prof) {
         for (int k = 0; k < DDM_STAGES; ++k) {
@@ -631,12 +642,28 @@ int ddm_create(ddm_ctx** out, int device, void* cuda_stream, size_t mem_budget_b
     c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
     c->budget = mem_budget_bytes;
     DeviceGuard g(device);
-    if (cudaMalloc(&c->dstat, sizeof(DevStatus)) != cudaSuccess ||
-        cudaMallocHost(&c->hstat, sizeof(DevStatus)) != cudaSuccess) {
+    // The host mirror of the status is mapped pinned memory, which a kernel
+    // writes directly (else plain pinned memory and a copy).
+    if (cudaMalloc(&c->dstat, sizeof(DevStatus)) != cudaSuccess) {
         cudaGetLastError();
-        if (c->dstat) cudaFree(c->dstat);
         delete c;
         return DDM_ERR_NOMEM;
+    }
+    if (cudaHostAlloc(&c->hstat, sizeof(DevStatus), cudaHostAllocMapped) == cudaSuccess) {
+        if (cudaHostGetDevicePointer(reinterpret_cast<void**>(&c->hstat_dev), c->hstat, 0) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            c->hstat_dev = nullptr;
+        }
+    } else {
+        cudaGetLastError();
+        c->hstat = nullptr;
+        if (cudaMallocHost(&c->hstat, sizeof(DevStatus)) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(c->dstat);
+            delete c;
+            return DDM_ERR_NOMEM;
+        }
     }
     memset(c->hstat, 0, sizeof(DevStatus));
     *out = c;
