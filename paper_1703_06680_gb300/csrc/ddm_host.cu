@@ -236,8 +236,7 @@ struct Plan {
     unsigned long long* lw_off;
     uint4* lw;
     uint4* urank;
-    uint4* srank;
-    unsigned long long* soff;
+    SubRank* srank;
     unsigned long long lw_cap;
     uint8_t* flag;
     // the rest
@@ -306,8 +305,7 @@ struct Plan {
         wcand = cv.take<uint2>(cand_cap);
         wmeta = cv.take<uint4>(window ? num_win : 0);
         urank = cv.take<uint4>(lists ? m : 0);
-        srank = cv.take<uint4>(window ? n : 0);
-        soff = cv.take<unsigned long long>(window ? n : 0);
+        srank = cv.take<SubRank>(window ? n : 0);
         flag = cv.take<uint8_t>(lists ? n : 0);
         sort.tile_hist = cv.take<uint32_t>(stiles * RADIX);
         sort.offs = cv.take<unsigned long long>(stiles * RADIX + 1);
@@ -426,6 +424,9 @@ int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
     }
     uint32_t* vals_sorted = (pl.passes & 1) ? pl.vals1 : pl.vals0;
     Records rec = pl.rec;
+    // Window path: the emission's rank tables replace the order arrays (the
+    // range path reads ids by rank from them), so the sweep does not write them.
+    if (pl.window) rec.sub_order = rec.upd_order = nullptr;
     if (pl.window || pl.join) {
         rec.windows = pl.windows;
         rec.win_shift = pl.win_shift;
@@ -462,7 +463,6 @@ int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
         a.lw = pl.lw;
         a.urank = pl.urank;
         a.srank = pl.window ? pl.srank : nullptr;
-        a.soff = pl.soff;
         a.wmeta = pl.window ? pl.wmeta : nullptr;
         a.wcand = pl.window ? pl.wcand : nullptr;
         a.cand_fill = pl.cand_fill;
@@ -495,7 +495,7 @@ int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
     // tables start 256-byte aligned and the next buffer starts 256-byte
     // aligned too, so rounding up to 16-byte words stays inside them.
     const size_t rec_words =
-        ((size_t)((char*)(rec.upd_order + pl.m) - (char*)rec.s_lo) + 15) / 16;
+        ((size_t)((char*)(pl.rec.upd_order + pl.m) - (char*)pl.rec.s_lo) + 15) / 16;
     // The sweep's tile aggregates (S lowers, U lowers, S uppers per SCAN_TILE
     // positions) are counted by the sort's last pass, which knows every output
     // position, into the scan status words (zeroed above, 24 bytes per tile
@@ -547,7 +547,7 @@ int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
     // here (subscriptions by the offsets scan, updates by launch_upd_ranks).
     if (fused_counts) {
         L += launch_rank_offsets(rec, pl.n, pl.cnt, pl.off, off_cap, &c->dstat->K, pl.off_status,
-                                 c->dstat, s, cnt_agg, pl.window ? pl.srank : nullptr, pl.soff);
+                                 c->dstat, s, cnt_agg, pl.window ? pl.srank : nullptr);
         if (pl.window) L += launch_upd_ranks(a, c->dstat, s);
     } else
         L += launch_offsets(pl.cnt, pl.n, pl.off, off_cap, &c->dstat->K, pl.off_status, c->dstat, s);

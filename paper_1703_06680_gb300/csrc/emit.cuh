@@ -50,8 +50,7 @@ struct EmitArgs {
     uint4* lw;                      // list storage {id, pos(U.hi), rank, 0}, lw_cap entries
     uint32_t lcap;                  // longest boundary list a window may use
     uint4* urank;                   // {id, pos(lo), pos(hi), 0} by lower-endpoint rank, m
-    uint4* srank;                   // window path: {id, pos(lo), pos(hi), cnt} by rank, n (or NULL)
-    unsigned long long* soff;       // window path: segment offset by rank, n
+    SubRank* srank;                 // window path: subscriptions by rank, n (or NULL)
     uint4* wmeta;                   // window path: {r0, ns, |W|, first wcand entry} per window
                                     // (ns = 0: skip), numWin
     uint2* wcand;                   // window path: id-sorted packed candidates, cand_cap entries
@@ -85,7 +84,7 @@ int launch_surv_compact(const unsigned long long* surv, const unsigned long long
 // Window path for d = 1.
 int launch_tile_active(const EmitArgs& a, DevStatus* st, cudaStream_t s);
 // Window path (fixed-slot lists): urank and the boundary lists from the
-// updates' records in id order; srank / soff come from launch_rank_offsets.
+// updates' records in id order; srank comes from launch_rank_offsets.
 int launch_upd_ranks(const EmitArgs& a, DevStatus* st, cudaStream_t s);
 int launch_win_setup(const EmitArgs& a, DevStatus* st, cudaStream_t s);
 int launch_emit_window(const EmitArgs& a, DevStatus* st, cudaStream_t s);

@@ -27,6 +27,16 @@ constexpr int WARP_SORT_MAX = 512;
 constexpr int BIG_BLOCK = 256;
 constexpr int BIG_ITEMS = 4;
 
+// Id of the update / subscription whose lower endpoint has rank r in its set:
+// from the window path's rank tables when they exist (the sweep then writes
+// no order arrays), else from the order arrays.
+__device__ __forceinline__ uint32_t upd_at_rank(const EmitArgs& a, uint64_t r) {
+    return a.srank ? a.urank[r].x : a.rec.upd_order[r];
+}
+__device__ __forceinline__ uint32_t sub_at_rank(const EmitArgs& a, uint64_t r) {
+    return a.srank ? a.srank[r].e.x : a.rec.sub_order[r];
+}
+
 // ---------------------------------------------------------------------------
 // a7 set-up: keys of dims 1..d-1 in rank order, with validation.
 // ---------------------------------------------------------------------------
@@ -128,7 +138,7 @@ __device__ __forceinline__ void class_a_body(const EmitArgs& a, DevStatus* st, u
             if (FILTER && pass) pass = pass_filter(a, o, a.updK, a.m, k);
             const unsigned bal = __ballot_sync(0xffffffffu, pass);
             if (WRITE && pass) {
-                const int32_t j = (int32_t)a.rec.upd_order[k] - sub_off_j;
+                const int32_t j = (int32_t)upd_at_rank(a, k) - sub_off_j;
                 put_pair(a, base + running + __popc(bal & lt), out_i, j, st);
             }
             running += __popc(bal);
@@ -167,7 +177,7 @@ __device__ __forceinline__ void class_b_body(const EmitArgs& a, DevStatus* st, u
         }
         for (uint32_t r = A + lane; r < B; r += 32) {
             if (FILTER && !pass_filter(a, o, a.subK, a.n, r)) continue;
-            const uint32_t i = a.rec.sub_order[r];
+            const uint32_t i = sub_at_rank(a, r);
             if (a.flag && !a.flag[i]) continue;
             if (!WRITE) {
                 atomicAdd(&a.cnt[i], 1u);

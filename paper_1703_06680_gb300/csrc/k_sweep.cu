@@ -159,7 +159,8 @@ k_sweep_scan(const uint32_t* __restrict__ vals, uint32_t E, uint32_t n, uint32_t
                       is_upper ? (unsigned long long)y : 0ull - (unsigned long long)z);
         if (!is_upper) {
             const uint32_t r = is_upd ? cUlo : cSlo;
-            if (r < (is_upd ? m : n)) (is_upd ? rec.upd_order : rec.sub_order)[r] = id;
+            if (rec.sub_order && r < (is_upd ? m : n))
+                (is_upd ? rec.upd_order : rec.sub_order)[r] = id;
         }
         cSlo += kind == KIND_SLO;
         cUlo += kind == KIND_ULO;
@@ -251,11 +252,10 @@ struct OffsetSource {
     const uint4* windows;
     uint32_t lcap;
     const unsigned long long* agg;  // kind 1: per-tile sums of the counts, or NULL
-    // kind 1, window emission (or NULL): the subscriptions' rank tables
-    // srank[r] = {i, pos(lo), pos(hi), cnt} and soff[r] = off[i], r = the rank of
-    // S_i's lower endpoint (its record's w field), scattered from id order.
-    uint4* srank;
-    unsigned long long* soff;
+    // kind 1, window emission (or NULL): the subscriptions' rank table, entry
+    // r = the rank of S_i's lower endpoint (its record's w field), scattered
+    // from id order.
+    SubRank* srank;
 };
 
 // Kinds 0 and 2 (kind 1 is read inside k_offsets).
@@ -382,9 +382,11 @@ k_offsets(OffsetSource src, uint32_t n, unsigned long long* __restrict__ off,
             off[tbase + i] = o;
             if (src.srank) {
                 if (rk[k] < n) {
-                    src.srank[rk[k]] = make_uint4((uint32_t)(tbase + i), pl[k], ph[k],
-                                                  s_in[pad32(i)]);
-                    src.soff[rk[k]] = o;
+                    SubRank e;
+                    e.e = make_uint4((uint32_t)(tbase + i), pl[k], ph[k], s_in[pad32(i)]);
+                    e.off = o;
+                    e.pad = 0ull;
+                    src.srank[rk[k]] = e;
                 } else {
                     raise_error(st, DDM_ERR_INTERNAL, 4);
                 }
@@ -417,7 +419,7 @@ int launch_offsets(const uint32_t* cnt, int64_t n, unsigned long long* off, uint
 int launch_rank_offsets(const Records& rec, int64_t n, uint32_t* cnt, unsigned long long* off,
                         uint64_t cap, unsigned long long* total, unsigned long long* status,
                         DevStatus* st, cudaStream_t s, const unsigned long long* cnt_agg,
-                        uint4* srank, unsigned long long* soff) {
+                        SubRank* srank) {
     if (n == 0) return 0;
     const uint64_t tiles = ceil_div((uint64_t)n, OFF_TILE);
     uint32_t* counter = reinterpret_cast<uint32_t*>(status + tiles);
@@ -428,7 +430,6 @@ int launch_rank_offsets(const Records& rec, int64_t n, uint32_t* cnt, unsigned l
     src.cnt_out = cnt;
     src.agg = tiles <= CNT_AGG_MAX_TILES ? cnt_agg : nullptr;
     src.srank = srank;
-    src.soff = srank ? soff : nullptr;
     launch_k(k_offsets, (unsigned)tiles, OFF_BLOCK, 0, s, src, (uint32_t)n, off, cap, total, status,
              counter, st);
     return 1;

@@ -60,49 +60,25 @@ __device__ __forceinline__ bool list_fits(const EmitArgs& a, uint32_t w, uint32_
     return s <= a.lcap && list_base(a, w) + s <= a.lw_cap;
 }
 
-// One pass over the updates in lower-endpoint order (rank r, id = upd_order[r]):
+// Tiled join (d > 1): one pass over the updates in lower-endpoint order (rank
+// r, id = upd_order[r]):
 //  - the rank table urank[r] = {id, pos(lo), pos(hi)}, so that windows read
-//    their candidates contiguously (and, on the window path, the same for the
-//    subscriptions: srank[r] = {id, pos(lo), pos(hi), cnt}, soff[r] = off);
+//    their candidates contiguously;
 //  - the boundary lists: U contributes {id, pos(U.hi), rank} to every boundary w*T
 //    with pos(U.lo) < w*T <= pos(U.hi) (the paper's UpdSet at that boundary).
 // The lanes of a warp hold consecutive ranks, whose lower endpoints are close
 // in the stream, so they mostly cross the same boundaries: the warp walks the
 // union of its lanes' boundary ranges and reserves the slots of all lanes
 // crossing boundary w with one atomic (order inside a list is irrelevant: the
-// window kernel sorts its candidates by id).
-// Blocks [0, gu) take the updates, blocks [gu, gridDim.x) the subscriptions.
-__global__ void k_tile_active(EmitArgs a, DevStatus* st, unsigned gu) {
+// join sorts its candidates by id).  The window path of d = 1 builds the same
+// tables from id order instead (k_upd_ranks, launch_rank_offsets).
+__global__ void k_tile_active(EmitArgs a, DevStatus* st) {
     pdl_begin();
     if (read_error(st)) return;
-    if (blockIdx.x >= gu) {
-        // Window path: the subscriptions in lower-endpoint order with what the
-        // emission needs of each, so that a window reads its own contiguously.
-        const int64_t sstride = (int64_t)(gridDim.x - gu) * blockDim.x;
-        // Two subscriptions per thread and iteration: all gathers in flight together.
-        for (int64_t r = (int64_t)(blockIdx.x - gu) * blockDim.x + threadIdx.x; r < a.n;
-             r += 2 * sstride) {
-            const int64_t r2 = r + sstride;
-            const bool two = r2 < a.n;
-            const uint32_t i = a.rec.sub_order[r];
-            const uint32_t i2 = two ? a.rec.sub_order[r2] : i;
-            const uint32_t pl = a.rec.s_lo[i].x, ph = a.rec.s_hi[i].x, c = a.cnt[i];
-            const unsigned long long o = a.off[i];
-            const uint32_t pl2 = a.rec.s_lo[i2].x, ph2 = a.rec.s_hi[i2].x, c2 = a.cnt[i2];
-            const unsigned long long o2 = a.off[i2];
-            a.srank[r] = make_uint4(i, pl, ph, c);
-            a.soff[r] = o;
-            if (two) {
-                a.srank[r2] = make_uint4(i2, pl2, ph2, c2);
-                a.soff[r2] = o2;
-            }
-        }
-        return;
-    }
     const int S = a.win_shift;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    const int64_t stride = (int64_t)gu * blockDim.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t r0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); r0 < a.m;
          r0 += stride) {
         const int64_t r = r0 + lane;
@@ -280,7 +256,7 @@ __global__ void __launch_bounds__(WIN_BLOCK) k_win_setup(EmitArgs a, DevStatus* 
     {
         uint32_t pm = 0, nlong = 0;
         for (uint32_t k = tid; k < ns; k += WIN_BLOCK) {
-            const uint4 e = a.srank[r0 + k];
+            const uint4 e = a.srank[r0 + k].e;
             const bool lng = e.z - e.y > LONG_SPAN;
             a.flag[e.x] = lng ? 1 : 0;
             nlong += lng;
@@ -345,7 +321,7 @@ __global__ void __launch_bounds__(WIN_BLOCK) k_win_setup(EmitArgs a, DevStatus* 
         // The whole window goes to the range path.
         uint32_t nreg = 0;
         for (uint32_t k = tid; k < ns; k += WIN_BLOCK) {
-            const uint4 e = a.srank[r0 + k];
+            const uint4 e = a.srank[r0 + k].e;
             if (e.z - e.y <= LONG_SPAN) { a.flag[e.x] = 1; ++nreg; }
         }
         nreg = __reduce_add_sync(0xffffffffu, nreg);
@@ -421,7 +397,11 @@ __global__ void __launch_bounds__(WIN_BLOCK, 4) k_emit_window(EmitArgs a, DevSta
     const uint2* const gcand = a.wcand + md.w;
     uint4 e_first = make_uint4(0u, 0u, 0u, 0u);
     unsigned long long off_first = 0;
-    if ((uint32_t)tid < ns) { e_first = a.srank[r0 + tid]; off_first = a.soff[r0 + tid]; }
+    if ((uint32_t)tid < ns) {
+        const SubRank q = a.srank[r0 + tid];
+        e_first = q.e;
+        off_first = q.off;
+    }
     for (uint32_t k = tid; k < W; k += blockDim.x) cand[k] = __ldg(gcand + k);
     __syncthreads();
 
@@ -435,7 +415,11 @@ __global__ void __launch_bounds__(WIN_BLOCK, 4) k_emit_window(EmitArgs a, DevSta
         uint4 e = make_uint4(0u, 0u, 0u, 0u);
         unsigned long long off = 0;
         if (g == (uint32_t)warp) { e = e_first; off = off_first; }  // zero when k >= ns
-        else if (k < ns) { e = a.srank[r0 + k]; off = a.soff[r0 + k]; }
+        else if (k < ns) {
+            const SubRank q = a.srank[r0 + k];
+            e = q.e;
+            off = q.off;
+        }
         const bool reg = k < ns && e.z - e.y <= LONG_SPAN;
         // Relative bounds; an idle lane tests [0xffff, 0]: lo < 0 never holds.
         const uint32_t pl = reg ? e.y - wT : REL_MAX, ph = reg ? e.z - wT : 0u;
@@ -516,10 +500,8 @@ static unsigned grid_for(uint64_t items, unsigned per_block, unsigned cap) {
 
 int launch_tile_active(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
     if (a.num_win == 0) return 0;
-    const unsigned gu = a.m ? grid_for((uint64_t)a.m, 256, 152 * 16) : 0u;
-    const unsigned gs = a.srank && a.n ? grid_for((uint64_t)a.n, 512, 152 * 8) : 0u;
-    if (gu + gs == 0) return 0;
-    launch_k(k_tile_active, gu + gs, 256, 0, s, a, st, gu);
+    if (a.m == 0) return 0;
+    launch_k(k_tile_active, grid_for((uint64_t)a.m, 256, 152 * 16), 256, 0, s, a, st);
     return 1;
 }
 

@@ -32,7 +32,7 @@ struct Records {
     uint4* s_hi;
     uint4* u_lo;
     uint4* u_hi;
-    uint32_t *sub_order, *upd_order;
+    uint32_t *sub_order, *upd_order;  // ids by lower-endpoint rank (NULL: not written)
     uint4* windows;       // (cSlo, cUlo, cUhi, p) at p = w << win_shift, or NULL
     int win_shift;
     uint32_t *dbg_who, *dbg_subset, *dbg_updset;  // optional diagnostics (may be NULL)
@@ -66,16 +66,22 @@ int launch_offsets(const uint32_t* cnt, int64_t n, unsigned long long* off, uint
 
 // a4 + a5 in one kernel: cnt[i] = B_i - C_i of the subscriptions' records and
 // off[] / *total as launch_offsets gives for those counts.  Same status words.
+// One subscription of the window emission, by the rank r of its lower
+// endpoint among the subscriptions' lower endpoints: e = {i, pos(S_i.lo),
+// pos(S_i.hi), cnt[i]} and off = off[i].  32 bytes: one sector per store.
+struct SubRank {
+    uint4 e;
+    unsigned long long off, pad;
+};
+
 // cnt_agg: the per-id-tile sums from launch_sweep_scan (or NULL): each tile
-// then takes its prefix from them instead of looking back.  srank / soff (or
-// NULL): the window emission's subscription rank tables, n entries each,
-// srank[r] = {i, pos(S_i.lo), pos(S_i.hi), cnt[i]} and soff[r] = off[i] with r
-// the rank of S_i's lower endpoint among the subscriptions' lower endpoints.
+// then takes its prefix from them instead of looking back.  srank (or NULL):
+// the window emission's subscription rank table (n entries), scattered from
+// id order.
 int launch_rank_offsets(const Records& rec, int64_t n, uint32_t* cnt, unsigned long long* off,
                         uint64_t cap, unsigned long long* total, unsigned long long* status,
                         DevStatus* st, cudaStream_t s,
-                        const unsigned long long* cnt_agg = nullptr, uint4* srank = nullptr,
-                        unsigned long long* soff = nullptr);
+                        const unsigned long long* cnt_agg = nullptr, SubRank* srank = nullptr);
 
 // Offsets of the boundary lists: value of window w = windows[w].y - windows[w].z
 // (updates active at the window boundary), or 0 when that exceeds lcap.
