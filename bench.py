@@ -55,6 +55,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--incremental-only", action="store_true",
+                    help="only the session change-report section (a profiling case)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
 
@@ -463,6 +465,9 @@ def run_ours(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.incremental_only:
+        print(json.dumps({"incremental": bench_incremental(args, dev)}), flush=True)
+        return
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
 

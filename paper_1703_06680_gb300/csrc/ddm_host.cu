@@ -519,8 +519,10 @@ int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
     const bool fused_counts = job.d == 1 && !dbg;
     unsigned long long* cnt_agg = fused_counts ? pl.off_status : nullptr;
     mark(c, 2);
-    L += launch_sweep_scan(vals_sorted, pl.E, pl.n, pl.m, rec, pl.scan_status, c->dstat, s, kinds,
-                           cnt_agg);
+    const int lsw = launch_sweep_scan(vals_sorted, pl.E, pl.n, pl.m, rec, pl.scan_status,
+                                      c->dstat, s, kinds, cnt_agg);
+    if (lsw < 0) return fail(c, DDM_ERR_INTERNAL, "sweep launch configuration");
+    L += lsw;
     mark(c, 3);
     if (job.d == 1) {
         if (!fused_counts)

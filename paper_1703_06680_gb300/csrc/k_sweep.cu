@@ -29,11 +29,60 @@ __device__ __forceinline__ unsigned long long kind_inc(uint32_t kind) {
                                    : kind == KIND_SHI ? (1ull << 42) : 0ull;
 }
 
+// One thread's walk over its SCAN_ITEMS endpoints with exact exclusive counts:
+// the rank records, the order arrays, the per-id-tile count sums and (DBG) the
+// diagnostics.  FULL: every item lies before E, so there is no end test.
+template <bool FULL, bool DBG>
+__device__ __forceinline__ void sweep_walk(const uint32_t (&v)[SCAN_ITEMS], uint64_t base,
+                                           uint32_t E, uint32_t n, uint32_t m,
+                                           const Records& rec, unsigned long long* s_agg,
+                                           bool agg, uint32_t& cSlo, uint32_t& cUlo,
+                                           uint32_t& cShi, DevStatus* st) {
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        const uint64_t p64 = base + k;
+        if (!FULL && p64 >= E) break;
+        const uint32_t p = (uint32_t)p64;
+        const uint32_t kind = v[k] >> 30, id = v[k] & ID_MASK;
+        const uint32_t cUhi = p - cSlo - cUlo - cShi;
+        // Guard: a payload or rank out of range means an upstream fault; skip it.
+        if (id >= ((kind & 1u) ? m : n) || cSlo > n || cUlo > m) {
+            raise_error(st, DDM_ERR_INTERNAL, 3);
+            continue;
+        }
+        // One record store per endpoint, address and value selected by kind.
+        const bool is_upd = kind & 1u, is_upper = kind >> 1;
+        uint4* const tab =
+            is_upper ? (is_upd ? rec.u_hi : rec.s_hi) : (is_upd ? rec.u_lo : rec.s_lo);
+        const uint32_t y = is_upd ? cSlo : cUlo;  // lower endpoints seen of the other set
+        const uint32_t z = is_upper ? 0u : (is_upd ? cShi : cUhi);
+        const uint32_t w = is_upper ? 0u : (is_upd ? cUlo : cSlo);
+        tab[id] = make_uint4(p, y, z, w);
+        // B_i at S_i's upper endpoint, -C_i at its lower one (mod 2^64).
+        if (agg && !is_upd)
+            atomicAdd(&s_agg[id / OFF_TILE],
+                      is_upper ? (unsigned long long)y : 0ull - (unsigned long long)z);
+        if (!is_upper && rec.sub_order && w < (is_upd ? m : n))
+            (is_upd ? rec.upd_order : rec.sub_order)[w] = id;
+        cSlo += kind == KIND_SLO;
+        cUlo += kind == KIND_ULO;
+        cShi += kind == KIND_SHI;
+        if (DBG) {
+            const uint32_t cUhi_after = p + 1 - cSlo - cUlo - cShi;
+            rec.dbg_who[p] = v[k];
+            rec.dbg_subset[p] = cSlo - cShi;
+            rec.dbg_updset[p] = cUlo - cUhi_after;
+        }
+    }
+}
+
 // Two ways to the counts before a tile.  With `kinds` (the tile aggregates that
 // the sort's last pass formed), the block sums the aggregates of all earlier
 // tiles itself; no tile waits for another.  Without, each tile publishes its
 // aggregate and looks back (decoupled look-back, tiles numbered in start order).
 // At most 64 registers: four blocks per SM keep every tile of 2e6 endpoints resident.
+// DBG: also the per-position diagnostics.
+template <bool DBG>
 __global__ void __launch_bounds__(SCAN_BLOCK, 4)
 k_sweep_scan(const uint32_t* __restrict__ vals, uint32_t E, uint32_t n, uint32_t m,
              Records rec, unsigned long long* __restrict__ status,
@@ -131,50 +180,20 @@ k_sweep_scan(const uint32_t* __restrict__ vals, uint32_t E, uint32_t n, uint32_t
     uint32_t cSlo = (uint32_t)(tile_prefix[0] + (excl & ((1ull << 21) - 1)));
     uint32_t cUlo = (uint32_t)(tile_prefix[1] + ((excl >> 21) & ((1ull << 21) - 1)));
     uint32_t cShi = (uint32_t)(tile_prefix[2] + ((excl >> 42) & ((1ull << 21) - 1)));
-#pragma unroll
-    for (int k = 0; k < SCAN_ITEMS; ++k) {
-        const uint64_t p64 = base + k;
-        if (p64 >= E) break;
-        const uint32_t p = (uint32_t)p64;
-        const uint32_t kind = v[k] >> 30, id = v[k] & ID_MASK;
-        const uint32_t cUhi = p - cSlo - cUlo - cShi;
-        // Guard: a payload or rank out of range means an upstream fault; skip it.
-        if (id >= ((kind & 1u) ? m : n) || cSlo > n || cUlo > m) {
-            raise_error(st, DDM_ERR_INTERNAL, 3);
-            continue;
-        }
-        if (rec.windows && (p & ((1u << rec.win_shift) - 1)) == 0)
-            rec.windows[p >> rec.win_shift] = make_uint4(cSlo, cUlo, cUhi, p);
-        // One record store per endpoint, address and value selected by kind.
-        const bool is_upd = kind & 1u, is_upper = kind >> 1;
-        uint4* const tab = is_upper ? (is_upd ? rec.u_hi : rec.s_hi) : (is_upd ? rec.u_lo : rec.s_lo);
-        const uint32_t own = is_upd ? cSlo : cUlo;  // lower endpoints seen of the other set
-        const uint32_t y = own;
-        const uint32_t z = is_upper ? 0u : (is_upd ? cShi : cUhi);
-        const uint32_t w = is_upper ? 0u : (is_upd ? cUlo : cSlo);
-        tab[id] = make_uint4(p, y, z, w);
-        // B_i at S_i's upper endpoint, -C_i at its lower one (mod 2^64).
-        if (cnt_agg && !is_upd)
-            atomicAdd(&s_agg[id / OFF_TILE],
-                      is_upper ? (unsigned long long)y : 0ull - (unsigned long long)z);
-        if (!is_upper) {
-            const uint32_t r = is_upd ? cUlo : cSlo;
-            if (rec.sub_order && r < (is_upd ? m : n))
-                (is_upd ? rec.upd_order : rec.sub_order)[r] = id;
-        }
-        cSlo += kind == KIND_SLO;
-        cUlo += kind == KIND_ULO;
-        cShi += kind == KIND_SHI;
-        if (rec.windows && p + 1 == E)  // closing entry at position E
-            rec.windows[(E + (1u << rec.win_shift) - 1) >> rec.win_shift] =
-                make_uint4(cSlo, cUlo, E - cSlo - cUlo - cShi, E);
-        if (rec.dbg_who) {
-            const uint32_t cUhi_after = p + 1 - cSlo - cUlo - cShi;
-            rec.dbg_who[p] = v[k];
-            rec.dbg_subset[p] = cSlo - cShi;
-            rec.dbg_updset[p] = cUlo - cUhi_after;
-        }
-    }
+    // A window boundary (a multiple of 2^win_shift >= SCAN_ITEMS) can only be
+    // a thread's first position; the counts there are this thread's start.
+    if (rec.windows && base < E && (base & ((1ull << rec.win_shift) - 1)) == 0)
+        rec.windows[base >> rec.win_shift] =
+            make_uint4(cSlo, cUlo, (uint32_t)base - cSlo - cUlo - cShi, (uint32_t)base);
+    const bool agg = cnt_agg != nullptr;
+    if (base + SCAN_ITEMS <= E)
+        sweep_walk<true, DBG>(v, base, E, n, m, rec, s_agg, agg, cSlo, cUlo, cShi, st);
+    else
+        sweep_walk<false, DBG>(v, base, E, n, m, rec, s_agg, agg, cSlo, cUlo, cShi, st);
+    // The thread holding position E - 1 writes the closing entry at E.
+    if (rec.windows && base < E && base + SCAN_ITEMS >= E)
+        rec.windows[(E + (1u << rec.win_shift) - 1) >> rec.win_shift] =
+            make_uint4(cSlo, cUlo, E - cSlo - cUlo - cShi, E);
     if (cnt_agg) {
         __syncthreads();
         for (uint32_t t = tid; t < cnt_tiles; t += SCAN_BLOCK)
@@ -194,9 +213,11 @@ int launch_sweep_scan(const uint32_t* vals, uint64_t E, int64_t n, int64_t m, co
     const uint64_t ctiles = ceil_div((uint64_t)n, (uint64_t)OFF_TILE);
     if (ctiles > CNT_AGG_MAX_TILES) cnt_agg = nullptr;
     const uint32_t ct = cnt_agg ? (uint32_t)ctiles : 0u;
-    launch_k(k_sweep_scan, (unsigned)tiles, SCAN_BLOCK, ct * sizeof(unsigned long long), s, vals,
-             (uint32_t)E, (uint32_t)n, (uint32_t)m, rec, status, counter,
-             reinterpret_cast<const uint4*>(kinds), cnt_agg, ct, st);
+    // Window boundaries fall on a thread's first position (see k_sweep_scan).
+    if (rec.windows && (1ull << rec.win_shift) % SCAN_ITEMS != 0) return -1;
+    launch_k(rec.dbg_who ? k_sweep_scan<true> : k_sweep_scan<false>, (unsigned)tiles, SCAN_BLOCK,
+             ct * sizeof(unsigned long long), s, vals, (uint32_t)E, (uint32_t)n, (uint32_t)m, rec,
+             status, counter, reinterpret_cast<const uint4*>(kinds), cnt_agg, ct, st);
     return 1;
 }
 

@@ -41,7 +41,10 @@ constexpr int WIN_WARPS = WIN_BLOCK / 32;
 constexpr uint32_t WCAP = 1024;       // candidates per window
 constexpr uint32_t LONG_SPAN = 512;   // positions; longer subscriptions use the range path
 constexpr int MAX_WIN_SHIFT = 10;     // windows of at most 1024 positions
-constexpr int NBUCKET = 256;          // buckets of the per-window id sort
+constexpr int SETUP_BITS = 8;         // log2 of the set-up block (threads per window)
+constexpr int SETUP_BLOCK = 1 << SETUP_BITS;
+constexpr int SETUP_WARPS = SETUP_BLOCK / 32;
+constexpr int NBUCKET = SETUP_BLOCK;  // buckets of the per-window id sort: one per thread
 
 constexpr uint32_t LCAP_W = 512;      // entries of a warp's candidate list (longer: in pieces)
 
@@ -212,11 +215,11 @@ __device__ __forceinline__ int2* shfl_ptr(int2* p, int l) {
 // and counts the flagged ones.  Kept apart from the filter so that the
 // latency of these dependent loads and the id sort does not hold the filter's
 // block slots: the filter kernel starts writing pairs after one load round.
-__global__ void __launch_bounds__(WIN_BLOCK) k_win_setup(EmitArgs a, DevStatus* st) {
+__global__ void __launch_bounds__(SETUP_BLOCK) k_win_setup(EmitArgs a, DevStatus* st) {
     pdl_begin();
     __shared__ uint4 raw[WCAP];                    // {id, lo, hi, arrival rank in bucket}
     __shared__ uint32_t byb[WCAP];                 // ids by bucket
-    __shared__ uint32_t bcnt[NBUCKET], bstart[NBUCKET], warp_tmp[WIN_WARPS];
+    __shared__ uint32_t bcnt[NBUCKET], bstart[NBUCKET], warp_tmp[SETUP_WARPS];
     __shared__ uint32_t s_pmax, s_nlow, s_base;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t w = blockIdx.x;
@@ -248,14 +251,14 @@ __global__ void __launch_bounds__(WIN_BLOCK) k_win_setup(EmitArgs a, DevStatus* 
     const uint64_t nall = (uint64_t)lw_n + nspec;
     const uint32_t nload = lfit ? (uint32_t)(nall < WCAP ? nall : WCAP) : 0u;
     if (tid == 0) { s_pmax = 0; s_nlow = 0; }
-    for (int b = tid; b < NBUCKET; b += WIN_BLOCK) bcnt[b] = 0;
+    for (int b = tid; b < NBUCKET; b += SETUP_BLOCK) bcnt[b] = 0;
     __syncthreads();
     // Round 2: the window's subscriptions (rank-ordered table; a first flag
     // for each: 1 = longer than LONG_SPAN), the boundary list and the rank
     // entries after the boundary.
     {
         uint32_t pm = 0, nlong = 0;
-        for (uint32_t k = tid; k < ns; k += WIN_BLOCK) {
+        for (uint32_t k = tid; k < ns; k += SETUP_BLOCK) {
             const uint4 e = a.srank[r0 + k].e;
             const bool lng = e.z - e.y > LONG_SPAN;
             a.flag[e.x] = lng ? 1 : 0;
@@ -269,11 +272,11 @@ __global__ void __launch_bounds__(WIN_BLOCK) k_win_setup(EmitArgs a, DevStatus* 
             if (nlong) atomicAdd(a.num_flagged, nlong);
         }
     }
-    for (uint32_t k0 = 0; k0 < nload; k0 += 4 * WIN_BLOCK) {
+    for (uint32_t k0 = 0; k0 < nload; k0 += 4 * SETUP_BLOCK) {
         uint4 e[4];
 #pragma unroll
         for (int it = 0; it < 4; ++it) {
-            const uint32_t k = k0 + tid + it * WIN_BLOCK;
+            const uint32_t k = k0 + tid + it * SETUP_BLOCK;
             e[it] = make_uint4(0u, 0u, 0u, 0u);
             if (k < nload) {
                 if (k < lw_n) {  // starts before the window: pos(lo) < any pos(S.hi)
@@ -287,7 +290,7 @@ __global__ void __launch_bounds__(WIN_BLOCK) k_win_setup(EmitArgs a, DevStatus* 
         }
 #pragma unroll
         for (int it = 0; it < 4; ++it) {
-            const uint32_t k = k0 + tid + it * WIN_BLOCK;
+            const uint32_t k = k0 + tid + it * SETUP_BLOCK;
             if (k < nload) raw[k] = e[it];
         }
     }
@@ -297,7 +300,8 @@ __global__ void __launch_bounds__(WIN_BLOCK) k_win_setup(EmitArgs a, DevStatus* 
     const uint32_t pmax = s_pmax;
     {
         uint32_t c = 0;
-        for (uint32_t k = lw_n + tid; k < nload; k += WIN_BLOCK) c += raw[k].y < pmax ? 1u : 0u;
+        for (uint32_t k = lw_n + tid; k < nload; k += SETUP_BLOCK)
+            c += raw[k].y < pmax ? 1u : 0u;
         c = __reduce_add_sync(0xffffffffu, c);
         if (lane == 0 && c) atomicAdd(&s_nlow, c);
     }
@@ -320,7 +324,7 @@ __global__ void __launch_bounds__(WIN_BLOCK) k_win_setup(EmitArgs a, DevStatus* 
     if (overflow) {
         // The whole window goes to the range path.
         uint32_t nreg = 0;
-        for (uint32_t k = tid; k < ns; k += WIN_BLOCK) {
+        for (uint32_t k = tid; k < ns; k += SETUP_BLOCK) {
             const uint4 e = a.srank[r0 + k].e;
             if (e.z - e.y <= LONG_SPAN) { a.flag[e.x] = 1; ++nreg; }
         }
@@ -334,12 +338,12 @@ __global__ void __launch_bounds__(WIN_BLOCK) k_win_setup(EmitArgs a, DevStatus* 
     // W sorted by id: bucket sort on the high id bits (bucket starts by a
     // block scan, arrival rank in the bucket by a shared atomic), then the
     // exact place inside a bucket by counting smaller ids among its members.
-    const int bshift = a.id_bits > 8 ? a.id_bits - 8 : 0;
-    for (uint32_t k = tid; k < W; k += WIN_BLOCK)
+    const int bshift = a.id_bits > SETUP_BITS ? a.id_bits - SETUP_BITS : 0;
+    for (uint32_t k = tid; k < W; k += SETUP_BLOCK)
         raw[k].w = atomicAdd(&bcnt[raw[k].x >> bshift], 1u);
     __syncthreads();
     {
-        static_assert(NBUCKET == WIN_BLOCK, "one bucket per thread");
+        static_assert(NBUCKET == SETUP_BLOCK && SETUP_BLOCK <= 1024, "one bucket per thread");
         const uint32_t c = bcnt[tid];
         uint32_t x = c;
 #pragma unroll
@@ -351,17 +355,17 @@ __global__ void __launch_bounds__(WIN_BLOCK) k_win_setup(EmitArgs a, DevStatus* 
         __syncthreads();
         uint32_t before = 0;
 #pragma unroll
-        for (int q = 0; q < WIN_WARPS; ++q) before += q < warp ? warp_tmp[q] : 0u;
+        for (int q = 0; q < SETUP_WARPS; ++q) before += q < warp ? warp_tmp[q] : 0u;
         bstart[tid] = before + x - c;
     }
     __syncthreads();
-    for (uint32_t k = tid; k < W; k += WIN_BLOCK) {
+    for (uint32_t k = tid; k < W; k += SETUP_BLOCK) {
         const uint4 e = raw[k];
         byb[bstart[e.x >> bshift] + e.w] = e.x;
     }
     __syncthreads();
     uint2* const cand = a.wcand + base;
-    for (uint32_t k = tid; k < W; k += WIN_BLOCK) {
+    for (uint32_t k = tid; k < W; k += SETUP_BLOCK) {
         const uint4 e = raw[k];
         const uint32_t b = e.x >> bshift, s0 = bstart[b], c = bcnt[b];
         uint32_t f = s0;
@@ -513,7 +517,7 @@ int launch_upd_ranks(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
 
 int launch_win_setup(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
     if (a.num_win == 0 || a.n == 0) return 0;
-    launch_k(k_win_setup, a.num_win, WIN_BLOCK, 0, s, a, st);
+    launch_k(k_win_setup, a.num_win, SETUP_BLOCK, 0, s, a, st);
     return 1;
 }
 
