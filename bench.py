@@ -597,6 +597,17 @@ def run_ours(args):
         "clocks": clocks,
         "wall_s_timed": wall,
     }
+    # The emission's store pattern without its filter (one warp per output
+    # segment, segments of unrelated ids in flight together), measured here:
+    # the ceiling that the emission's bandwidth is read against.
+    if args.d == 1 and top == "emit" and n > 0 and K > 0:
+        wp = {"segments": n, "mean_pairs": max(1, round(K / n))}
+        for name, sc in (("scattered", True), ("sequential", False)):
+            ms, nb = ctx.debug_write_pattern(n, wp["mean_pairs"], scattered=sc, reps=5)
+            wp[name + "_gbs"] = nb / (ms * 1e-3) / 1e9
+        line["write_pattern"] = wp
+        line["roofline"]["pattern_ceiling_gbs"] = wp["scattered_gbs"]
+        line["roofline"]["frac_of_pattern"] = achieved / wp["scattered_gbs"]
     if args.d > 1:
         # d > 1 is bound by the per-candidate filter: report the dimension-0
         # candidates (pairs that intersect in dimension 0, an exact d = 1 count of

@@ -399,6 +399,28 @@ int ddm_debug_sweep(ddm_ctx *ctx, const ddm_regions *regions, uint32_t *sorted_w
  */
 int ddm_debug_wait_timeout(ddm_ctx *ctx, int which, uint32_t spin_limit);
 
+/*
+ * Measurement aid: the write pattern of the window emission without its
+ * filter, as the ceiling against which the emission's bandwidth is read.
+ * nseg segments of 8-byte pairs, segment lengths drawn (hash of the segment
+ * id) uniformly from mean_len/2 .. mean_len/2 + mean_len, laid out back to
+ * back like the sorted pair list; one warp writes a segment in steps of 32
+ * consecutive pairs with streaming stores.  scattered = 0: warps take the
+ * segments in id order (concurrent segments adjacent in memory); scattered
+ * != 0: in the order g * step mod nseg, step coprime to nseg near 0.618 nseg
+ * (concurrent segments far apart, as the emission's windows meet
+ * subscriptions of unrelated ids).  Runs reps + 1 times (the first warms up),
+ * writing 256 MiB between runs to flush L2, and stores the fastest CUDA-event
+ * time in *ms_out (ms) and the bytes written per run in *bytes_out (may be
+ * NULL).  nseg 1 .. 2^26, mean_len 1 .. 4096, reps 1 .. 100, else
+ * DDM_ERR_INVALID.  Allocates its buffers for the call with cudaMalloc,
+ * outside the context's memory budget (DDM_ERR_NOMEM when that fails), and
+ * frees them before returning.  Synchronous, on the context's stream.  Not
+ * part of the paper's method.
+ */
+int ddm_debug_write_pattern(ddm_ctx *ctx, uint32_t nseg, uint32_t mean_len, int scattered,
+                            int reps, double *ms_out, uint64_t *bytes_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -97,6 +97,9 @@ SIGNATURES = {
                                               _U64P, _U64P]),
     "ddm_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(Stats)]),
     "ddm_debug_wait_timeout": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_uint32]),
+    "ddm_debug_write_pattern": (ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int,
+                                               ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                               ctypes.POINTER(ctypes.c_uint64)]),
 }
 
 
@@ -415,6 +418,16 @@ class Context:
         DDM_ERR_DEVICE_TIMEOUT)."""
         self._check(self._lib.ddm_debug_wait_timeout(self._h, int(which), int(spin_limit)))
 
+    def debug_write_pattern(self, nseg: int, mean_len: int, scattered: bool = True,
+                            reps: int = 5):
+        """ddm_debug_write_pattern: the emission's store pattern without its filter.
+        Returns (fastest ms, bytes written per run)."""
+        ms = ctypes.c_double(0.0)
+        nbytes = ctypes.c_uint64(0)
+        self._check(self._lib.ddm_debug_write_pattern(self._h, int(nseg), int(mean_len),
+                                                      1 if scattered else 0, int(reps),
+                                                      ctypes.byref(ms), ctypes.byref(nbytes)))
+        return ms.value, nbytes.value
     def debug_sweep(self, sub_lo, sub_hi, upd_lo, upd_hi):
         """ddm_debug_sweep: (sorted_who, subset_size, updset_size, sub_count, upd_count)."""
         torch = _torch()

@@ -24,6 +24,11 @@ namespace ddm {
 thread_local bool g_pdl = false;
 int launch_wait_selftest(int which, uint32_t limit, unsigned long long* status, DevStatus* st,
                          cudaStream_t s);
+// k_selftest.cu: the write-pattern reference of the window emission.
+int launch_wp_lengths(uint32_t* len, uint32_t nseg, uint32_t mean_len, uint32_t seed,
+                      cudaStream_t s);
+int launch_wp_write(int2* out, const unsigned long long* off, uint32_t nseg, uint32_t step,
+                    cudaStream_t s);
 // k_status.cu: a call's zero fill (status and zeroed workspace) and the status
 // copy into the mapped host mirror.
 int launch_prologue(DevStatus* st, void* zero, uint64_t zero_bytes, cudaStream_t s);
@@ -1614,6 +1619,95 @@ int ddm_debug_wait_timeout(ddm_ctx* c, int which, uint32_t spin_limit) {
                                               c->stream);
     CK(cudaGetLastError());
     return finish(c, nullptr);
+}
+
+int ddm_debug_write_pattern(ddm_ctx* c, uint32_t nseg, uint32_t mean_len, int scattered,
+                            int reps, double* ms_out, uint64_t* bytes_out) {
+    if (!c) return DDM_ERR_INVALID;
+    if (!ms_out || nseg < 1 || nseg > (1u << 26) || mean_len < 1 || mean_len > 4096 ||
+        reps < 1 || reps > 100)
+        return fail(c, DDM_ERR_INVALID,
+                    "write pattern: nseg 1..2^26, mean_len 1..4096, reps 1..100");
+    DeviceGuard g(c->device);
+    cudaStream_t s = c->stream;
+    const uint64_t ntile = ceil_div((uint64_t)nseg, (uint64_t)OFF_TILE);
+    uint32_t* len = nullptr;
+    unsigned long long *off = nullptr, *st = nullptr;
+    int2* out = nullptr;
+    void* flush = nullptr;
+    const size_t flush_bytes = 256u << 20;  // larger than L2: written between timed runs
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = DDM_OK;
+    auto release = [&]() {
+        cudaFree(len); cudaFree(off); cudaFree(st); cudaFree(out); cudaFree(flush);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    if (cudaMalloc(&len, nseg * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&off, (nseg + 1ull) * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&st, (ntile + 3) * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&flush, flush_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        release();
+        return fail(c, DDM_ERR_NOMEM, "write pattern buffers");
+    }
+    // Lengths, then offsets by the library's scan (status words and total zeroed).
+    unsigned long long K = 0;
+    if (cudaMemsetAsync(c->dstat, 0, sizeof(DevStatus), s) != cudaSuccess ||
+        cudaMemsetAsync(st, 0, (ntile + 3) * sizeof(unsigned long long), s) != cudaSuccess) {
+        cudaGetLastError();
+        release();
+        return fail(c, DDM_ERR_CUDA, "write pattern set-up");
+    }
+    c->stats.launches += launch_wp_lengths(len, nseg, mean_len, 0x9e3779b9u, s);
+    c->stats.launches += launch_offsets(len, nseg, off, ~0ull, st + ntile + 2, st, c->dstat, s);
+    if (cudaMemcpyAsync(&K, st + ntile + 2, sizeof(K), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        release();
+        return fail(c, DDM_ERR_CUDA, "write pattern offsets");
+    }
+    if (cudaMalloc(&out, K * sizeof(int2)) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        release();
+        return fail(c, DDM_ERR_NOMEM, "write pattern output");
+    }
+    // Scattered order: a step near 0.618 nseg, coprime to nseg.
+    uint32_t step = 0;
+    if (scattered && nseg > 2) {
+        step = (uint32_t)(0.6180339887 * nseg) | 1u;
+        auto gcd = [](uint32_t a, uint32_t b) {
+            while (b) {
+                const uint32_t t = a % b;
+                a = b;
+                b = t;
+            }
+            return a;
+        };
+        while (gcd(step, nseg) != 1) step += 2;
+    }
+    double best = 1e30;
+    for (int r = 0; r < reps + 1 && rc == DDM_OK; ++r) {
+        if (cudaMemsetAsync(flush, r & 0xff, flush_bytes, s) != cudaSuccess ||
+            cudaEventRecord(e0, s) != cudaSuccess) { rc = DDM_ERR_CUDA; break; }
+        c->stats.launches += launch_wp_write(out, off, nseg, step, s);
+        float ms = 0.f;
+        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) { rc = DDM_ERR_CUDA; break; }
+        if (r > 0 && ms < best) best = ms;  // the first run warms up
+    }
+    if (rc != DDM_OK) {
+        cudaGetLastError();
+        release();
+        return fail(c, rc, "write pattern timing");
+    }
+    release();
+    rc = finish(c, nullptr);
+    if (rc) return rc;
+    *ms_out = best;
+    if (bytes_out) *bytes_out = K * sizeof(int2);
+    return DDM_OK;
 }
 
 int ddm_debug_sweep(ddm_ctx* c, const ddm_regions* r, uint32_t* sorted_who,

@@ -386,6 +386,37 @@ def test_bounded_wait_times_out_and_context_survives(which):
         assert e.value.code == ddm._lib.DDM_ERR_INVALID
 
 
+# --- measurement aid: the emission's write pattern without its filter -----------------
+
+def _wp_hash(x):
+    # the segment-length hash of the write-pattern aid (xorshift-multiply mix, 32-bit)
+    x &= 0xFFFFFFFF
+    x ^= x >> 16
+    x = (x * 0x7FEB352D) & 0xFFFFFFFF
+    x ^= x >> 15
+    x = (x * 0x846CA68B) & 0xFFFFFFFF
+    x ^= x >> 16
+    return x
+
+
+@pytest.mark.parametrize("scattered", [False, True], ids=["id_order", "scattered"])
+def test_write_pattern_aid_writes_the_stated_bytes(scattered):
+    # The aid writes exactly the segments it states (lengths from its hash) and
+    # reports a positive time; out-of-range arguments are rejected.
+    import paper_1703_06680_gb300 as ddm
+    nseg, mean = 3001, 37
+    want = 8 * sum(mean // 2 + _wp_hash(s ^ 0x9E3779B9) % (mean + 1) for s in range(nseg))
+    with ddm.Context(0) as c:
+        ms, nbytes = c.debug_write_pattern(nseg, mean, scattered=scattered, reps=2)
+        assert nbytes == want and ms > 0
+        for bad in ((0, 10), (10, 0), (10, 5000)):
+            with pytest.raises(ddm.DDMError) as e:
+                c.debug_write_pattern(*bad)
+            assert e.value.code == ddm._lib.DDM_ERR_INVALID
+        reg = synth.small_1d()
+        assert np.array_equal(gpu_pairs(c, reg), oracle.sbm(reg))  # context still usable
+
+
 def test_tile_parameters_change_only_speed():
     # Every sort tile size (keys per thread) and every join window gives the
     # oracle's pairs, including the flat-scan sort above 1024 tiles.
