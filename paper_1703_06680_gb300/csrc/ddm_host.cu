@@ -551,11 +551,15 @@ int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
     if (pl.window && !fused_counts)
         return fail(c, DDM_ERR_INTERNAL, "window path without fused counts");
     // Window path: the rank tables of the emission are scattered from id order
-    // here (subscriptions by the offsets scan, updates by launch_upd_ranks).
-    if (fused_counts) {
+    // here, in one launch (subscriptions by the offsets scan, updates beside it).
+    if (fused_counts && pl.window && pl.n > 0) {
+        const int lr = launch_rank_tables(rec, pl.n, pl.cnt, pl.off, off_cap, &c->dstat->K,
+                                          pl.off_status, cnt_agg, a, c->dstat, s);
+        if (lr < 0) return fail(c, DDM_ERR_INTERNAL, "rank tables launch configuration");
+        L += lr;
+    } else if (fused_counts) {
         L += launch_rank_offsets(rec, pl.n, pl.cnt, pl.off, off_cap, &c->dstat->K, pl.off_status,
-                                 c->dstat, s, cnt_agg, pl.window ? pl.srank : nullptr);
-        if (pl.window) L += launch_upd_ranks(a, c->dstat, s);
+                                 c->dstat, s, cnt_agg);
     } else
         L += launch_offsets(pl.cnt, pl.n, pl.off, off_cap, &c->dstat->K, pl.off_status, c->dstat, s);
     if (batch) L += launch_inst_offsets(ba, pl.off, pl.inst_off, s);

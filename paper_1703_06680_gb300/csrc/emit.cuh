@@ -83,9 +83,15 @@ int launch_surv_compact(const unsigned long long* surv, const unsigned long long
 
 // Window path for d = 1.
 int launch_tile_active(const EmitArgs& a, DevStatus* st, cudaStream_t s);
-// Window path (fixed-slot lists): urank and the boundary lists from the
-// updates' records in id order; srank comes from launch_rank_offsets.
-int launch_upd_ranks(const EmitArgs& a, DevStatus* st, cudaStream_t s);
+// Window path (fixed-slot lists), in one launch: the counts and offsets of
+// launch_rank_offsets with the subscription rank table a.srank, and from the
+// updates' records in id order the update rank table a.urank and the boundary
+// lists.  Returns -1 when not on the window path (n == 0, no windows, or no
+// srank).
+int launch_rank_tables(const Records& rec, int64_t n, uint32_t* cnt, unsigned long long* off,
+                       uint64_t cap, unsigned long long* total, unsigned long long* status,
+                       const unsigned long long* cnt_agg, const EmitArgs& a, DevStatus* st,
+                       cudaStream_t s);
 int launch_win_setup(const EmitArgs& a, DevStatus* st, cudaStream_t s);
 int launch_emit_window(const EmitArgs& a, DevStatus* st, cudaStream_t s);
 

@@ -31,6 +31,7 @@
 #include <atomic>
 
 #include "emit.cuh"
+#include "offsets.cuh"
 
 namespace ddm {
 
@@ -74,7 +75,7 @@ __device__ __forceinline__ bool list_fits(const EmitArgs& a, uint32_t w, uint32_
 // union of its lanes' boundary ranges and reserves the slots of all lanes
 // crossing boundary w with one atomic (order inside a list is irrelevant: the
 // join sorts its candidates by id).  The window path of d = 1 builds the same
-// tables from id order instead (k_upd_ranks, launch_rank_offsets).
+// tables from id order instead (k_rank_tables).
 __global__ void k_tile_active(EmitArgs a, DevStatus* st) {
     pdl_begin();
     if (read_error(st)) return;
@@ -124,12 +125,12 @@ __global__ void k_tile_active(EmitArgs a, DevStatus* st) {
 // boundary list of every window boundary it spans, one atomic per list entry
 // (about a fifth of the updates span one at the usual densities).  The
 // subscriptions' rank tables come from the offsets scan (launch_rank_offsets).
-__global__ void __launch_bounds__(256) k_upd_ranks(EmitArgs a, DevStatus* st) {
-    pdl_begin();
+__device__ __forceinline__ void upd_ranks_blocks(const EmitArgs& a, DevStatus* st,
+                                                 uint32_t block, uint32_t nblocks) {
     if (read_error(st)) return;
     const int S = a.win_shift;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < a.m; j += stride) {
+    const int64_t stride = (int64_t)nblocks * blockDim.x;
+    for (int64_t j = (int64_t)block * blockDim.x + threadIdx.x; j < a.m; j += stride) {
         const uint4 lo = a.rec.u_lo[j];
         const uint32_t ph = a.rec.u_hi[j].x, pl = lo.x, r = lo.w;
         if (r >= a.m) {
@@ -149,6 +150,22 @@ __global__ void __launch_bounds__(256) k_upd_ranks(EmitArgs a, DevStatus* st) {
                 raise_error(st, DDM_ERR_INTERNAL, 10);
         }
     }
+}
+
+// The window path's rank tables in one launch: blocks [0, off_blocks) run the
+// offsets scan over the subscriptions' counts, which also scatters their rank
+// table (offsets_tile); the others build the update table and the boundary
+// lists.  Both read only the sweep's records, so their latencies overlap.
+// Three blocks per SM (up to 85 registers) keep the scan part free of spills.
+__global__ void __launch_bounds__(OFF_BLOCK, 3)
+k_rank_tables(OffsetSource src, uint32_t n, unsigned long long* off, unsigned long long cap,
+              unsigned long long* total_out, unsigned long long* status, uint32_t* tile_counter,
+              uint32_t off_blocks, EmitArgs a, DevStatus* st) {
+    pdl_begin();
+    if (blockIdx.x < off_blocks)
+        offsets_tile(src, n, off, cap, total_out, status, tile_counter, st, blockIdx.x);
+    else
+        upd_ranks_blocks(a, st, blockIdx.x - off_blocks, gridDim.x - off_blocks);
 }
 
 // One subscription of the filter: its relative bounds, output id, id base
@@ -509,9 +526,17 @@ int launch_tile_active(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
     return 1;
 }
 
-int launch_upd_ranks(const EmitArgs& a, DevStatus* st, cudaStream_t s) {
-    if (a.num_win == 0 || a.m == 0) return 0;
-    launch_k(k_upd_ranks, grid_for((uint64_t)a.m, 256, 152 * 8), 256, 0, s, a, st);
+int launch_rank_tables(const Records& rec, int64_t n, uint32_t* cnt, unsigned long long* off,
+                       uint64_t cap, unsigned long long* total, unsigned long long* status,
+                       const unsigned long long* cnt_agg, const EmitArgs& a, DevStatus* st,
+                       cudaStream_t s) {
+    if (n == 0 || a.num_win == 0 || !a.srank) return -1;
+    const uint64_t tiles = ceil_div((uint64_t)n, (uint64_t)OFF_TILE);
+    uint32_t* counter = reinterpret_cast<uint32_t*>(status + tiles);
+    const OffsetSource src = rank_offset_source(rec, n, cnt, cnt_agg, a.srank);
+    const unsigned ub = a.m ? grid_for((uint64_t)a.m, OFF_BLOCK * 4, 152 * 2) : 0u;
+    launch_k(k_rank_tables, (unsigned)tiles + ub, OFF_BLOCK, 0, s, src, (uint32_t)n, off,
+             (unsigned long long)cap, total, status, counter, (uint32_t)tiles, a, st);
     return 1;
 }
 
