@@ -556,13 +556,17 @@ def run_ours(args):
     stage_avg = {k: v / args.steps for k, v in stage_sum.items()}
     N, n, m = args.N, reg.n, reg.m
     E = 2 * N
-    alg_bytes = {   # algorithmic bytes per launch of each stage
+    alg_bytes = {   # algorithmic bytes per launch of each stage (d = 1 window path)
         "keybuild": 8 * N + 16 * E,
         "radix_sort": 4 * 16 * E - 4 * E,
-        "sweep_scan": 4 * E + 20 * N + 4 * N,
+        # payloads read, one 16-byte rank record written per endpoint
+        "sweep_scan": 4 * E + 16 * E,
         "counts": 12 * n,
-        "offsets": 4 * n + 8 * (n + 1),
-        "emit_setup": 36 * m,
+        # both records read, count and offset written, 32-byte subscription and
+        # 16-byte update rank entries scattered
+        "offsets": 32 * N + 12 * n + 32 * n + 16 * m,
+        # subscription entries read, candidates read (16 B) and packed (8 B)
+        "emit_setup": 32 * n + 24 * m,
         "emit": 8 * K,
         "segsort": 8 * K,
     }
