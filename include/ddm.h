@@ -220,14 +220,16 @@ int ddm_count_noalloc(const ddm_regions *regions, void *cuda_stream, uint64_t *K
  *                         (default 18), i.e. tiles of 3072, 4096 or 4608 keys.
  *   DDM_PARAM_JOIN_SHIFT  log2 of the window length, in sorted-stream positions, of
  *                         the tiled join for d > 1: 9 .. 11 (default 11).
- *   DDM_PARAM_ND_WRITE    how ddm_match writes the pairs for d > 1 with the tiled join:
- *                         1 = a second filter pass into each subscription's segment,
- *                         then a per-segment sort; 2 = the count pass also records
- *                         every surviving pair as a 64-bit key and one radix sort of
- *                         those keys gives the list (no second filter pass; needs 16
- *                         bytes per pair and per slot of room, room sized by the last
- *                         call's K; falls back to 1 when a window's share overflows);
- *                         0 (default) = 2 for d >= 3, 1 for d = 2 (measured).
+ *   DDM_PARAM_ND_WRITE    how ddm_match and ddm_match_batch write the pairs for d > 1
+ *                         with the tiled join: 1 = a second filter pass into each
+ *                         subscription's segment, then a per-segment sort; 2 = the
+ *                         count pass also records every surviving pair as a 64-bit
+ *                         key and one radix sort of those keys gives the list (no
+ *                         second filter pass; needs 16 bytes per pair and per slot of
+ *                         room, room sized by the K of the context's last d > 1 count
+ *                         or match; falls back to 1 when a window's share overflows);
+ *                         0 (default) = 2 for d >= 3 and for d = 2 when that last K
+ *                         is at most 4 (n + m), else 1 (measured).
  * Results never depend on any tunable; only speed does.
  */
 #define DDM_PARAM_WIN_SHIFT 1

@@ -35,4 +35,11 @@ int launch_keybuild_batch(const BatchArgs& b, unsigned long long* keys, uint32_t
 int launch_inst_offsets(const BatchArgs& b, const unsigned long long* off,
                         unsigned long long* inst_off, cudaStream_t s);
 
+// K sorted survivor keys (i << jbits) | j with global ids to int32 pairs local
+// to the instance (n_base / m_base: the instances' first global ids, num + 1
+// entries each, on the device).
+int launch_batch_unpack(const unsigned long long* keys, uint64_t K, int jbits,
+                        const int64_t* n_base, const int64_t* m_base, int num, int32_t* pairs,
+                        cudaStream_t s);
+
 }  // namespace ddm

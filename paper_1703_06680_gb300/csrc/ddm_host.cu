@@ -476,7 +476,7 @@ int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
     }
     a.vals = vals_sorted;
     a.surv = nullptr;
-    if (pl.join && mode == Mode::Match && !batch && c->surv_keys) {
+    if (pl.join && mode == Mode::Match && c->surv_keys) {
         a.surv = c->surv_keys;
         a.surv_cap = c->surv_cap;
         a.surv_fill = pl.surv_fill;
@@ -814,7 +814,11 @@ int ddm_count(ddm_ctx* c, const ddm_regions* r, uint64_t* K_out) {
     if (rc) return rc;
     rc = enqueue_plain(c, &ro, Mode::Count, nullptr, 0, nullptr);
     if (rc) return rc;
-    return finish(c, K_out);
+    uint64_t K = 0;
+    rc = finish(c, &K);
+    if (K_out) *K_out = K;
+    if (rc == DDM_OK && ro.d > 1) c->surv_hint = K;  // sizes the next d > 1 match
+    return rc;
 }
 
 }  // extern "C"
@@ -823,6 +827,18 @@ namespace {
 
 constexpr int MATCH_RETRY = 1;  // not an error code: take the general path
 
+// d > 1 pairs from the count pass's survivors (one sort of K keys) or from a
+// second filter pass and per-segment sorts.  Measured on GB300: the survivors
+// win at d >= 3 (the filter dominates) and at d = 2 when the output is sparse
+// (K of the last d > 1 call at most 4 (n + m): the per-segment sorts of many
+// short segments dominate), the write pass at d = 2 with dense output (the
+// sort of K keys dominates).  DDM_PARAM_ND_WRITE overrides.
+bool use_survivors(const ddm_ctx* c, int d, int64_t n, int64_t m) {
+    if (d < 2 || c->nd_write == 1) return false;
+    if (c->nd_write == 2 || d >= 3) return true;
+    return c->surv_hint > 0 && c->surv_hint <= 4 * (uint64_t)(n + m);
+}
+
 // d > 1 with the tiled join: the count pass records every survivor as the key
 // (i << id_bits(m)) | j, and the sorted pair list is one radix sort of those
 // keys, unpacked into `pairs` -- no second filter pass and no per-segment
@@ -830,13 +846,17 @@ constexpr int MATCH_RETRY = 1;  // not an error code: take the general path
 // MATCH_RETRY (nothing written, the error text cleared) when the room cannot be
 // had, when not every survivor fitted, or when subscriptions of overflowing
 // windows went to the range path; the caller then runs the general pipeline.
-int match_from_survivors(ddm_ctx* c, const ddm_regions* r, int32_t* pairs, uint64_t cap,
-                         uint64_t* K_out) {
-    const int64_t n = r->n, m = r->m;
+// A batched job (job.num_inst > 0) works the same way on global ids; its pairs
+// are unpacked to ids local to their instance and inst_offsets (num + 1, host)
+// receives the instances' first pairs.
+int match_from_survivors(ddm_ctx* c, const Job& job, int32_t* pairs, uint64_t cap,
+                         uint64_t* K_out, uint64_t* inst_offsets = nullptr) {
+    const int64_t n = job.n, m = job.m;
+    const int num = job.num_inst;
     // Room for the keys: one slice per join window, sized by the window's
     // subscriptions.
     Plan pl0;
-    pl0.layout(nullptr, r->d, n, m, Mode::Match, 0, c->win_shift, c->nd_path, c->sort_items,
+    pl0.layout(nullptr, job.d, n, m, Mode::Match, num, c->win_shift, c->nd_path, c->sort_items,
                c->join_shift);
     const uint32_t slices = pl0.num_win;
     const uint64_t hint = c->surv_hint;  // 0: this attempt is not sized from a known K
@@ -864,8 +884,6 @@ int match_from_survivors(ddm_ctx* c, const ddm_regions* r, int32_t* pairs, uint6
     Carve cv;
     cv.base = c->sv;
     carve(cv);
-    Job job;
-    job.d = r->d; job.n = n; job.m = m; job.r = r;
     c->surv_keys = kb[0];
     c->surv_cap = per_sub;
     int rc = enqueue(c, job, Mode::Match, nullptr, 0, nullptr, Phase::Prefix);
@@ -876,8 +894,11 @@ int match_from_survivors(ddm_ctx* c, const ddm_regions* r, int32_t* pairs, uint6
     if (rc) return rc;
     c->surv_hint = K;
     Plan pl;
-    pl.layout(c->ws, job.d, n, m, Mode::Match, 0, c->win_shift, c->nd_path, c->sort_items,
+    pl.layout(c->ws, job.d, n, m, Mode::Match, num, c->win_shift, c->nd_path, c->sort_items,
               c->join_shift);
+    if (num > 0)
+        CK(cudaMemcpy(inst_offsets, pl.inst_off, (num + 1) * sizeof(uint64_t),
+                      cudaMemcpyDeviceToHost));
     std::vector<unsigned long long> fill(slices);
     uint32_t flagged = 0;
     CK(cudaMemcpy(fill.data(), pl.surv_fill, slices * sizeof(unsigned long long),
@@ -919,8 +940,12 @@ int match_from_survivors(ddm_ctx* c, const ddm_regions* r, int32_t* pairs, uint6
         // Keys only; the T - K unused slots (~0) sort last.
         c->stats.launches += launch_radix_sort<unsigned long long>(
             kb[1], nullptr, kb[0], nullptr, T, passes, sc, false, c->dstat, s);
-        c->stats.launches += launch_delta_unpack(kb[(passes & 1) ? 0 : 1], K, id_bits(m), pairs,
-                                                 s);
+        const unsigned long long* sorted = kb[(passes & 1) ? 0 : 1];
+        if (num > 0)
+            c->stats.launches += launch_batch_unpack(sorted, K, id_bits(m), pl.n_base, pl.m_base,
+                                                     num, pairs, s);
+        else
+            c->stats.launches += launch_delta_unpack(sorted, K, id_bits(m), pairs, s);
     }
     mark(c, 7);
     mark(c, 8);
@@ -942,18 +967,19 @@ int ddm_match(ddm_ctx* c, const ddm_regions* r, int32_t* pairs, uint64_t cap, ui
     std::vector<const float*> hold;
     rc = order_dims(c, r, &ro, hold);
     if (rc) return rc;
-    // d > 1 pairs from the count pass's survivors (one sort) or from a second
-    // filter pass and per-segment sorts: measured on GB300, the survivors win
-    // at d >= 3 (the filter dominates), the write pass at d = 2 (the sort of
-    // K keys dominates); DDM_PARAM_ND_WRITE overrides.
-    const bool survivors = c->nd_write == 2 || (c->nd_write == 0 && ro.d >= 3);
-    if (survivors && ro.d > 1 && c->nd_path != 2 && ro.n > 0 && ro.m > 0 && pairs) {
-        rc = match_from_survivors(c, &ro, pairs, cap, K_out);
+    if (use_survivors(c, ro.d, ro.n, ro.m) && c->nd_path != 2 && ro.n > 0 && ro.m > 0 && pairs) {
+        Job job;
+        job.d = ro.d; job.n = ro.n; job.m = ro.m; job.r = &ro;
+        rc = match_from_survivors(c, job, pairs, cap, K_out);
         if (rc != MATCH_RETRY) return rc;
     }
     rc = enqueue_plain(c, &ro, Mode::Match, pairs, cap, nullptr);
     if (rc) return rc;
-    return finish(c, K_out);
+    uint64_t K = 0;
+    rc = finish(c, &K);
+    if (K_out) *K_out = K;
+    if (ro.d > 1 && (rc == DDM_OK || rc == DDM_ERR_CAPACITY)) c->surv_hint = K;
+    return rc;
 }
 
 int ddm_match_host(ddm_ctx* c, const ddm_regions* r, int32_t* pairs, uint64_t cap,
@@ -1040,12 +1066,21 @@ int ddm_match_batch(ddm_ctx* c, int num, const ddm_regions* inst, int32_t* pairs
         return DDM_OK;
     }
     DeviceGuard g(c->device);
+    if (pairs && use_survivors(c, job.d, job.n, job.m) && c->nd_path != 2 && job.n > 0 &&
+        job.m > 0) {
+        int rc = match_from_survivors(c, job, pairs, cap, K_out, inst_offsets);
+        if (rc != MATCH_RETRY) return rc;
+    }
     const Mode mode = pairs ? Mode::Match : Mode::Count;
     int rc = enqueue(c, job, mode, pairs, pairs ? cap : 0, nullptr);
     if (rc) return rc;
     CK(cudaMemcpyAsync(inst_offsets, c->last_inst_off, (num + 1) * sizeof(uint64_t),
                        cudaMemcpyDeviceToHost, c->stream));
-    return finish(c, K_out);
+    uint64_t K = 0;
+    rc = finish(c, &K);
+    if (K_out) *K_out = K;
+    if (job.d > 1 && (rc == DDM_OK || rc == DDM_ERR_CAPACITY)) c->surv_hint = K;
+    return rc;
 }
 
 }  // extern "C"

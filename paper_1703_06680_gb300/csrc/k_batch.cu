@@ -87,6 +87,33 @@ int launch_keybuild_batch(const BatchArgs& b, unsigned long long* keys, uint32_t
     return 1;
 }
 
+// Sorted survivor keys (i << jbits) | j of a batched d > 1 match, with global
+// ids, to pairs of ids local to their instance (the instance of subscription i
+// holds update j too: the join only pairs extents of one instance).
+__global__ void k_batch_unpack(const unsigned long long* __restrict__ keys, uint64_t K, int jbits,
+                               const int64_t* __restrict__ n_base,
+                               const int64_t* __restrict__ m_base, int num,
+                               int2* __restrict__ pairs) {
+    pdl_begin();
+    const unsigned long long jmask = (1ull << jbits) - 1ull;
+    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < K;
+         k += (uint64_t)gridDim.x * blockDim.x) {
+        const unsigned long long key = keys[k];
+        const int64_t i = (int64_t)(key >> jbits), j = (int64_t)(key & jmask);
+        const int b = inst_of(n_base, num, i);
+        pairs[k] = make_int2((int32_t)(i - n_base[b]), (int32_t)(j - m_base[b]));
+    }
+}
+
+int launch_batch_unpack(const unsigned long long* keys, uint64_t K, int jbits,
+                        const int64_t* n_base, const int64_t* m_base, int num, int32_t* pairs,
+                        cudaStream_t s) {
+    if (K == 0) return 0;
+    launch_k(k_batch_unpack, grid_for(K), 256, 0, s, keys, K, jbits, n_base, m_base, num,
+             reinterpret_cast<int2*>(pairs));
+    return 1;
+}
+
 int launch_inst_offsets(const BatchArgs& b, const unsigned long long* off,
                         unsigned long long* inst_off, cudaStream_t s) {
     launch_k(k_inst_offsets, grid_for(b.num + 1), 256, 0, s, b, off, inst_off);

@@ -46,6 +46,41 @@ def test_batch_mixed_sizes(ctx, d):
     check_batch(ctx, regs)
 
 
+@pytest.mark.parametrize("d,mixed", [(2, False), (2, True), (3, False), (3, True)])
+def test_batch_write_modes_agree(d, mixed):
+    # The survivor path (one sort of the recorded pairs, unpacked to ids local to
+    # each instance) and the write pass give the same pairs and offsets, with
+    # empty instances and instances without subscriptions or updates among them.
+    # At one density the survivors' room (sized from the average K / n) suffices;
+    # with mixed densities dense windows may overflow it and fall back.
+    import paper_1703_06680_gb300 as ddm
+    rng = np.random.default_rng(300 + d + 10 * mixed)
+    regs = []
+    for b in range(120):
+        n, m = int(rng.integers(0, 300)), int(rng.integers(0, 300))
+        if b % 17 == 0:
+            n = 0
+        if b % 19 == 0:
+            m = 0
+        N = max(n + m, 1)
+        alpha = float(rng.choice([0.01, 1, 100])) if mixed else 1.0
+        regs.append(synth.make_regions(d, n, m, synth.side_for(alpha, N, d), 7000 * d + b))
+    insts = [to_dev(r) for r in regs]
+    got = {}
+    with ddm.Context(0) as c:
+        for mode in (1, 2):
+            c.set_param(ddm._lib.PARAM_ND_WRITE, mode)
+            s0 = c.stats()["survivor_calls"]
+            pairs, offs = c.match_batch(insts)
+            got[mode] = (pairs.cpu().numpy(), np.asarray(offs))
+            used = c.stats()["survivor_calls"] > s0
+            assert (not used) if mode == 1 else (used or mixed)
+    assert np.array_equal(got[1][0], got[2][0]) and np.array_equal(got[1][1], got[2][1])
+    offs = got[2][1]
+    for b, r in enumerate(regs):
+        assert np.array_equal(got[2][0][int(offs[b]):int(offs[b + 1])], oracle.sbm(r)), b
+
+
 def test_batch_dense_ties(ctx):
     from tests.helpers import tiny_grid_instance
     rng = np.random.default_rng(7)
