@@ -258,9 +258,9 @@ def bench_baselines(ctx, dev, reps: int = 5):
 def bench_incremental(args, dev, steps: int = 10, warmup: int = 3):
     """The headline workload as a session: every timestep drifts the extents by
     N(0, 0.01 side) and reports only the pairs that appeared or disappeared
-    (ddm_session_emit_delta), against count + full emission of the same
-    timestep; both also measured with their result delivered to pinned host
-    memory (what a consumer off the GPU receives)."""
+    (ddm_session_emit_delta, which counts the timestep itself), against count +
+    full emission of the same timestep; both also measured with their result
+    delivered to pinned host memory (what a consumer off the GPU receives)."""
     import torch
     import paper_1703_06680_gb300 as ddm
     reg = workload(args, 0)
@@ -294,12 +294,13 @@ def bench_incremental(args, dev, steps: int = 10, warmup: int = 3):
         return tot / max(n, 1), out
 
     def report(to_host=False):
-        K = sess.count()
+        # One library call: the report counts the drifted timestep itself (a report
+        # needs no K first; the full emission below needs K to size its output).
         a, r = sess.emit_delta(add_b, rem_b)
         if to_host:
             host[:len(a)].copy_(a, non_blocking=True)
             host[len(a):len(a) + len(r)].copy_(r, non_blocking=True)
-        return K, len(a), len(r)
+        return sess.K, len(a), len(r)
 
     def full(to_host=False):
         K = sess.count()

@@ -341,10 +341,12 @@ int ddm_session_emit(ddm_session *s, void *cuda_stream, int32_t *pairs, uint64_t
                      uint64_t *K_out);
 
 /*
- * Incremental matching: the change report of one timestep.  After
- * ddm_session_count, reports the pairs whose status changed since the last
- * successful ddm_session_emit_delta call (the first call reports every pair
- * as added):
+ * Incremental matching: the change report of one timestep.  Reports the
+ * pairs whose status changed since the last successful ddm_session_emit_delta
+ * call (the first call, which needs ddm_session_count first, reports every
+ * pair as added).  A later report of a timestep not yet counted runs the count
+ * phase itself, on the same stream with no synchronisation in between (K is
+ * not needed for a report):
  *   added   (DEVICE, 2 * cap_added int32)   pairs present now and not then,
  *   removed (DEVICE, 2 * cap_removed int32) pairs present then and not now,
  * both sorted lexicographically; *n_added / *n_removed receive their numbers.
@@ -356,8 +358,9 @@ int ddm_session_emit(ddm_session *s, void *cuda_stream, int32_t *pairs, uint64_t
  * from the sorted endpoint stream of the count phase).  The work therefore
  * follows the motion, not K.  If either list does not fit, returns
  * DDM_ERR_CAPACITY with both numbers set; calling again without a new count
- * writes the same report into larger buffers.  After a delivered report the
- * next one needs a new ddm_session_count.  Device memory (counted against the
+ * writes the same report into larger buffers.  A delivered report consumes
+ * the count: the next timestep is counted again (by ddm_session_count or by
+ * the report itself).  Device memory (counted against the
  * session budget): a copy of the coordinates, and 16 bytes per changed pair
  * plus sort scratch; for d > 1 also the updates' bounds of dimensions 1..d-1
  * sorted per dimension (16 bytes per update and dimension).  Synchronous.
@@ -368,6 +371,13 @@ int ddm_session_emit(ddm_session *s, void *cuda_stream, int32_t *pairs, uint64_t
 int ddm_session_emit_delta(ddm_session *s, void *cuda_stream, int32_t *added, uint64_t cap_added,
                            int32_t *removed, uint64_t cap_removed, uint64_t *n_added,
                            uint64_t *n_removed);
+
+/*
+ * K of the session's last count phase (run by ddm_session_count or by a
+ * change report that counted its timestep itself); 0 before the first.
+ * DDM_ERR_INVALID when s or K_out is NULL.  Host only, no device work.
+ */
+int ddm_session_K(ddm_session *s, uint64_t *K_out);
 
 /*
  * Diagnostic view of the sweep stages for dimension 0 (the sorted endpoint

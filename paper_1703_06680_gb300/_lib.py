@@ -95,6 +95,7 @@ SIGNATURES = {
     "ddm_session_emit": (ctypes.c_int, [_P, _P, _P, ctypes.c_uint64, _U64P]),
     "ddm_session_emit_delta": (ctypes.c_int, [_P, _P, _P, ctypes.c_uint64, _P, ctypes.c_uint64,
                                               _U64P, _U64P]),
+    "ddm_session_K": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64)]),
     "ddm_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(Stats)]),
     "ddm_debug_wait_timeout": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_uint32]),
     "ddm_debug_write_pattern": (ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int,
@@ -456,8 +457,9 @@ class Session:
         if rc != DDM_OK:
             raise DDMError(rc, "ddm_session_create failed")
         self._h = h
-        self._K_last = 0   # K of the last count()
+        self._K_last = 0   # K of the last count phase
         self._K_ref = 0    # K of the reference list of emit_delta()
+        self._counted = False  # a count phase is held (count() since the last drift/emit)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -482,14 +484,21 @@ class Session:
     def _stream(stream):
         return ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
 
+    @property
+    def K(self) -> int:
+        """K of the last count phase (count(), or a report that counted itself)."""
+        return self._K_last
+
     def drift(self, seed: int, step: int, sigma: float, stream=None):
         self._check(self._lib.ddm_session_drift(self._h, self._stream(stream), seed & (2**64 - 1),
                                                 step, float(sigma)))
+        self._counted = False
 
     def count(self, stream=None) -> int:
         K = ctypes.c_uint64(0)
         self._check(self._lib.ddm_session_count(self._h, self._stream(stream), ctypes.byref(K)))
         self._K_last = int(K.value)
+        self._counted = True
         return int(K.value)
 
     def emit(self, out, stream=None) -> int:
@@ -500,15 +509,20 @@ class Session:
                                         ctypes.c_void_p(out.data_ptr() if cap else 0), cap,
                                         ctypes.byref(K))
         self._check(rc, K.value)
+        self._counted = False
         return int(K.value)
 
     def emit_delta(self, added=None, removed=None, stream=None):
-        """Change report of the last count() against the previous emit_delta():
+        """Change report of this timestep against the previous emit_delta():
         returns (added, removed) as (rows, 2) int32 CUDA tensors, each sorted.  Given
         output tensors are filled and sliced; otherwise they are allocated at the
-        bounds (this timestep's K and the previous report's K)."""
+        bounds (this timestep's K and the previous report's K), for which the
+        timestep is counted first.  With given tensors, a timestep not counted
+        yet is counted by the report itself (one library call)."""
         import torch
         dev = torch.device("cuda", self.device)
+        if (added is None or removed is None) and not self._counted:
+            self.count(stream)
         if added is None:
             added = torch.empty((max(self._K_last, 1), 2), dtype=torch.int32, device=dev)
         if removed is None:
@@ -519,7 +533,10 @@ class Session:
             ctypes.c_void_p(removed.data_ptr()), removed.shape[0], ctypes.byref(na),
             ctypes.byref(nr))
         self._check(rc, max(na.value, nr.value))
-        self._K_ref = self._K_last
+        K = ctypes.c_uint64(0)
+        self._check(self._lib.ddm_session_K(self._h, ctypes.byref(K)))
+        self._K_last = self._K_ref = int(K.value)
+        self._counted = False
         return added[:na.value], removed[:nr.value]
 
     def packed(self):

@@ -1279,6 +1279,12 @@ int ddm_session_count(ddm_session* s, void* stream, uint64_t* K_out) {
     return DDM_OK;
 }
 
+int ddm_session_K(ddm_session* s, uint64_t* K_out) {
+    if (!s || !K_out) return DDM_ERR_INVALID;
+    *K_out = s->K;
+    return DDM_OK;
+}
+
 int ddm_session_emit(ddm_session* s, void* stream, int32_t* pairs, uint64_t cap, uint64_t* K_out) {
     if (!s) return DDM_ERR_INVALID;
     ddm_ctx* c = s->ctx;
@@ -1302,8 +1308,9 @@ int ddm_session_emit_delta(ddm_session* s, void* stream, int32_t* added, uint64_
     DeviceGuard g(c->device);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     c->stream = st;
-    if (!s->counted)
-        return fail(c, DDM_ERR_INVALID, "ddm_session_emit_delta needs ddm_session_count first");
+    if (!s->counted && !s->have_ref)
+        return fail(c, DDM_ERR_INVALID,
+                    "the first ddm_session_emit_delta needs ddm_session_count first");
     if ((!added && cap_added) || (!removed && cap_removed))
         return fail(c, DDM_ERR_INVALID, "output is NULL but its capacity is not 0");
     if ((reinterpret_cast<uintptr_t>(added) | reinterpret_cast<uintptr_t>(removed)) & 7u)
@@ -1337,7 +1344,17 @@ int ddm_session_emit_delta(ddm_session* s, void* stream, int32_t* added, uint64_
         s->have_ref = true;
         return DDM_OK;
     }
-    // Later reports: candidates from the coordinates that moved.
+    // Later reports: candidates from the coordinates that moved.  A timestep
+    // not counted yet is counted here, on the same stream without a host round
+    // trip (the report needs the sorted stream and rank records, not K); its
+    // prologue has cleared the status block.
+    bool fresh = false;
+    if (!s->counted) {
+        rc = session_prefix(s);
+        if (rc) return rc;
+        s->counted = true;
+        fresh = true;
+    }
     Plan pl;  // the layout of the count phase that produced the sorted stream
     pl.layout(c->ws, d, n, m, Mode::Match, 0, c->win_shift, c->nd_path, c->sort_items,
               c->join_shift);
@@ -1357,6 +1374,7 @@ int ddm_session_emit_delta(ddm_session* s, void* stream, int32_t* added, uint64_
                 default: a.now.upd_hi[k] = nowp; a.ref.upd_hi[k] = refp; break;
             }
         }
+    a.rec = pl.rec;
     a.ibits = id_bits(n);
     a.jbits = id_bits(m);
     a.counters = &c->dstat->aux[2];  // [2] added, [3] removed, [4] write cursor
@@ -1383,6 +1401,8 @@ int ddm_session_emit_delta(ddm_session* s, void* stream, int32_t* added, uint64_
             tmp[1] = cv.take<uint32_t>(d > 1 ? m : 0);
             if (d > 1) carve_sort<uint32_t>(cv, (uint64_t)m, 4, sc32, zb32, ze32);
             pk = cv.take<uint4>(pl.E);
+            a.ulo = cv.take<uint4>(m);
+            a.uhi = cv.take<uint4>(m);
             kb[0] = cv.take<unsigned long long>(cap);
             kb[1] = cv.take<unsigned long long>(cap);
             vb[0] = cv.take<uint32_t>(cap);
@@ -1401,7 +1421,7 @@ int ddm_session_emit_delta(ddm_session* s, void* stream, int32_t* added, uint64_
         a.cap = cap;
         PdlScope pdl_scope(c->pdl);
         uint64_t& L = c->stats.launches;
-        CK(cudaMemsetAsync(c->dstat, 0, sizeof(DevStatus), st));
+        if (!(fresh && attempt == 0)) CK(cudaMemsetAsync(c->dstat, 0, sizeof(DevStatus), st));
         CK(cudaMemsetAsync(a.disp, 0, DDM_MAX_DIMS * sizeof(unsigned long long), st));
         L += launch_delta_disp(a, c->dstat, st);
         L += launch_delta_refk(a, pk, st);
@@ -1425,6 +1445,7 @@ int ddm_session_emit_delta(ddm_session* s, void* stream, int32_t* added, uint64_
                                  s->ref_coords, s->coords, coord_bytes / sizeof(float), st);
         rc = finish(c, nullptr);
         if (rc) return rc;
+        if (fresh && attempt == 0) s->K = c->hstat->K;  // the count phase's K
         const uint64_t na = c->hstat->aux[2], nr = c->hstat->aux[3];
         const uint32_t f = static_cast<uint32_t>(c->hstat->aux[5]);
         if (n_added) *n_added = na;

@@ -30,8 +30,18 @@ struct DeltaArgs {
     const uint32_t* hi_key[DDM_MAX_DIMS - 1];
     const uint32_t* hi_id[DDM_MAX_DIMS - 1];
     const uint4* pk;                // dimension 0, per stream position: {current key,
-                                    // reference key, payload, 0} (E)
-    unsigned long long* disp;       // per dimension: bits of the largest |now - ref| (double)
+                                    // reference key, payload, w} (E); w = for a
+                                    // subscription bound the start of its walk in the
+                                    // stream of the other kind (below), else 0
+    // Dimension 0, the updates' bounds of one kind in stream order: ulo[r] for
+    // the r-th update lower endpoint, uhi[r] for the r-th upper, each {current
+    // key, reference key, update id, 0} (m each).  An S upper at stream position
+    // p walks ulo from cUlo(p), an S lower walks uhi from cUhi(p).
+    uint4* ulo;
+    uint4* uhi;
+    Records rec;                    // the count phase's rank records
+    unsigned long long* disp;       // per dimension: bits of the largest |now - ref| (float,
+                                    // rounded up, in the low 32 bits)
     unsigned long long* counters;   // [0] added, [1] removed, [2] write cursor
     unsigned long long* keys_out;   // (removed << (ibits + jbits)) | (i << jbits) | j per
                                     // changed pair, at most cap entries
@@ -51,7 +61,8 @@ int launch_delta_disp(const DeltaArgs& a, DevStatus* st, cudaStream_t s);
 int launch_delta_keys(const DeltaArgs& a, cudaStream_t s);
 
 // pk[p] = {keys[p], reference key (dimension 0) of the endpoint at stream
-// position p, vals[p], 0}, and disp[0].
+// position p, vals[p], walk start}, the per-kind update streams ulo / uhi, and
+// disp[0].
 int launch_delta_refk(const DeltaArgs& a, uint4* pk, cudaStream_t s);
 
 // The changed pairs, each exactly once: counters[0], [1] count them, and their

@@ -10,10 +10,13 @@
 // dimension k displaced by at most D_k, the two are now at most 2 D_k apart
 // (a <= b before and a > b now give 0 < a' - b' <= (a' - a) - (b' - b)).  So
 // the candidates of comparison (k, t) of S_i are the update bounds within
-// 2 D_k of S_i's bound: for dimension 0 a walk in the sorted endpoint stream
-// that the count phase has just produced (one thread per stream position, so
-// neighbouring threads walk neighbouring ranges), for the other dimensions a
-// binary search in the updates' bounds sorted per dimension.  A candidate is
+// 2 D_k of S_i's bound: for dimension 0 a walk among the update bounds of
+// the one kind the comparison involves (c1: lowers, c2: uppers), kept in
+// stream order from the sorted endpoint stream that the count phase has just
+// produced and entered where the count phase's rank records place S_i's bound
+// (subscription bounds taken in stream order, so neighbouring threads walk
+// neighbouring ranges); for the other dimensions a binary search in the
+// updates' bounds sorted per dimension.  A candidate is
 // kept if its predicate differs between the reference and the current
 // coordinates and (k, t) is the first of its comparisons, in the order
 // c1(0), c2(0), c1(1), ..., that changed: each changed pair is found exactly
@@ -25,11 +28,14 @@
 namespace ddm {
 
 constexpr int DELTA_BLOCK = 256;
+constexpr int DELTA_WALK = 4;  // entries read together per step of a neighbourhood walk
 
 // |now - ref| along one bound; 0 when the value did not change (which also
 // covers an infinite bound that stays infinite).
-__device__ __forceinline__ double moved(float now, float ref) {
-    return now == ref ? 0.0 : fabs((double)now - (double)ref);
+// Rounded up, so an upper bound of the exact distance (single precision with
+// directed rounding: the radii below stay supersets of the exact ones).
+__device__ __forceinline__ float moved(float now, float ref) {
+    return now == ref ? 0.f : __fsub_ru(fmaxf(now, ref), fminf(now, ref));
 }
 
 __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
@@ -40,14 +46,14 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
     return v;
 }
 
-// Non-negative doubles order like their bit patterns, so the maximum is kept
-// as an integer maximum of the bits.
+// Non-negative floats order like their bit patterns, so the maximum is kept
+// as an integer maximum of the bits (in the low 32 bits of disp[k]).
 __global__ void k_delta_disp(DeltaArgs a, DevStatus* st) {
     pdl_begin();
     if (read_error(st)) return;
     const uint64_t per_dim = 2ull * (a.n + a.m);
     for (int k = 1; k < a.d; ++k) {  // dimension 0: k_delta_refk
-        double mx = 0.0;
+        float mx = 0.f;
         for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < per_dim;
              e += (uint64_t)gridDim.x * blockDim.x) {
             const bool upd = e >= 2ull * a.n;
@@ -59,9 +65,9 @@ __global__ void k_delta_disp(DeltaArgs a, DevStatus* st) {
                                   : (hi ? a.now.sub_hi[k] : a.now.sub_lo[k]);
             const float* pr = upd ? (hi ? a.ref.upd_hi[k] : a.ref.upd_lo[k])
                                   : (hi ? a.ref.sub_hi[k] : a.ref.sub_lo[k]);
-            mx = fmax(mx, moved(pn[id], pr[id]));  // fmax drops a NaN (never produced)
+            mx = fmaxf(mx, moved(pn[id], pr[id]));  // fmaxf drops a NaN (never produced)
         }
-        const unsigned long long b = warp_max_u64((unsigned long long)__double_as_longlong(mx));
+        const unsigned long long b = warp_max_u64((unsigned long long)__float_as_uint(mx));
         if ((threadIdx.x & 31) == 0 && b) atomicMax(&a.disp[k], b);
     }
 }
@@ -99,19 +105,32 @@ int launch_delta_keys(const DeltaArgs& a, cudaStream_t s) {
 // Per dimension-0 stream position: the current key, the reference key of the
 // same endpoint (one gather per endpoint) and the payload, packed so that the
 // walks below read one 16-byte entry per step; and the largest displacement
-// along dimension 0 (disp[0]).
+// along dimension 0 (disp[0]).  An update bound also goes to the stream of its
+// kind at its rank among that kind (its rank record: w of a lower, z of an
+// upper); a subscription bound records where its walk starts in the stream of
+// the other kind: the update lowers before it (an upper's y) or the update
+// uppers before it (a lower's z).
 __global__ void k_delta_refk(DeltaArgs a, uint4* __restrict__ pk) {
     pdl_begin();
-    double mx = 0.0;
+    float mx = 0.f;
     for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < a.E; p += gridDim.x * blockDim.x) {
         const uint32_t v = a.vals[p], kind = v >> 30, id = v & ID_MASK, key = a.keys[p];
         const float* src = kind == KIND_SLO ? a.ref.sub_lo[0] : kind == KIND_ULO ? a.ref.upd_lo[0]
                          : kind == KIND_SHI ? a.ref.sub_hi[0] : a.ref.upd_hi[0];
+        const uint4* rec = kind == KIND_SLO ? a.rec.s_lo : kind == KIND_ULO ? a.rec.u_lo
+                         : kind == KIND_SHI ? a.rec.s_hi : a.rec.u_hi;
         const float r = src[id];
-        pk[p] = make_uint4(key, float_key(r), v, 0u);
-        mx = fmax(mx, moved(key_float(key), r));
+        const uint4 rr = rec[id];
+        const uint32_t rk = float_key(r);
+        uint32_t start = 0;
+        if (kind == KIND_SLO) start = rr.z;       // update uppers before S.lo
+        else if (kind == KIND_SHI) start = rr.y;  // update lowers before S.hi
+        else if (kind == KIND_ULO && rr.w < a.m) a.ulo[rr.w] = make_uint4(key, rk, id, 0u);
+        else if (kind == KIND_UHI && rr.z < a.m) a.uhi[rr.z] = make_uint4(key, rk, id, 0u);
+        pk[p] = make_uint4(key, rk, v, start);
+        mx = fmaxf(mx, moved(key_float(key), r));
     }
-    const unsigned long long b = warp_max_u64((unsigned long long)__double_as_longlong(mx));
+    const unsigned long long b = warp_max_u64((unsigned long long)__float_as_uint(mx));
     if ((threadIdx.x & 31) == 0 && b) atomicMax(&a.disp[0], b);
 }
 
@@ -221,28 +240,32 @@ struct LaneKeys {
 
 // Keys of the values within r of x (a superset: bounds rounded outwards;
 // everything when r is not finite).
-__device__ __forceinline__ void key_window(float x, double r, uint32_t& klo, uint32_t& khi) {
-    if (!(r < 1e300)) {
+__device__ __forceinline__ void key_window(float x, float r, uint32_t& klo, uint32_t& khi) {
+    if (!(r < INFINITY)) {
         klo = 0u;
         khi = 0xffffffffu;
         return;
     }
-    const double lo = (double)x - r, hi = (double)x + r;
-    klo = float_key(__double2float_rd(lo));
-    khi = float_key(__double2float_ru(hi));
-    if (lo != lo) klo = 0u;            // x infinite: inf - inf
-    if (hi != hi) khi = 0xffffffffu;
+    const float lo = __fsub_rd(x, r), hi = __fadd_ru(x, r);
+    klo = lo != lo ? 0u : float_key(lo);            // x infinite: a NaN cannot arise,
+    khi = hi != hi ? 0xffffffffu : float_key(hi);   // kept for safety
 }
 
-__device__ __forceinline__ double radius(const DeltaArgs& a, int k) {
-    const double D = __longlong_as_double((long long)a.disp[k]);
-    return D == 0.0 ? 0.0 : 2.0 * D * (1.0 + 0x1p-30);
+__device__ __forceinline__ float disp_of(const DeltaArgs& a, int k) {
+    return __uint_as_float((uint32_t)a.disp[k]);
+}
+
+// Dimension k >= 1: two endpoints whose comparison changed are now at most
+// 2 D_k apart.
+__device__ __forceinline__ float radius(const DeltaArgs& a, int k) {
+    return __fmul_ru(2.f, disp_of(a, k));
 }
 
 // Dimension 0: the stream positions, 64 per warp step; the subscription
 // bounds among them are handed out to the lanes (ballots), and each walks its
-// neighbourhood, testing each update bound of the other kind with the keys
-// alone (current and reference keys, packed per position).  Dimensions
+// neighbourhood in the stream of the update bounds it is compared with (c1 of
+// an S upper: update lowers; c2 of an S lower: update uppers), testing them
+// with the keys alone (current and reference keys, packed).  Dimensions
 // k >= 1: items (k, t, i), 32 per warp step, by binary search.  The lanes of a
 // warp reserve their output slots together.
 __global__ void __launch_bounds__(DELTA_BLOCK) k_delta_cand(DeltaArgs a, DevStatus* st) {
@@ -256,7 +279,7 @@ __global__ void __launch_bounds__(DELTA_BLOCK) k_delta_cand(DeltaArgs a, DevStat
     const uint64_t warp_id = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     LaneKeys out;
-    const double D0 = __longlong_as_double((long long)a.disp[0]);
+    const float D0 = disp_of(a, 0);
     if (threadIdx.x == 0) scnt = 0;
     __syncthreads();
     // A block takes 8 x 64 stream positions per iteration (the same number of
@@ -284,14 +307,15 @@ __global__ void __launch_bounds__(DELTA_BLOCK) k_delta_cand(DeltaArgs a, DevStat
             const uint32_t p = (uint32_t)pos;
             const uint4 ep = a.pk[p < a.E ? p : 0];  // mm != 0 and p < E by construction
             const uint32_t kind = ep.z >> 30;
-            const bool t0 = kind == KIND_SHI;                 // c1: U lowers near S.hi
-            const uint32_t want = t0 ? KIND_ULO : KIND_UHI;   // c2: U uppers near S.lo
+            const bool t0 = kind == KIND_SHI;           // c1: U lowers near S.hi
+            const uint4* const ws = t0 ? a.ulo : a.uhi;  // c2: U uppers near S.lo
             const uint32_t i = ep.z & ID_MASK, kp = ep.x, rp = ep.y;
+            const uint32_t start = ep.w < a.m ? ep.w : a.m;
             // The walk covers every update bound within |d_p| + D of this bound:
             // a changed comparison needs |now_q - now_p| <= |d_q - d_p| <= D + |d_p|.
             const float xp = key_float(kp);
-            const double dp = moved(xp, key_float(rp));
-            const double rad = D0 == 0.0 ? 0.0 : (D0 + dp) * (1.0 + 0x1p-30);
+            const float dp = moved(xp, key_float(rp));
+            const float rad = D0 == 0.f ? 0.f : __fadd_ru(D0, dp);
             uint32_t klo, khi;
             key_window(xp, rad, klo, khi);
             // This subscription's other bound along dimension 0 (loaded once, on
@@ -299,11 +323,10 @@ __global__ void __launch_bounds__(DELTA_BLOCK) k_delta_cand(DeltaArgs a, DevStat
             bool have_o = false;
             uint32_t ko_now = 0, ko_ref = 0;
             auto test = [&](const uint4 eq) {
-                if ((eq.z >> 30) != want) return;
                 const bool now = t0 ? eq.x <= kp : kp <= eq.x;
                 const bool ref = t0 ? eq.y <= rp : rp <= eq.y;
                 if (now == ref) return;
-                const uint32_t j = eq.z & ID_MASK;
+                const uint32_t j = eq.z;
                 if (!have_o) {
                     ko_now = float_key(t0 ? a.now.sub_lo[0][i] : a.now.sub_hi[0][i]);
                     ko_ref = float_key(t0 ? a.ref.sub_lo[0][i] : a.ref.sub_hi[0][i]);
@@ -325,15 +348,40 @@ __global__ void __launch_bounds__(DELTA_BLOCK) k_delta_cand(DeltaArgs a, DevStat
                 }
                 if (pr != pn) out.put(a, pn ? 1 : 2, i, j);
             };
-            for (uint32_t q = p; q-- > 0;) {
-                const uint4 eq = a.pk[q];
-                if (eq.x < klo) break;
-                test(eq);
+            // The update bounds of the wanted kind in stream order: those before
+            // this bound end at `start`.  Each side is read DELTA_WALK entries at a
+            // time (one round trip for the usual few entries within the radius).
+            for (uint32_t q = start; q > 0;) {
+                const uint32_t nq = q < DELTA_WALK ? q : DELTA_WALK;
+                uint4 e4[DELTA_WALK];
+#pragma unroll
+                for (int u = 0; u < DELTA_WALK; ++u)
+                    e4[u] = (uint32_t)u < nq ? ws[q - 1 - u] : make_uint4(0u, 0u, 0u, 0u);
+                bool stop = false;
+#pragma unroll
+                for (int u = 0; u < DELTA_WALK; ++u) {
+                    if (stop || (uint32_t)u >= nq) continue;
+                    if (e4[u].x < klo) stop = true;
+                    else test(e4[u]);
+                }
+                if (stop) break;
+                q -= nq;
             }
-            for (uint32_t q = p + 1; q < a.E; ++q) {
-                const uint4 eq = a.pk[q];
-                if (eq.x > khi) break;
-                test(eq);
+            for (uint32_t q = start; q < a.m;) {
+                const uint32_t nq = a.m - q < DELTA_WALK ? a.m - q : DELTA_WALK;
+                uint4 e4[DELTA_WALK];
+#pragma unroll
+                for (int u = 0; u < DELTA_WALK; ++u)
+                    e4[u] = (uint32_t)u < nq ? ws[q + u] : make_uint4(0u, 0u, 0u, 0u);
+                bool stop = false;
+#pragma unroll
+                for (int u = 0; u < DELTA_WALK; ++u) {
+                    if (stop || (uint32_t)u >= nq) continue;
+                    if (e4[u].x > khi) stop = true;
+                    else test(e4[u]);
+                }
+                if (stop) break;
+                q += nq;
             }
           }
           out.stage(a, lane, sbuf, &scnt, SBUF);

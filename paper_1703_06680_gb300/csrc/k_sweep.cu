@@ -56,7 +56,8 @@ __device__ __forceinline__ void sweep_walk(const uint32_t (&v)[SCAN_ITEMS], uint
         uint4* const tab =
             is_upper ? (is_upd ? rec.u_hi : rec.s_hi) : (is_upd ? rec.u_lo : rec.s_lo);
         const uint32_t y = is_upd ? cSlo : cUlo;  // lower endpoints seen of the other set
-        const uint32_t z = is_upper ? 0u : (is_upd ? cShi : cUhi);
+        // Lowers: uppers of the other set seen; uppers: own rank among this set's uppers.
+        const uint32_t z = is_upper ? (is_upd ? cUhi : cShi) : (is_upd ? cShi : cUhi);
         const uint32_t w = is_upper ? 0u : (is_upd ? cUlo : cSlo);
         tab[id] = make_uint4(p, y, z, w);
         // B_i at S_i's upper endpoint, -C_i at its lower one (mod 2^64).

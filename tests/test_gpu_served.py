@@ -167,8 +167,9 @@ def test_emit_delta_no_motion_and_capacity_retry(ddm):
     import torch
     reg = synth.make_regions(2, 3000, 3500, 3000.0, 5151)
     sess = ddm.Session(*to_dev(reg))
+    buf = torch.empty((16, 2), dtype=torch.int32, device="cuda:0")
     with pytest.raises(ddm.DDMError):
-        sess.emit_delta()                          # no count yet
+        sess.emit_delta(buf, buf)                  # the first report needs a count first
     K = sess.count()
     added, removed = sess.emit_delta()
     assert len(added) == K and len(removed) == 0
@@ -186,6 +187,35 @@ def test_emit_delta_no_motion_and_capacity_retry(ddm):
     want_prev, want = oracle.sbm(reg), oracle.sbm(host)
     assert np.array_equal(added.cpu().numpy(), _rows_minus(want, want_prev))
     assert np.array_equal(removed.cpu().numpy(), _rows_minus(want_prev, want))
+    sess.close()
+
+
+@pytest.mark.parametrize("d", [1, 2])
+def test_emit_delta_counts_its_own_timestep(ddm, d):
+    # After the first report, a report of a timestep nobody counted runs the
+    # count phase itself (one library call): the same differences, and the
+    # session's K is that timestep's.
+    import torch
+    N = 40_000
+    side = synth.side_for(100.0 if d == 1 else 10.0, N, d)
+    reg = synth.make_regions(d, N // 2, N - N // 2, side, 5200 + d)
+    sess = ddm.Session(*to_dev(reg))
+    host = reg
+    prev = oracle.sbm(host)
+    assert sess.count() == len(prev)
+    sess.emit_delta()
+    cap = max(len(prev), 16)
+    add_b = torch.empty((cap, 2), dtype=torch.int32, device="cuda:0")
+    rem_b = torch.empty((cap, 2), dtype=torch.int32, device="cuda:0")
+    for step in range(3):
+        sess.drift(33, step, 0.02 * side)
+        host = synth.drift(host, 33, step, 0.02 * side)
+        want = oracle.sbm(host)
+        added, removed = sess.emit_delta(add_b, rem_b)
+        assert sess.K == len(want)
+        assert np.array_equal(added.cpu().numpy(), _rows_minus(want, prev)), step
+        assert np.array_equal(removed.cpu().numpy(), _rows_minus(prev, want)), step
+        prev = want
     sess.close()
 
 
