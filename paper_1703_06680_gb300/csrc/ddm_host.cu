@@ -1401,8 +1401,8 @@ int ddm_session_emit_delta(ddm_session* s, void* stream, int32_t* added, uint64_
             tmp[1] = cv.take<uint32_t>(d > 1 ? m : 0);
             if (d > 1) carve_sort<uint32_t>(cv, (uint64_t)m, 4, sc32, zb32, ze32);
             pk = cv.take<uint4>(pl.E);
-            a.ulo = cv.take<uint4>(m);
-            a.uhi = cv.take<uint4>(m);
+            a.ulo = cv.take<uint4>(2 * m);
+            a.uhi = cv.take<uint4>(2 * m);
             kb[0] = cv.take<unsigned long long>(cap);
             kb[1] = cv.take<unsigned long long>(cap);
             vb[0] = cv.take<uint32_t>(cap);

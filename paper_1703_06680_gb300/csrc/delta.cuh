@@ -33,10 +33,12 @@ struct DeltaArgs {
                                     // reference key, payload, w} (E); w = for a
                                     // subscription bound the start of its walk in the
                                     // stream of the other kind (below), else 0
-    // Dimension 0, the updates' bounds of one kind in stream order: ulo[r] for
-    // the r-th update lower endpoint, uhi[r] for the r-th upper, each {current
-    // key, reference key, update id, 0} (m each).  An S upper at stream position
-    // p walks ulo from cUlo(p), an S lower walks uhi from cUhi(p).
+    // Dimension 0, the updates' bounds of one kind in stream order: entry r of
+    // ulo for the r-th update lower endpoint, of uhi for the r-th upper, each 32
+    // bytes at [2r, 2r + 1]: {current key, reference key, update id, 0} and the
+    // update's other bound {current key, reference key, 0, 0} (2m uint4 each).
+    // An S upper at stream position p walks ulo from cUlo(p), an S lower walks
+    // uhi from cUhi(p).
     uint4* ulo;
     uint4* uhi;
     Records rec;                    // the count phase's rank records

@@ -103,13 +103,13 @@ int launch_delta_keys(const DeltaArgs& a, cudaStream_t s) {
 }
 
 // Per dimension-0 stream position: the current key, the reference key of the
-// same endpoint (one gather per endpoint) and the payload, packed so that the
-// walks below read one 16-byte entry per step; and the largest displacement
-// along dimension 0 (disp[0]).  An update bound also goes to the stream of its
-// kind at its rank among that kind (its rank record: w of a lower, z of an
-// upper); a subscription bound records where its walk starts in the stream of
-// the other kind: the update lowers before it (an upper's y) or the update
-// uppers before it (a lower's z).
+// same endpoint (one gather per endpoint) and the payload, packed; and the
+// largest displacement along dimension 0 (disp[0]).  An update bound also goes
+// to the stream of its kind at its rank among that kind (its rank record: w of
+// a lower, z of an upper), with its update's other bound, so that a walk needs
+// no gather by id; a subscription bound records where its walk starts in the
+// stream of the other kind: the update lowers before it (an upper's y) or the
+// update uppers before it (a lower's z).
 __global__ void k_delta_refk(DeltaArgs a, uint4* __restrict__ pk) {
     pdl_begin();
     float mx = 0.f;
@@ -125,8 +125,14 @@ __global__ void k_delta_refk(DeltaArgs a, uint4* __restrict__ pk) {
         uint32_t start = 0;
         if (kind == KIND_SLO) start = rr.z;       // update uppers before S.lo
         else if (kind == KIND_SHI) start = rr.y;  // update lowers before S.hi
-        else if (kind == KIND_ULO && rr.w < a.m) a.ulo[rr.w] = make_uint4(key, rk, id, 0u);
-        else if (kind == KIND_UHI && rr.z < a.m) a.uhi[rr.z] = make_uint4(key, rk, id, 0u);
+        else if ((kind == KIND_ULO && rr.w < a.m) || (kind == KIND_UHI && rr.z < a.m)) {
+            const bool lo = kind == KIND_ULO;
+            const uint32_t on = float_key(lo ? a.now.upd_hi[0][id] : a.now.upd_lo[0][id]);
+            const uint32_t orf = float_key(lo ? a.ref.upd_hi[0][id] : a.ref.upd_lo[0][id]);
+            uint4* const dst = lo ? a.ulo + 2ull * rr.w : a.uhi + 2ull * rr.z;
+            dst[0] = make_uint4(key, rk, id, 0u);
+            dst[1] = make_uint4(on, orf, 0u, 0u);
+        }
         pk[p] = make_uint4(key, rk, v, start);
         mx = fmaxf(mx, moved(key_float(key), r));
     }
@@ -318,23 +324,17 @@ __global__ void __launch_bounds__(DELTA_BLOCK) k_delta_cand(DeltaArgs a, DevStat
             const float rad = D0 == 0.f ? 0.f : __fadd_ru(D0, dp);
             uint32_t klo, khi;
             key_window(xp, rad, klo, khi);
-            // This subscription's other bound along dimension 0 (loaded once, on
-            // the first changed comparison).
-            bool have_o = false;
-            uint32_t ko_now = 0, ko_ref = 0;
-            auto test = [&](const uint4 eq) {
+            // This subscription's other bound along dimension 0, loaded together
+            // with the walk's first entries (most lanes meet a changed comparison).
+            const uint32_t ko_now = float_key(t0 ? a.now.sub_lo[0][i] : a.now.sub_hi[0][i]);
+            const uint32_t ko_ref = float_key(t0 ? a.ref.sub_lo[0][i] : a.ref.sub_hi[0][i]);
+            auto test = [&](const uint4 eq, const uint4 eo) {
                 const bool now = t0 ? eq.x <= kp : kp <= eq.x;
                 const bool ref = t0 ? eq.y <= rp : rp <= eq.y;
                 if (now == ref) return;
                 const uint32_t j = eq.z;
-                if (!have_o) {
-                    ko_now = float_key(t0 ? a.now.sub_lo[0][i] : a.now.sub_hi[0][i]);
-                    ko_ref = float_key(t0 ? a.ref.sub_lo[0][i] : a.ref.sub_hi[0][i]);
-                    have_o = true;
-                }
-                // The update's other bound, now and then.
-                const uint32_t uo_now = float_key(t0 ? a.now.upd_hi[0][j] : a.now.upd_lo[0][j]);
-                const uint32_t uo_ref = float_key(t0 ? a.ref.upd_hi[0][j] : a.ref.upd_lo[0][j]);
+                // The update's other bound, now and then (carried by the entry).
+                const uint32_t uo_now = eo.x, uo_ref = eo.y;
                 // c1 = [U.lo <= S.hi], c2 = [S.lo <= U.hi] along dimension 0.
                 const bool c1n = t0 ? now : uo_now <= ko_now;
                 const bool c1r = t0 ? ref : uo_ref <= ko_ref;
@@ -353,32 +353,38 @@ __global__ void __launch_bounds__(DELTA_BLOCK) k_delta_cand(DeltaArgs a, DevStat
             // time (one round trip for the usual few entries within the radius).
             for (uint32_t q = start; q > 0;) {
                 const uint32_t nq = q < DELTA_WALK ? q : DELTA_WALK;
-                uint4 e4[DELTA_WALK];
+                uint4 e4[DELTA_WALK], o4[DELTA_WALK];
 #pragma unroll
-                for (int u = 0; u < DELTA_WALK; ++u)
-                    e4[u] = (uint32_t)u < nq ? ws[q - 1 - u] : make_uint4(0u, 0u, 0u, 0u);
+                for (int u = 0; u < DELTA_WALK; ++u) {
+                    const uint64_t at = 2ull * (q - 1 - u);
+                    e4[u] = (uint32_t)u < nq ? ws[at] : make_uint4(0u, 0u, 0u, 0u);
+                    o4[u] = (uint32_t)u < nq ? ws[at + 1] : make_uint4(0u, 0u, 0u, 0u);
+                }
                 bool stop = false;
 #pragma unroll
                 for (int u = 0; u < DELTA_WALK; ++u) {
                     if (stop || (uint32_t)u >= nq) continue;
                     if (e4[u].x < klo) stop = true;
-                    else test(e4[u]);
+                    else test(e4[u], o4[u]);
                 }
                 if (stop) break;
                 q -= nq;
             }
             for (uint32_t q = start; q < a.m;) {
                 const uint32_t nq = a.m - q < DELTA_WALK ? a.m - q : DELTA_WALK;
-                uint4 e4[DELTA_WALK];
+                uint4 e4[DELTA_WALK], o4[DELTA_WALK];
 #pragma unroll
-                for (int u = 0; u < DELTA_WALK; ++u)
-                    e4[u] = (uint32_t)u < nq ? ws[q + u] : make_uint4(0u, 0u, 0u, 0u);
+                for (int u = 0; u < DELTA_WALK; ++u) {
+                    const uint64_t at = 2ull * (q + u);
+                    e4[u] = (uint32_t)u < nq ? ws[at] : make_uint4(0u, 0u, 0u, 0u);
+                    o4[u] = (uint32_t)u < nq ? ws[at + 1] : make_uint4(0u, 0u, 0u, 0u);
+                }
                 bool stop = false;
 #pragma unroll
                 for (int u = 0; u < DELTA_WALK; ++u) {
                     if (stop || (uint32_t)u >= nq) continue;
                     if (e4[u].x > khi) stop = true;
-                    else test(e4[u]);
+                    else test(e4[u], o4[u]);
                 }
                 if (stop) break;
                 q += nq;
