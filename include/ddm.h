@@ -228,8 +228,9 @@ int ddm_count_noalloc(const ddm_regions *regions, void *cuda_stream, uint64_t *K
  *                         second filter pass; needs 16 bytes per pair and per slot of
  *                         room, room sized by the K of the context's last d > 1 count
  *                         or match; falls back to 1 when a window's share overflows);
- *                         0 (default) = 2 for d >= 3 and for d = 2 when that last K
- *                         is at most 4 (n + m), else 1 (measured).
+ *                         0 (default) = 2 for d >= 3, and for a batched call at
+ *                         d = 2 when that last K is at most 4 (n + m); else 1
+ *                         (measured).
  * Results never depend on any tunable; only speed does.
  */
 #define DDM_PARAM_WIN_SHIFT 1

@@ -29,7 +29,6 @@ struct BatchArgs {
     float* upd_hi[DDM_MAX_DIMS];
 };
 
-int launch_concat(const BatchArgs& b, cudaStream_t s);
 int launch_keybuild_batch(const BatchArgs& b, unsigned long long* keys, uint32_t* vals,
                           DevStatus* st, cudaStream_t s);
 int launch_inst_offsets(const BatchArgs& b, const unsigned long long* off,

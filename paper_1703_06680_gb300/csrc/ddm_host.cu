@@ -484,7 +484,6 @@ int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
   if (do_prefix) {
     mark(c, 0);
     if (batch) {
-        L += launch_concat(ba, s);
         L += launch_keybuild_batch(ba, (unsigned long long*)pl.keys0, pl.vals0, c->dstat, s);
     } else {
         L += launch_keybuild_d0(dims.sub_lo[0], dims.sub_hi[0], dims.upd_lo[0], dims.upd_hi[0],
@@ -829,14 +828,16 @@ constexpr int MATCH_RETRY = 1;  // not an error code: take the general path
 
 // d > 1 pairs from the count pass's survivors (one sort of K keys) or from a
 // second filter pass and per-segment sorts.  Measured on GB300: the survivors
-// win at d >= 3 (the filter dominates) and at d = 2 when the output is sparse
-// (K of the last d > 1 call at most 4 (n + m): the per-segment sorts of many
-// short segments dominate), the write pass at d = 2 with dense output (the
-// sort of K keys dominates).  DDM_PARAM_ND_WRITE overrides.
-bool use_survivors(const ddm_ctx* c, int d, int64_t n, int64_t m) {
+// win at d >= 3 (the filter dominates), and for a batched call at d = 2 when
+// the output is sparse (K of the last d > 1 call at most 4 (n + m): the
+// per-segment sorts of tens of millions of short segments dominate); a plain
+// d = 2 call keeps the write pass (a tie at N = 1e6, alpha = 1; the survivors'
+// extra host round trip loses at smaller sizes; the sort of K keys loses with
+// dense output).  DDM_PARAM_ND_WRITE overrides.
+bool use_survivors(const ddm_ctx* c, int d, int64_t n, int64_t m, bool batch) {
     if (d < 2 || c->nd_write == 1) return false;
     if (c->nd_write == 2 || d >= 3) return true;
-    return c->surv_hint > 0 && c->surv_hint <= 4 * (uint64_t)(n + m);
+    return batch && c->surv_hint > 0 && c->surv_hint <= 4 * (uint64_t)(n + m);
 }
 
 // d > 1 with the tiled join: the count pass records every survivor as the key
@@ -967,7 +968,8 @@ int ddm_match(ddm_ctx* c, const ddm_regions* r, int32_t* pairs, uint64_t cap, ui
     std::vector<const float*> hold;
     rc = order_dims(c, r, &ro, hold);
     if (rc) return rc;
-    if (use_survivors(c, ro.d, ro.n, ro.m) && c->nd_path != 2 && ro.n > 0 && ro.m > 0 && pairs) {
+    if (use_survivors(c, ro.d, ro.n, ro.m, false) && c->nd_path != 2 && ro.n > 0 && ro.m > 0 &&
+        pairs) {
         Job job;
         job.d = ro.d; job.n = ro.n; job.m = ro.m; job.r = &ro;
         rc = match_from_survivors(c, job, pairs, cap, K_out);
@@ -1066,7 +1068,7 @@ int ddm_match_batch(ddm_ctx* c, int num, const ddm_regions* inst, int32_t* pairs
         return DDM_OK;
     }
     DeviceGuard g(c->device);
-    if (pairs && use_survivors(c, job.d, job.n, job.m) && c->nd_path != 2 && job.n > 0 &&
+    if (pairs && use_survivors(c, job.d, job.n, job.m, true) && c->nd_path != 2 && job.n > 0 &&
         job.m > 0) {
         int rc = match_from_survivors(c, job, pairs, cap, K_out, inst_offsets);
         if (rc != MATCH_RETRY) return rc;

@@ -15,30 +15,9 @@
 
 namespace ddm {
 
-// Gather every instance's coordinates into the concatenated arrays.
-__global__ void k_concat(BatchArgs b) {
-    pdl_begin();
-    const int64_t R = b.n + b.m;
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < R;
-         r += (int64_t)gridDim.x * blockDim.x) {
-        const bool upd = r >= b.n;
-        const int64_t g = upd ? r - b.n : r;
-        const int inst = inst_of(upd ? b.m_base : b.n_base, b.num, g);
-        const int64_t local = g - (upd ? b.m_base[inst] : b.n_base[inst]);
-        const InstPtrs& ip = b.table[inst];
-        for (int k = 0; k < b.d; ++k) {
-            if (upd) {
-                b.upd_lo[k][g] = ip.upd_lo[k][local];
-                b.upd_hi[k][g] = ip.upd_hi[k][local];
-            } else {
-                b.sub_lo[k][g] = ip.sub_lo[k][local];
-                b.sub_hi[k][g] = ip.sub_hi[k][local];
-            }
-        }
-    }
-}
-
-// Instance-tagged dimension-0 keys in [S lo | U lo | S hi | U hi] layout.
+// One pass per region: the instance's coordinates of every dimension into the
+// concatenated arrays, and the instance-tagged dimension-0 keys in
+// [S lo | U lo | S hi | U hi] layout (one instance search per region).
 __global__ void k_keybuild_batch(BatchArgs b, unsigned long long* __restrict__ keys,
                                  uint32_t* __restrict__ vals, DevStatus* st) {
     pdl_begin();
@@ -47,16 +26,27 @@ __global__ void k_keybuild_batch(BatchArgs b, unsigned long long* __restrict__ k
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < R;
          r += (int64_t)gridDim.x * blockDim.x) {
         const bool upd = r >= b.n;
-        const int64_t id = upd ? r - b.n : r;
-        const int inst = inst_of(upd ? b.m_base : b.n_base, b.num, id);
-        const float lo = upd ? b.upd_lo[0][id] : b.sub_lo[0][id];
-        const float hi = upd ? b.upd_hi[0][id] : b.sub_hi[0][id];
+        const int64_t g = upd ? r - b.n : r;
+        const int inst = inst_of(upd ? b.m_base : b.n_base, b.num, g);
+        const int64_t local = g - (upd ? b.m_base[inst] : b.n_base[inst]);
+        const InstPtrs& ip = b.table[inst];
+        float lo = 0.f, hi = 0.f;
+        for (int k = 0; k < b.d; ++k) {
+            const float l = upd ? ip.upd_lo[k][local] : ip.sub_lo[k][local];
+            const float h = upd ? ip.upd_hi[k][local] : ip.sub_hi[k][local];
+            (upd ? b.upd_lo[k] : b.sub_lo[k])[g] = l;
+            (upd ? b.upd_hi[k] : b.sub_hi[k])[g] = h;
+            if (k == 0) {
+                lo = l;
+                hi = h;
+            }
+        }
         bad |= is_nan_bits(lo) || is_nan_bits(hi) || !(lo <= hi);
         const unsigned long long tag = (unsigned long long)inst << 32;
         keys[r] = tag | float_key(lo);
         keys[R + r] = tag | float_key(hi);
-        vals[r] = payload(upd ? KIND_ULO : KIND_SLO, (uint32_t)id);
-        vals[R + r] = payload(upd ? KIND_UHI : KIND_SHI, (uint32_t)id);
+        vals[r] = payload(upd ? KIND_ULO : KIND_SLO, (uint32_t)g);
+        vals[R + r] = payload(upd ? KIND_UHI : KIND_SHI, (uint32_t)g);
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0) raise_error(st, DDM_ERR_INVALID, 15);
 }
@@ -74,11 +64,6 @@ static unsigned grid_for(uint64_t items) {
     return (unsigned)(g < 1 ? 1 : (g > 152 * 16 ? 152 * 16 : g));
 }
 
-int launch_concat(const BatchArgs& b, cudaStream_t s) {
-    if (b.n + b.m == 0) return 0;
-    launch_k(k_concat, grid_for(b.n + b.m), 256, 0, s, b);
-    return 1;
-}
 
 int launch_keybuild_batch(const BatchArgs& b, unsigned long long* keys, uint32_t* vals,
                           DevStatus* st, cudaStream_t s) {

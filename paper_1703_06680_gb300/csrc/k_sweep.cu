@@ -33,10 +33,17 @@ __device__ __forceinline__ unsigned long long kind_inc(uint32_t kind) {
 // One thread's walk over its SCAN_ITEMS endpoints with exact exclusive counts:
 // the rank records, the order arrays, the per-id-tile count sums and (DBG) the
 // diagnostics.  FULL: every item lies before E, so there is no end test.
+// Adds x (< 2^32) to the 64-bit sum held as {low, high} 32-bit words in shared
+// memory: a native 32-bit atomic, and one more for the rare carry.
+__device__ __forceinline__ void add_u64_pair(uint32_t* w, uint32_t x) {
+    const uint32_t old = atomicAdd(&w[0], x);
+    if (old + x < old) atomicAdd(&w[1], 1u);
+}
+
 template <bool FULL, bool DBG>
 __device__ __forceinline__ void sweep_walk(const uint32_t (&v)[SCAN_ITEMS], uint64_t base,
                                            uint32_t E, uint32_t n, uint32_t m,
-                                           const Records& rec, unsigned long long* s_agg,
+                                           const Records& rec, uint32_t* s_agg,
                                            bool agg, uint32_t& cSlo, uint32_t& cUlo,
                                            uint32_t& cShi, DevStatus* st) {
 #pragma unroll
@@ -60,10 +67,10 @@ __device__ __forceinline__ void sweep_walk(const uint32_t (&v)[SCAN_ITEMS], uint
         const uint32_t z = is_upper ? (is_upd ? cUhi : cShi) : (is_upd ? cShi : cUhi);
         const uint32_t w = is_upper ? 0u : (is_upd ? cUlo : cSlo);
         tab[id] = make_uint4(p, y, z, w);
-        // B_i at S_i's upper endpoint, -C_i at its lower one (mod 2^64).
+        // B_i at S_i's upper endpoint, C_i at its lower one, summed apart: id tile t
+        // holds {B low, B high, C low, C high} at s_agg[4t].
         if (agg && !is_upd)
-            atomicAdd(&s_agg[id / OFF_TILE],
-                      is_upper ? (unsigned long long)y : 0ull - (unsigned long long)z);
+            add_u64_pair(&s_agg[4 * (id / OFF_TILE) + (is_upper ? 0 : 2)], is_upper ? y : z);
         if (!is_upper && rec.sub_order && w < (is_upd ? m : n))
             (is_upd ? rec.upd_order : rec.sub_order)[w] = id;
         cSlo += kind == KIND_SLO;
@@ -95,11 +102,11 @@ k_sweep_scan(const uint32_t* __restrict__ vals, uint32_t E, uint32_t n, uint32_t
     __shared__ uint32_t kind_sum[SCAN_BLOCK / 32][3];
     __shared__ unsigned long long tile_prefix[3];
     __shared__ uint32_t tile_id_s;
-    extern __shared__ unsigned long long s_agg[];  // cnt_tiles words when cnt_agg is set
+    extern __shared__ uint32_t s_agg[];  // 4 words per id tile when cnt_agg is set
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) tile_id_s = kinds ? blockIdx.x : atomicAdd(tile_counter, 1u);
     if (cnt_agg)
-        for (uint32_t t = tid; t < cnt_tiles; t += SCAN_BLOCK) s_agg[t] = 0ull;
+        for (uint32_t t = tid; t < 4 * cnt_tiles; t += SCAN_BLOCK) s_agg[t] = 0u;
     __syncthreads();
     const uint32_t tile = tile_id_s;
     const uint64_t base = (uint64_t)tile * SCAN_TILE + (uint64_t)tid * SCAN_ITEMS;
@@ -198,8 +205,12 @@ k_sweep_scan(const uint32_t* __restrict__ vals, uint32_t E, uint32_t n, uint32_t
             make_uint4(cSlo, cUlo, E - cSlo - cUlo - cShi, E);
     if (cnt_agg) {
         __syncthreads();
-        for (uint32_t t = tid; t < cnt_tiles; t += SCAN_BLOCK)
-            if (s_agg[t]) atomicAdd(&cnt_agg[t], s_agg[t]);
+        for (uint32_t t = tid; t < cnt_tiles; t += SCAN_BLOCK) {
+            const uint32_t* w = s_agg + 4 * t;
+            const unsigned long long b = ((unsigned long long)w[1] << 32) | w[0];
+            const unsigned long long c = ((unsigned long long)w[3] << 32) | w[2];
+            if (b != c) atomicAdd(&cnt_agg[t], b - c);  // mod 2^64: all blocks' terms add up
+        }
     }
 }
 
@@ -218,7 +229,7 @@ int launch_sweep_scan(const uint32_t* vals, uint64_t E, int64_t n, int64_t m, co
     // Window boundaries fall on a thread's first position (see k_sweep_scan).
     if (rec.windows && (1ull << rec.win_shift) % SCAN_ITEMS != 0) return -1;
     launch_k(rec.dbg_who ? k_sweep_scan<true> : k_sweep_scan<false>, (unsigned)tiles, SCAN_BLOCK,
-             ct * sizeof(unsigned long long), s, vals, (uint32_t)E, (uint32_t)n, (uint32_t)m, rec,
+             4 * ct * sizeof(uint32_t), s, vals, (uint32_t)E, (uint32_t)n, (uint32_t)m, rec,
              status, counter, reinterpret_cast<const uint4*>(kinds), cnt_agg, ct, st);
     return 1;
 }
@@ -247,7 +258,8 @@ int launch_rank_count(const Records& rec, int64_t n, int64_t m, uint32_t* cnt,
         return (unsigned)(g < 1 ? 1 : (g > 152 * 16 ? 152 * 16 : g));
     };
     int launches = 0;
-    if (n > 0) launch_k(k_rank_count, grid(n), 256, 0, s, rec.s_lo, rec.s_hi, n, cnt, st), ++launches;
+    if (n > 0)
+        launch_k(k_rank_count, grid(n), 256, 0, s, rec.s_lo, rec.s_hi, n, cnt, st), ++launches;
     if (upd_cnt && m > 0)
         launch_k(k_rank_count, grid(m), 256, 0, s, rec.u_lo, rec.u_hi, m, upd_cnt, st), ++launches;
     return launches;
