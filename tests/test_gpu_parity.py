@@ -74,6 +74,25 @@ def test_nd_full_size_complete(ctx, d, alpha):
     torch.cuda.empty_cache()
 
 
+def test_d1_beyond_the_scan_counter_limits(ctx):
+    # N = 9e6 (E = 1.8e7 endpoints, n = 4.5e6): more than 4096 scan tiles and more
+    # than 2048 subscription-id tiles, so the sweep and the offsets scan take their
+    # decoupled look-backs instead of the tile counters that the sort and the sweep
+    # form below those sizes (and the sort its flat scan); the complete pair list
+    # against the oracle, pooled.
+    import torch
+    from tests.oracle_pool import check_full
+    N = 9_000_000
+    reg = synth.large_1d(1.0, 0, N)
+    t = to_dev(reg)
+    K = ctx.count(*t)
+    pairs = ctx.match(*t, cap=K)
+    assert pairs.shape[0] == K
+    assert check_full(pairs, ("large_1d", (1.0, 0, N)), reg.n) == K
+    del pairs
+    torch.cuda.empty_cache()
+
+
 # --- the sweep stages (a1-a4) against the oracle's Algorithm 4 trace --------------
 
 def test_sweep_stages_match_oracle_trace(ctx):
