@@ -95,6 +95,7 @@ struct DevStatus {
     int detail;                // where a timeout or check fired (diagnostics)
     unsigned long long K;      // number of pairs (after the offsets scan)
     unsigned long long aux[6]; // per-call diagnostics / plans
+    unsigned long long flagged; // host copy only: subscriptions sent to the range path
 };
 
 __device__ __forceinline__ void raise_error(DevStatus* st, int code, int detail) {

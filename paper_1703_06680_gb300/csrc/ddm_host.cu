@@ -32,7 +32,8 @@ int launch_wp_write(int2* out, const unsigned long long* off, uint32_t nseg, uin
 // k_status.cu: a call's zero fill (status and zeroed workspace) and the status
 // copy into the mapped host mirror.
 int launch_prologue(DevStatus* st, void* zero, uint64_t zero_bytes, cudaStream_t s);
-int launch_publish(const DevStatus* st, DevStatus* host_mapped, cudaStream_t s);
+int launch_publish(const DevStatus* st, DevStatus* host_mapped, const uint32_t* flagged,
+                   cudaStream_t s);
 }
 
 struct ddm_ctx {
@@ -46,6 +47,13 @@ struct ddm_ctx {
     DevStatus* dstat = nullptr;  // device
     DevStatus* hstat = nullptr;  // pinned host mirror
     DevStatus* hstat_dev = nullptr;  // its device address when mapped (else NULL: copy)
+    // ddm_match on the window path: the range path (flagged subscriptions) is
+    // left out of the enqueued pipeline and launched after the one
+    // synchronisation only if the status reports flagged subscriptions.
+    bool defer_fallback = false;      // set by ddm_match around its enqueue
+    bool fallback_pending = false;    // the last enqueue left the range path out
+    EmitArgs fallback_args{};         // its arguments
+    const uint32_t* flag_count = nullptr;  // the flagged counter, for the next finish only
     // host-buffer entry point staging (inputs, outputs)
     char* io = nullptr;
     size_t io_size = 0;
@@ -575,9 +583,15 @@ int enqueue(ddm_ctx* c, const Job& job, Mode mode, int32_t* pairs, uint64_t cap,
     }
     else if (mode == Mode::Match) L += launch_emit_ranges(a, c->dstat, s);
     mark(c, 7);
-    if ((pl.window || pl.join) && mode == Mode::Match)
-        L += launch_emit_ranges(a, c->dstat, s);  // flagged subscriptions only
-    if (mode == Mode::Match) L += launch_segment_sort(a, c->dstat, s);
+    if (c->defer_fallback && pl.window && mode == Mode::Match && phase == Phase::All) {
+        c->fallback_args = a;  // range path of the flagged subscriptions, if any (ddm_match)
+        c->fallback_pending = true;
+        c->flag_count = pl.num_flagged;  // read by the next finish() only
+    } else {
+        if ((pl.window || pl.join) && mode == Mode::Match)
+            L += launch_emit_ranges(a, c->dstat, s);  // flagged subscriptions only
+        if (mode == Mode::Match) L += launch_segment_sort(a, c->dstat, s);
+    }
     mark(c, 8);
   }
     CK(cudaGetLastError());
@@ -596,7 +610,8 @@ int enqueue_plain(ddm_ctx* c, const ddm_regions* r, Mode mode, int32_t* pairs, u
 int finish(ddm_ctx* c, uint64_t* K_out) {
     if (c->hstat_dev) {
         PdlScope pdl_scope(c->pdl);
-        c->stats.launches += launch_publish(c->dstat, c->hstat_dev, c->stream);
+        c->stats.launches += launch_publish(c->dstat, c->hstat_dev, c->flag_count, c->stream);
+        c->flag_count = nullptr;  // one use: the workspace may move before the next call
         CK(cudaGetLastError());
     } else {
         CK(cudaMemcpyAsync(c->hstat, c->dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost,
@@ -975,10 +990,28 @@ int ddm_match(ddm_ctx* c, const ddm_regions* r, int32_t* pairs, uint64_t cap, ui
         rc = match_from_survivors(c, job, pairs, cap, K_out);
         if (rc != MATCH_RETRY) return rc;
     }
+    c->defer_fallback = c->hstat_dev != nullptr;  // the flagged count reaches the host
+    c->fallback_pending = false;
     rc = enqueue_plain(c, &ro, Mode::Match, pairs, cap, nullptr);
-    if (rc) return rc;
+    c->defer_fallback = false;
+    if (rc) {
+        c->fallback_pending = false;
+        c->flag_count = nullptr;
+        return rc;
+    }
     uint64_t K = 0;
     rc = finish(c, &K);
+    c->flag_count = nullptr;
+    if (c->fallback_pending) {  // window path: the range path only when it has work
+        c->fallback_pending = false;
+        if (rc == DDM_OK && c->hstat->flagged > 0) {
+            PdlScope pdl_scope(c->pdl);
+            c->stats.launches += launch_emit_ranges(c->fallback_args, c->dstat, c->stream);
+            c->stats.launches += launch_segment_sort(c->fallback_args, c->dstat, c->stream);
+            CK(cudaGetLastError());
+            rc = finish(c, &K);
+        }
+    }
     if (K_out) *K_out = K;
     if (ro.d > 1 && (rc == DDM_OK || rc == DDM_ERR_CAPACITY)) c->surv_hint = K;
     return rc;
